@@ -1,0 +1,320 @@
+"""Benchmark of the APRIL intermediate filter on GB300.
+
+One step = one pass of the filter (Algorithm 2 on every candidate pair) over
+the paper-scale workload: 200k + 200k synthetic star polygons on a 2^16 grid,
+~2.7M MBR-join candidate pairs (seeded; the synthetic stand-in for the
+paper's TIGER/OSM joins).  The A/F sets are built and uploaded once (the
+paper precomputes approximations); the timed region runs the filter kernels
+on pairs and sets already resident in HBM.  L2 is flushed between timed
+steps.
+
+Output: one JSON line (rank 0).  `value` is pairs/s of the selected mode
+(default: batched); the line also carries the plain one-pair-per-thread
+kernel's pairs/s on the same pairs, the end-to-end number through the
+host-buffer entry point, the HBM roofline of the dominant kernel, and the
+oracle's CPU throughput on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode batched|warp|plain]
+  python bench.py --impl reference ...   # the oracle (CPU) on the same workload
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "APRIL filter pairs/s & HBM GB/s (batched vs plain); serving p50/p99 latency"
+CONFIG_NAMES = {1: "tiny-plain-1k", 2: "paper-scale-200k", 3: "skewed-pareto-200k"}
+PAIR_ID_BYTES = 8       # r and s ids
+DESC_BYTES = 32         # two 16-byte object descriptors
+VERDICT_BYTES = 1
+IV_BYTES = 8            # one interval = two uint32
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3])
+    ap.add_argument("--mode", default="batched", choices=["batched", "warp", "plain"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    src = open(os.path.join(ROOT, "paper_2307_01716_gb300", "csrc", "filter.cu"), "rb").read()
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    for e in json.load(open(p)):
+        if e.get("kernel") == kernel and e.get("workload") == workload and e.get("src_sha") == sha:
+            return e.get("dram_bytes_per_launch")
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self):
+        self.proc = None
+        self.path = os.path.join(tempfile.gettempdir(), f"april_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self, device_index: int = 0):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9 or parts[0] != str(device_index):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(w, seconds: float, seed: int = 1234):
+    """The oracle, as it stands, on a bounded random sample of the pairs."""
+    import oracle
+    g = oracle.Grid(w.order)
+    rng = np.random.default_rng(seed)
+    done = 0
+    t0 = time.perf_counter()
+    batch = 200
+    while time.perf_counter() - t0 < seconds:
+        idx = np.sort(rng.choice(len(w.pr), batch, replace=False))
+        oracle.verdicts(w.R.xy, w.R.off, w.S.xy, w.S.off, w.pr[idx], w.ps[idx], g)
+        done += batch
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} random pairs of the {len(w.pr)} (seeded), cell-set oracle, single thread, "
+                      f"{dt:.1f} s"}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from synth import configs
+    import oracle
+    w = configs.make(args.config)
+    g = oracle.Grid(w.order)
+    rng = np.random.default_rng(99)
+    per_step = 300
+    times = []
+    for step in range(args.warmup + args.steps):
+        idx = np.sort(rng.choice(len(w.pr), per_step, replace=False))
+        t0 = time.perf_counter()
+        oracle.verdicts(w.R.xy, w.R.off, w.S.xy, w.S.off, w.pr[idx], w.ps[idx], g)
+        if step >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    value = per_step * len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": {"workload": w.name, "pairs": int(len(w.pr)),
+                                              "sample_pairs_per_step": per_step},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} random pairs per step of {len(w.pr)}"},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    from synth import configs
+    from paper_2307_01716_gb300 import april as A
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = configs.make(args.config)
+    grid = A.global_grid(w.order)
+    R = A.april_build_sets(w.R.xy, w.R.off, grid)
+    S = A.april_build_sets(w.S.xy, w.S.off, grid)
+    dR, dS = A.april_upload(R, dev), A.april_upload(S, dev)
+    ctx = A.Context(local)
+    n = len(w.pr)
+    d_r = torch.from_numpy(w.pr.view(np.int32)).to(dev)
+    d_s = torch.from_numpy(w.ps.view(np.int32)).to(dev)
+    out = torch.empty(n, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    # algorithmic bytes: the intervals sequential Algorithm 2 reads, per pair
+    host_v, consumed = A.april_host_filter(R, S, w.pr, w.ps)
+    b_alg = float(IV_BYTES * consumed.sum() + n * (PAIR_ID_BYTES + DESC_BYTES + VERDICT_BYTES))
+
+    def make_runner(mode_name):
+        m = A.MODES[mode_name]
+        sb = ctx.scratch_bytes(m, n)
+        scratch = torch.empty(max(sb, 256), dtype=torch.uint8, device=dev) if sb else None
+
+        def run():
+            ctx.april_filter_pairs(dR, dS, d_r, d_s, n, out, m, scratch, stream)
+        return run
+
+    def time_mode(mode_name, steps, warmup):
+        run = make_runner(mode_name)
+        for _ in range(warmup):
+            run()
+        ctx.april_sync_status(stream)
+        if not np.array_equal(out.cpu().numpy(), host_v):
+            raise SystemExit(f"mode {mode_name}: verdicts differ from Algorithm 2 on the host")
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        for k in range(steps):
+            flush.fill_(k & 0xFF)
+            evs[k][0].record(stream)
+            run()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            dist.barrier()
+        ctx.april_sync_status(stream)
+        return [a.elapsed_time(b) for a, b in evs]
+
+    mode = args.mode
+    try:
+        ctx.scratch_bytes(A.MODES[mode], n)
+    except A.AprilError:
+        mode = "warp"
+    clocks = Clocks()
+    clocks.start()
+    t_main = time_mode(mode, args.steps, args.warmup)
+    clk = clocks.stop(local)
+    t_plain = time_mode("plain", max(3, args.steps // 2), args.warmup) if mode != "plain" else t_main
+
+    ms = statistics.mean(t_main)
+    ms_t = torch.tensor([ms], device=dev)
+    if ws > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = ws * n / (ms_max * 1e-3)
+    plain_ms = statistics.mean(t_plain)
+
+    # end to end through the host-buffer entry point (pinned host pairs in,
+    # host verdicts out, copies inside the timed region)
+    m = A.MODES[mode]
+    work = torch.empty(ctx.host_work_bytes(m, n), dtype=torch.uint8, device=dev)
+    h_r = torch.from_numpy(w.pr.view(np.int32)).pin_memory()
+    h_s = torch.from_numpy(w.ps.view(np.int32)).pin_memory()
+    h_v = torch.empty(n, dtype=torch.uint8).pin_memory()
+    for _ in range(args.warmup):
+        ctx.april_filter_pairs_host(dR, dS, h_r, h_s, n, h_v, m, work, stream)
+    e2e_t = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        ctx.april_filter_pairs_host(dR, dS, h_r, h_s, n, h_v, m, work, stream)
+        e2e_t.append(time.perf_counter() - t0)
+    if not np.array_equal(h_v.numpy(), host_v):
+        raise SystemExit("end-to-end verdicts differ")
+    e2e_s = statistics.mean(e2e_t)
+
+    peak, peak_kind = peaks()
+    achieved = b_alg / (ms * 1e-3) / 1e9
+    kernel_name = {"plain": "k_plain", "warp": "k_warp", "batched": "k_batched"}[mode]
+    traffic = kernel_traffic(kernel_name, w.name)
+    launches = {"plain": 1, "warp": 1, "batched": 1}[mode]
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": w.name, "polygons_per_side": int(w.R.n), "grid_order": w.order,
+                   "pairs": n, "mode": mode, "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "plain": {"pairs_per_s": n / (plain_ms * 1e-3), "ms_per_step": plain_ms,
+                  "speedup_of_mode": plain_ms / ms},
+        "useful_GBps": achieved,
+        "algorithmic_bytes_per_step": b_alg,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": kernel_name,
+                     "peak_kind": f"{peak_kind} copy bandwidth (burst)"},
+        "e2e": {"value": n / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": n},
+        "gpu_launches": launches * args.steps,
+        "clocks": clk,
+        "verdict_mix": (np.bincount(host_v, minlength=3)[:3] / n).round(4).tolist(),
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+        line["cpu_baseline"]["cpu"] = os.uname().machine
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,219 @@
+/*
+ * april.h -- C ABI of the GB300 APRIL intermediate filter.
+ *
+ * APRIL (Georgiadis, Tzirita Zacharatou, Mamoulis, "Raster Interval Object
+ * Approximations for Spatial Intersection Joins", arXiv 2307.01716)
+ * approximates every polygon by two sorted lists of disjoint Hilbert-order
+ * cell intervals on a 2^N x 2^N grid (Sec. 4.1): the A-list (every cell the
+ * polygon meets) and the F-list (the cells it fully covers).  For a candidate
+ * pair (r, s) from an MBR join, three merge joins decide the pair
+ * (Sec. 4.2, Algorithm 2):
+ *     A(r) x A(s) has no overlapping intervals        -> true negative
+ *     A(r) x F(s) or F(r) x A(s) has an overlap       -> true hit
+ *     otherwise                                       -> inconclusive
+ *
+ * Conventions
+ *   - Every function returns an april_status: APRIL_OK (0), APRIL_PENDING (1)
+ *     or a negative error code.  No C++ exception crosses this boundary.
+ *     april_last_error() returns the text of the most recent error of the
+ *     calling thread.
+ *   - Coordinates are integer lattice points: the data space [0,1]^2 is the
+ *     lattice {0..2^24}^2.  Cell corners and centres of any grid with a cell
+ *     side of at least 2 lattice units are lattice points, so all geometric
+ *     predicates are exact.
+ *   - Intervals are half-open [st, end) of uint32 Hilbert ids (Sec. 3.2,
+ *     Sec. 4.1).  On a 2^16 grid the end of an interval that contains the
+ *     last cell (id 2^32 - 1) is stored as 0 (2^32 mod 2^32); consumers
+ *     compare "last = end - 1" in uint32 arithmetic.
+ *   - Device memory and streams belong to the caller.  "stream" arguments are
+ *     cudaStream_t values passed as void*.  The library never frees caller
+ *     memory.  Objects the library allocates (april_sets, april_ctx) are
+ *     released by their *_destroy function.
+ */
+#ifndef APRIL_H
+#define APRIL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t april_status;
+
+#define APRIL_OK 0
+#define APRIL_PENDING 1
+#define APRIL_ERR_INVALID_ARG (-1)      /* bad pointer, size, mode or grid */
+#define APRIL_ERR_OUT_OF_RANGE_ID (-2)  /* a pair names an object id >= n_objects */
+#define APRIL_ERR_OVER_BUDGET (-3)      /* a request exceeds the memory budget */
+#define APRIL_ERR_CUDA (-4)             /* a CUDA runtime call failed */
+#define APRIL_ERR_DEVICE_TIMEOUT (-5)   /* a bounded device wait ran out */
+#define APRIL_ERR_CANCELLED (-6)        /* the request was cancelled */
+#define APRIL_ERR_NO_MEMORY (-7)        /* host allocation failed */
+#define APRIL_ERR_GEOMETRY (-8)         /* degenerate polygon (< 3 vertices, outside the grid) */
+
+/* Verdict byte per pair (Algorithm 2; "refinement" is returned as
+ * APRIL_INCONCLUSIVE instead of being run). */
+#define APRIL_TRUE_NEGATIVE 0
+#define APRIL_TRUE_HIT 1
+#define APRIL_INCONCLUSIVE 2
+#define APRIL_VERDICT_ERROR 0xFF        /* the pair named an out-of-range object */
+
+/* Filter kernels (see april_filter_pairs). */
+#define APRIL_MODE_PLAIN 0    /* one pair per thread, Algorithm 2 as written */
+#define APRIL_MODE_WARP 1     /* one pair per warp, windowed parallel merge */
+#define APRIL_MODE_BATCHED 2  /* length-binned persistent kernel, long pairs split over a CTA */
+
+/* A 2^order x 2^order grid of square cells of side 2^log2_cell lattice units
+ * with lower-left corner (ox, oy) (Sec. 3.1: one global grid per data space;
+ * Sec. 5.2: one per partition).  1 <= order <= 16, log2_cell >= 1.  The
+ * global grid of order N over [0,1]^2 is {0, 0, 24 - N, N}. */
+typedef struct april_grid {
+    int64_t ox;
+    int64_t oy;
+    uint32_t log2_cell;
+    uint32_t order;
+} april_grid;
+
+/* ---------------------------------------------------------------- errors */
+
+/* Copies the calling thread's most recent error message (NUL-terminated,
+ * truncated to buf_size) into buf.  Returns APRIL_OK. */
+april_status april_last_error(char *buf, size_t buf_size);
+
+/* --------------------------------------------------------- construction */
+
+/* Host-side A/F interval lists of a polygon set (library-owned). */
+typedef struct april_sets april_sets;
+
+/* Builds the APRIL approximation of n_polys simple polygons (Sec. 4.1 lists;
+ * construction in the spirit of Sec. 6: the cells an edge touches are found by
+ * exact grid traversal, the cells between them in Hilbert order are
+ * classified one gap at a time by a point-in-polygon test, Sec. 6.2).
+ *
+ *   xy        int32 lattice coordinates, interleaved x,y; polygon p owns
+ *             vertices vert_off[p] .. vert_off[p+1]-1 (the ring is implicitly
+ *             closed; either orientation).  Host memory, read only.
+ *   vert_off  n_polys+1 uint64 offsets (in vertices).
+ *   grid      the grid (see april_grid).  Every polygon must meet the grid.
+ *   n_threads host threads to use (0 = all hardware threads).
+ *   out       receives the new sets; free with april_sets_destroy.
+ *
+ * Cell semantics: a closed cell is in A when it meets the closed polygon and
+ * in F when it lies inside it.  Lists are maximal (consecutive ids merged).
+ * Errors: APRIL_ERR_INVALID_ARG (null pointers, bad grid),
+ * APRIL_ERR_GEOMETRY (a polygon with < 3 vertices or outside the grid),
+ * APRIL_ERR_NO_MEMORY. */
+april_status april_build_sets(const int32_t *xy, const uint64_t *vert_off, uint32_t n_polys,
+                              const april_grid *grid, uint32_t n_threads, april_sets **out);
+
+void april_sets_destroy(april_sets *sets);
+
+typedef struct april_sets_info {
+    uint32_t n_objects;
+    uint32_t order;
+    uint64_t a_intervals;    /* total A intervals */
+    uint64_t f_intervals;    /* total F intervals */
+    uint64_t iv_slots;       /* interval slots in the device image (with alignment padding) */
+    uint64_t device_bytes;   /* bytes april_upload needs */
+} april_sets_info;
+
+april_status april_sets_get_info(const april_sets *sets, april_sets_info *info);
+
+/* Host view of one list: *iv points to 2*(*n) uint32 values st0,end0,st1,...
+ * owned by the sets.  which: 0 = A-list, 1 = F-list. */
+april_status april_sets_list(const april_sets *sets, uint32_t obj, int which, const uint32_t **iv,
+                             uint32_t *n);
+
+/* ------------------------------------------------------------ device sets */
+
+/* Device image of a set, as written by april_upload.
+ *   desc: n_objects records of 4 uint32 {a_off, a_len, f_off, f_len};
+ *         offsets count intervals from iv and are even (16-byte aligned).
+ *   iv:   iv_slots intervals of 2 uint32 {st, end}.
+ * Both pointers are device addresses inside the caller's buffer. */
+typedef struct april_dev_sets {
+    const uint32_t *desc;
+    const uint32_t *iv;
+    uint32_t n_objects;
+    uint32_t order;
+    uint64_t iv_slots;
+} april_dev_sets;
+
+/* Copies the sets into a caller-allocated device buffer of at least
+ * info.device_bytes bytes (256-byte aligned), asynchronously on stream, and
+ * fills *out.  The host sets must stay alive until the copy completed. */
+april_status april_upload(const april_sets *sets, void *dev_buf, size_t dev_bytes, void *stream,
+                          april_dev_sets *out);
+
+/* ---------------------------------------------------------------- context */
+
+typedef struct april_ctx april_ctx;
+
+/* Creates a filter context on CUDA device `device`.  The context owns a
+ * 256-byte device status block (allocated here with cudaMalloc) that kernels
+ * use to report out-of-range ids and exhausted waits. */
+april_status april_ctx_create(int device, april_ctx **out);
+void april_ctx_destroy(april_ctx *ctx);
+
+/* ------------------------------------------------------------------ filter */
+
+/* Device scratch (bytes) april_filter_pairs needs for `mode` and n pairs.
+ * PLAIN and WARP need none. */
+april_status april_filter_scratch_bytes(int mode, uint64_t n, size_t *bytes);
+
+/* Runs the APRIL intermediate filter (Algorithm 2) on n candidate pairs.
+ *
+ *   R, S       device sets from april_upload (same grid).
+ *   d_r, d_s   device arrays of n uint32 object ids (pair k = (d_r[k], d_s[k])).
+ *   d_verdict  device array of n bytes; receives APRIL_TRUE_NEGATIVE,
+ *              APRIL_TRUE_HIT, APRIL_INCONCLUSIVE, or APRIL_VERDICT_ERROR for
+ *              a pair with an out-of-range id.
+ *   mode       APRIL_MODE_PLAIN / _WARP / _BATCHED.
+ *   d_scratch  device scratch of april_filter_scratch_bytes() bytes
+ *              (256-byte aligned), or NULL when that is 0.
+ *   stream     cudaStream_t (void*); all work is enqueued on it.
+ *
+ * Asynchronous: launch errors are returned at once; device-side errors (an
+ * out-of-range id, an exhausted bounded wait) are recorded in the context and
+ * returned by april_sync_status.  n == 0 is a no-op. */
+april_status april_filter_pairs(april_ctx *ctx, const april_dev_sets *R, const april_dev_sets *S,
+                                const uint32_t *d_r, const uint32_t *d_s, uint64_t n, uint8_t *d_verdict,
+                                int mode, void *d_scratch, size_t scratch_bytes, void *stream);
+
+/* End-to-end variant for host data: copies the n pairs from host memory to the
+ * device, runs april_filter_pairs, copies the n verdicts back to host memory,
+ * and waits for the stream.  h_r, h_s and h_verdict are host arrays (pinned
+ * memory makes the copies asynchronous DMA); d_work is a caller-allocated
+ * device buffer of april_filter_host_work_bytes() bytes (256-byte aligned)
+ * that holds the staged pairs, the verdicts and the mode's scratch.
+ * Returns the same codes as april_filter_pairs followed by april_sync_status. */
+april_status april_filter_host_work_bytes(int mode, uint64_t n, size_t *bytes);
+april_status april_filter_pairs_host(april_ctx *ctx, const april_dev_sets *R, const april_dev_sets *S,
+                                     const uint32_t *h_r, const uint32_t *h_s, uint64_t n, uint8_t *h_verdict,
+                                     int mode, void *d_work, size_t work_bytes, void *stream);
+
+/* Waits for `stream`, then returns and clears the context's device status:
+ * APRIL_OK, APRIL_ERR_OUT_OF_RANGE_ID or APRIL_ERR_DEVICE_TIMEOUT (or
+ * APRIL_ERR_CUDA if the stream itself failed). */
+april_status april_sync_status(april_ctx *ctx, void *stream);
+
+/* ----------------------------------------------------- host Algorithm 2 */
+
+/* Algorithm 2 exactly as printed (sequential merge joins AA, AF, FA with early
+ * exit), run on the host over built sets; a CPU reference execution of the
+ * paper's method used for measurement, never by april_filter_pairs.
+ * consumed[k] (optional) receives the number of intervals the three joins read
+ * for pair k: for every join that ran, (position where the merge stopped + 1)
+ * on each side, capped at the list lengths.  Out-of-range ids give
+ * APRIL_VERDICT_ERROR and consumed 0. */
+april_status april_host_filter(const april_sets *R, const april_sets *S, const uint32_t *pr,
+                               const uint32_t *ps, uint64_t n, uint32_t n_threads, uint8_t *verdict,
+                               uint64_t *consumed);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* APRIL_H */

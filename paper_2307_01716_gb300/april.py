@@ -1,0 +1,239 @@
+"""Thin ctypes binding of libapril (include/april.h).
+
+Argument marshalling only: every step of the filter runs inside libapril's
+CUDA kernels.  PyTorch supplies device memory and streams.  Importing this
+module loads the in-tree libapril.so and raises if it is missing; there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libapril.so")
+
+APRIL_OK = 0
+APRIL_PENDING = 1
+ERRORS = {
+    -1: "INVALID_ARG", -2: "OUT_OF_RANGE_ID", -3: "OVER_BUDGET", -4: "CUDA_ERROR",
+    -5: "DEVICE_TIMEOUT", -6: "CANCELLED", -7: "NO_MEMORY", -8: "GEOMETRY",
+}
+TRUE_NEGATIVE, TRUE_HIT, INCONCLUSIVE, VERDICT_ERROR = 0, 1, 2, 0xFF
+MODE_PLAIN, MODE_WARP, MODE_BATCHED = 0, 1, 2
+MODES = {"plain": MODE_PLAIN, "warp": MODE_WARP, "batched": MODE_BATCHED}
+
+
+class AprilError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"april status {status} ({ERRORS.get(status, '?')}): {msg}")
+        self.status = status
+
+
+class april_grid(ctypes.Structure):
+    _fields_ = [("ox", ctypes.c_int64), ("oy", ctypes.c_int64),
+                ("log2_cell", ctypes.c_uint32), ("order", ctypes.c_uint32)]
+
+
+class april_sets_info(ctypes.Structure):
+    _fields_ = [("n_objects", ctypes.c_uint32), ("order", ctypes.c_uint32),
+                ("a_intervals", ctypes.c_uint64), ("f_intervals", ctypes.c_uint64),
+                ("iv_slots", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64)]
+
+
+class april_dev_sets(ctypes.Structure):
+    _fields_ = [("desc", ctypes.c_void_p), ("iv", ctypes.c_void_p), ("n_objects", ctypes.c_uint32),
+                ("order", ctypes.c_uint32), ("iv_slots", ctypes.c_uint64)]
+
+
+_vp = ctypes.c_void_p
+_u32 = ctypes.c_uint32
+_u64 = ctypes.c_uint64
+_st = ctypes.c_int32
+
+# name -> (restype, argtypes); the same names as include/april.h
+SIGNATURES = {
+    "april_last_error": (_st, [ctypes.c_char_p, ctypes.c_size_t]),
+    "april_build_sets": (_st, [_vp, _vp, _u32, ctypes.POINTER(april_grid), _u32, ctypes.POINTER(_vp)]),
+    "april_sets_destroy": (None, [_vp]),
+    "april_sets_get_info": (_st, [_vp, ctypes.POINTER(april_sets_info)]),
+    "april_sets_list": (_st, [_vp, _u32, ctypes.c_int, ctypes.POINTER(ctypes.POINTER(_u32)),
+                              ctypes.POINTER(_u32)]),
+    "april_upload": (_st, [_vp, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(april_dev_sets)]),
+    "april_ctx_create": (_st, [ctypes.c_int, ctypes.POINTER(_vp)]),
+    "april_ctx_destroy": (None, [_vp]),
+    "april_filter_scratch_bytes": (_st, [ctypes.c_int, _u64, ctypes.POINTER(ctypes.c_size_t)]),
+    "april_filter_pairs": (_st, [_vp, ctypes.POINTER(april_dev_sets), ctypes.POINTER(april_dev_sets), _vp, _vp,
+                                 _u64, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
+    "april_sync_status": (_st, [_vp, _vp]),
+    "april_filter_host_work_bytes": (_st, [ctypes.c_int, _u64, ctypes.POINTER(ctypes.c_size_t)]),
+    "april_filter_pairs_host": (_st, [_vp, ctypes.POINTER(april_dev_sets), ctypes.POINTER(april_dev_sets), _vp, _vp,
+                                      _u64, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
+    "april_host_filter": (_st, [_vp, _vp, _vp, _vp, _u64, _u32, _vp, _vp]),
+}
+
+_lib = None
+
+
+def load():
+    """Load libapril.so (building it first if the sources are newer)."""
+    global _lib
+    if _lib is None:
+        from . import build as _build
+        if not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libapril.so missing at {LIB_PATH}")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(512)
+    load().april_last_error(buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+def check(status: int) -> int:
+    if status < 0:
+        raise AprilError(status, last_error())
+    return status
+
+
+def _ptr(a) -> int:
+    """Address of a numpy array or torch tensor (no copy)."""
+    if a is None:
+        return 0
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def global_grid(order: int) -> april_grid:
+    return april_grid(0, 0, 24 - order, order)
+
+
+def grid(order: int, ox: int = 0, oy: int = 0, log2_cell: int | None = None) -> april_grid:
+    return april_grid(int(ox), int(oy), 24 - order if log2_cell is None else int(log2_cell), order)
+
+
+class Sets:
+    """Host A/F lists of one polygon set (april_build_sets)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.april_sets_destroy(self.handle)
+            self.handle = None
+
+    def info(self) -> april_sets_info:
+        inf = april_sets_info()
+        check(load().april_sets_get_info(self.handle, ctypes.byref(inf)))
+        return inf
+
+    def list(self, obj: int, which: int) -> np.ndarray:
+        """(n, 2) uint32 array [st, end) of the A (which=0) or F (1) list."""
+        p = ctypes.POINTER(_u32)()
+        n = _u32()
+        check(load().april_sets_list(self.handle, obj, which, ctypes.byref(p), ctypes.byref(n)))
+        if n.value == 0:
+            return np.zeros((0, 2), dtype=np.uint32)
+        return np.ctypeslib.as_array(p, shape=(n.value * 2,)).reshape(-1, 2).copy()
+
+
+def april_build_sets(xy: np.ndarray, vert_off: np.ndarray, grd: april_grid, n_threads: int = 0) -> Sets:
+    xy32 = np.ascontiguousarray(xy, dtype=np.int32).reshape(-1)
+    off = np.ascontiguousarray(vert_off, dtype=np.uint64)
+    h = _vp()
+    check(load().april_build_sets(_ptr(xy32), _ptr(off), len(off) - 1, ctypes.byref(grd), n_threads,
+                                  ctypes.byref(h)))
+    return Sets(h.value)
+
+
+@dataclass
+class DevSets:
+    """A device image of Sets; `buf` (a torch uint8 tensor) keeps the memory alive."""
+    c: april_dev_sets
+    buf: object
+
+    @property
+    def nbytes(self) -> int:
+        return int(self.buf.numel())
+
+
+def april_upload(sets: Sets, device=None, stream=None) -> DevSets:
+    import torch
+    inf = sets.info()
+    buf = torch.empty(max(int(inf.device_bytes), 256), dtype=torch.uint8, device=device or "cuda")
+    out = april_dev_sets()
+    st = stream if stream is not None else torch.cuda.current_stream(buf.device)
+    check(load().april_upload(sets.handle, buf.data_ptr(), buf.numel(), st.cuda_stream, ctypes.byref(out)))
+    st.synchronize()  # the host image may be released after this
+    return DevSets(out, buf)
+
+
+class Context:
+    """april_ctx: device status block and kernel dispatch."""
+
+    def __init__(self, device: int = 0):
+        h = _vp()
+        check(load().april_ctx_create(device, ctypes.byref(h)))
+        self.handle = h.value
+        self.device = device
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.april_ctx_destroy(self.handle)
+            self.handle = None
+
+    def scratch_bytes(self, mode: int, n: int) -> int:
+        b = ctypes.c_size_t()
+        check(load().april_filter_scratch_bytes(mode, n, ctypes.byref(b)))
+        return b.value
+
+    def april_filter_pairs(self, R: DevSets, S: DevSets, d_r, d_s, n: int, d_verdict, mode: int,
+                           scratch=None, stream=None) -> None:
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream()
+        sb = 0 if scratch is None else int(scratch.numel() * scratch.element_size())
+        check(load().april_filter_pairs(self.handle, ctypes.byref(R.c), ctypes.byref(S.c), _ptr(d_r), _ptr(d_s),
+                                        n, _ptr(d_verdict), mode, _ptr(scratch), sb, st.cuda_stream))
+
+    def host_work_bytes(self, mode: int, n: int) -> int:
+        b = ctypes.c_size_t()
+        check(load().april_filter_host_work_bytes(mode, n, ctypes.byref(b)))
+        return b.value
+
+    def april_filter_pairs_host(self, R: DevSets, S: DevSets, h_r, h_s, n: int, h_verdict, mode: int, work,
+                                stream=None) -> int:
+        """Host pairs in, host verdicts out (synchronous); `work` is a device uint8 tensor."""
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream()
+        return check(load().april_filter_pairs_host(self.handle, ctypes.byref(R.c), ctypes.byref(S.c), _ptr(h_r),
+                                                    _ptr(h_s), n, _ptr(h_verdict), mode, _ptr(work),
+                                                    int(work.numel()), st.cuda_stream))
+
+    def april_sync_status(self, stream=None) -> int:
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream()
+        return check(load().april_sync_status(self.handle, st.cuda_stream))
+
+
+def april_host_filter(R: Sets, S: Sets, pr: np.ndarray, ps: np.ndarray, n_threads: int = 0):
+    """Host Algorithm 2 over built sets: (verdicts, consumed intervals)."""
+    pr = np.ascontiguousarray(pr, dtype=np.uint32)
+    ps = np.ascontiguousarray(ps, dtype=np.uint32)
+    v = np.zeros(len(pr), dtype=np.uint8)
+    c = np.zeros(len(pr), dtype=np.uint64)
+    check(load().april_host_filter(R.handle, S.handle, _ptr(pr), _ptr(ps), len(pr), n_threads, _ptr(v), _ptr(c)))
+    return v, c

@@ -1,0 +1,501 @@
+// Host construction of APRIL approximations (A- and F-interval lists), the
+// sets' accessors, and a host execution of Algorithm 2 used for measurement.
+//
+// Construction (paper Sec. 4.1 for what the lists hold, Sec. 6 for how):
+//  1. Touched cells.  For every edge, each cell row its closed y-range meets is
+//     intersected exactly (rational arithmetic in int64) with the edge to get
+//     the x-range of the edge inside that closed row strip; every closed cell
+//     of that x-range meets the edge.  For each such cell an exact
+//     separating-axis test tells whether the edge also enters the cell's OPEN
+//     square ("crossed").  This is the grid traversal of Sec. 6.1 done row by
+//     row, with closed cells so that edges along grid lines and through grid
+//     corners mark every cell they touch.
+//  2. The touched cells are sorted by Hilbert id.  Between two consecutive
+//     touched ids lies a gap of untouched cells; consecutive Hilbert cells
+//     share an edge, and an untouched cell is either inside the polygon or
+//     disjoint from it, so a whole gap is one class and a single
+//     point-in-polygon test at its first cell decides it (Sec. 6.2, Alg. 3's
+//     observation).  A touched cell that is not crossed is Full when its
+//     centre is inside the polygon (it touches the boundary only along its
+//     border), otherwise Partial.  Crossed cells are Partial.
+//  3. One pass over the sorted ids emits maximal A intervals (all non-empty
+//     cells) and F intervals (Full cells).
+// Point-in-polygon tests use a crossing count against the edges bucketed by
+// the cell row whose centre line they straddle.
+
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <thread>
+
+#include "april_internal.h"
+
+namespace april {
+
+static thread_local std::string g_last_error;
+
+april_status fail(april_status code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+namespace {
+
+// ---------------------------------------------------------------- Hilbert
+// The curve of Sec. 3.2 (orientation: the order-1 curve visits (0,0), (0,1),
+// (1,1), (1,0)).  Walking down the levels, the sub-square the point lies in
+// is traversed by the base curve under one of four symmetries of the square:
+// identity, transpose (x<->y), anti-transpose ((x,y) -> (~y,~x) per bit) and
+// the half turn ((x,y) -> (~x,~y)).  Quadrant 0 of the base curve carries the
+// transpose, quadrant 3 the anti-transpose, quadrants 1 and 2 the identity;
+// these four maps form a Klein group, so the state update is a table lookup.
+enum : uint8_t { SYM_I = 0, SYM_T = 1, SYM_A = 2, SYM_R = 3 };
+static const uint8_t kAfterT[4] = {SYM_T, SYM_I, SYM_R, SYM_A};
+static const uint8_t kAfterA[4] = {SYM_A, SYM_R, SYM_I, SYM_T};
+
+inline void apply_sym(uint8_t s, uint32_t &bx, uint32_t &by) {
+    uint32_t x = bx, y = by;
+    switch (s) {
+        case SYM_I: break;
+        case SYM_T: bx = y; by = x; break;
+        case SYM_A: bx = y ^ 1u; by = x ^ 1u; break;
+        default: bx = x ^ 1u; by = y ^ 1u; break;
+    }
+}
+
+inline uint64_t hilbert_id(uint32_t order, uint32_t x, uint32_t y) {
+    uint8_t s = SYM_I;
+    uint64_t d = 0;
+    for (int k = (int)order - 1; k >= 0; --k) {
+        uint32_t bx = (x >> k) & 1u, by = (y >> k) & 1u;
+        apply_sym(s, bx, by);
+        uint32_t digit = (bx << 1) | (bx ^ by);  // (0,0)->0 (0,1)->1 (1,1)->2 (1,0)->3
+        d = (d << 2) | digit;
+        if (digit == 0) s = kAfterT[s];
+        else if (digit == 3) s = kAfterA[s];
+    }
+    return d;
+}
+
+inline void hilbert_cell(uint32_t order, uint64_t d, uint32_t &x, uint32_t &y) {
+    uint8_t s = SYM_I;
+    x = y = 0;
+    for (int k = (int)order - 1; k >= 0; --k) {
+        uint32_t digit = (uint32_t)(d >> (2 * k)) & 3u;
+        uint32_t bx = digit >> 1, by = (digit >> 1) ^ (digit & 1u);
+        apply_sym(s, bx, by);  // every symmetry here is its own inverse
+        x |= bx << k;
+        y |= by << k;
+        if (digit == 0) s = kAfterT[s];
+        else if (digit == 3) s = kAfterA[s];
+    }
+}
+
+// ------------------------------------------------------------- predicates
+inline int64_t floor_div(int64_t a, int64_t b) {  // b > 0
+    int64_t q = a / b;
+    return (a % b != 0 && a < 0) ? q - 1 : q;
+}
+inline int64_t ceil_div(int64_t a, int64_t b) { return -floor_div(-a, b); }
+
+inline int64_t turn(int64_t ax, int64_t ay, int64_t bx, int64_t by, int64_t px, int64_t py) {
+    return (bx - ax) * (py - ay) - (by - ay) * (px - ax);
+}
+
+// Closed segment vs open square (x0,x0+h) x (y0,y0+h): they are disjoint iff
+// weakly separated along x, along y, or along the segment's normal.
+inline bool enters_open_square(int64_t ax, int64_t ay, int64_t bx, int64_t by, int64_t x0, int64_t y0,
+                               int64_t h) {
+    int64_t x1 = x0 + h, y1 = y0 + h;
+    if (std::max(ax, bx) <= x0 || std::min(ax, bx) >= x1) return false;
+    if (std::max(ay, by) <= y0 || std::min(ay, by) >= y1) return false;
+    int64_t t[4] = {turn(ax, ay, bx, by, x0, y0), turn(ax, ay, bx, by, x1, y0),
+                    turn(ax, ay, bx, by, x1, y1), turn(ax, ay, bx, by, x0, y1)};
+    bool pos = t[0] >= 0 && t[1] >= 0 && t[2] >= 0 && t[3] >= 0;
+    bool neg = t[0] <= 0 && t[1] <= 0 && t[2] <= 0 && t[3] <= 0;
+    return !(pos || neg);
+}
+
+struct GridI {
+    int64_t ox, oy, h;
+    uint32_t order;
+    int64_t G;
+};
+
+struct Scratch {
+    std::vector<uint64_t> keys;      // (hilbert id << 1) | crossed
+    std::vector<int64_t> ex0, ey0, ex1, ey1;  // edges, oriented upwards (ey0 < ey1)
+    std::vector<uint32_t> row_start, row_edges;
+};
+
+struct PolyLists {
+    std::vector<uint32_t> A, F;  // st,end pairs
+};
+
+// Emits maximal intervals from a stream of increasing [st, end) runs.
+struct RunSink {
+    std::vector<uint32_t> *out;
+    bool open = false;
+    uint64_t st = 0, en = 0;
+    void add(uint64_t a, uint64_t b) {
+        if (open && a == en) {
+            en = b;
+            return;
+        }
+        flush();
+        open = true;
+        st = a;
+        en = b;
+    }
+    void flush() {
+        if (open) {
+            out->push_back((uint32_t)st);
+            out->push_back((uint32_t)en);  // 2^32 wraps to 0 by design
+        }
+        open = false;
+    }
+};
+
+april_status build_one(const int32_t *xy, uint64_t nv, const GridI &g, Scratch &sc, PolyLists &out) {
+    out.A.clear();
+    out.F.clear();
+    if (nv < 3) return fail(APRIL_ERR_GEOMETRY, "polygon with fewer than 3 vertices");
+    const int64_t h = g.h, G = g.G, ox = g.ox, oy = g.oy;
+    int64_t xmn = xy[0], xmx = xy[0], ymn = xy[1], ymx = xy[1];
+    for (uint64_t k = 1; k < nv; ++k) {
+        xmn = std::min<int64_t>(xmn, xy[2 * k]);
+        xmx = std::max<int64_t>(xmx, xy[2 * k]);
+        ymn = std::min<int64_t>(ymn, xy[2 * k + 1]);
+        ymx = std::max<int64_t>(ymx, xy[2 * k + 1]);
+    }
+    // window of cells meeting the MBR
+    int64_t wi0 = std::max<int64_t>(ceil_div(xmn - ox, h) - 1, 0);
+    int64_t wi1 = std::min<int64_t>(floor_div(xmx - ox, h), G - 1);
+    int64_t wj0 = std::max<int64_t>(ceil_div(ymn - oy, h) - 1, 0);
+    int64_t wj1 = std::min<int64_t>(floor_div(ymx - oy, h), G - 1);
+    if (wi0 > wi1 || wj0 > wj1) return fail(APRIL_ERR_GEOMETRY, "polygon outside the grid");
+
+    // edges, upward
+    sc.ex0.resize(nv); sc.ey0.resize(nv); sc.ex1.resize(nv); sc.ey1.resize(nv);
+    for (uint64_t k = 0; k < nv; ++k) {
+        uint64_t kn = (k + 1 == nv) ? 0 : k + 1;
+        int64_t ax = xy[2 * k], ay = xy[2 * k + 1], bx = xy[2 * kn], by = xy[2 * kn + 1];
+        if (ay > by || (ay == by && ax > bx)) {
+            std::swap(ax, bx);
+            std::swap(ay, by);
+        }
+        sc.ex0[k] = ax; sc.ey0[k] = ay; sc.ex1[k] = bx; sc.ey1[k] = by;
+    }
+
+    // 1. touched cells, row by row per edge
+    sc.keys.clear();
+    for (uint64_t k = 0; k < nv; ++k) {
+        const int64_t ax = sc.ex0[k], ay = sc.ey0[k], bx = sc.ex1[k], by = sc.ey1[k];
+        int64_t j0 = std::max<int64_t>(ceil_div(ay - oy, h) - 1, 0);
+        int64_t j1 = std::min<int64_t>(floor_div(by - oy, h), G - 1);
+        const int64_t den = by - ay;  // >= 0
+        for (int64_t j = j0; j <= j1; ++j) {
+            const int64_t Y0 = oy + j * h, Y1 = Y0 + h;
+            int64_t i0, i1;
+            if (den == 0) {
+                // horizontal edge: in this closed strip iff Y0 <= ay <= Y1
+                if (ay < Y0 || ay > Y1) continue;
+                i0 = ceil_div(ax - ox, h) - 1;
+                i1 = floor_div(bx - ox, h);
+            } else {
+                const int64_t ya = std::max(ay, Y0), yb = std::min(by, Y1);
+                if (ya > yb) continue;
+                const int64_t dx = bx - ax;
+                const int64_t n1 = ax * den + (ya - ay) * dx;  // x(ya) * den
+                const int64_t n2 = ax * den + (yb - ay) * dx;  // x(yb) * den
+                const int64_t lo = std::min(n1, n2) - ox * den, hi = std::max(n1, n2) - ox * den;
+                i0 = ceil_div(lo, den * h) - 1;
+                i1 = floor_div(hi, den * h);
+            }
+            i0 = std::max<int64_t>(i0, 0);
+            i1 = std::min<int64_t>(i1, G - 1);
+            for (int64_t i = i0; i <= i1; ++i) {
+                bool crossed = enters_open_square(ax, ay, bx, by, ox + i * h, Y0, h);
+                uint64_t d = hilbert_id(g.order, (uint32_t)i, (uint32_t)j);
+                sc.keys.push_back((d << 1) | (crossed ? 1u : 0u));
+            }
+        }
+    }
+    std::sort(sc.keys.begin(), sc.keys.end());
+
+    // point-in-polygon support: edges bucketed by the rows whose centre line
+    // they straddle ((ey0 <= yc < ey1), the half-open crossing rule)
+    const int64_t nrows = wj1 - wj0 + 1;
+    sc.row_start.assign((size_t)nrows + 1, 0);
+    auto row_span = [&](uint64_t k, int64_t &r0, int64_t &r1) {
+        // rows j with ey0 <= oy + j*h + h/2 < ey1
+        r0 = ceil_div(sc.ey0[k] - oy - h / 2, h);
+        r1 = ceil_div(sc.ey1[k] - oy - h / 2, h) - 1;
+        r0 = std::max(r0, wj0);
+        r1 = std::min(r1, wj1);
+    };
+    for (uint64_t k = 0; k < nv; ++k) {
+        int64_t r0, r1;
+        row_span(k, r0, r1);
+        for (int64_t r = r0; r <= r1; ++r) sc.row_start[(size_t)(r - wj0) + 1]++;
+    }
+    for (int64_t r = 0; r < nrows; ++r) sc.row_start[(size_t)r + 1] += sc.row_start[(size_t)r];
+    sc.row_edges.resize(sc.row_start[(size_t)nrows]);
+    {
+        std::vector<uint32_t> fill(sc.row_start.begin(), sc.row_start.end() - 1);
+        for (uint64_t k = 0; k < nv; ++k) {
+            int64_t r0, r1;
+            row_span(k, r0, r1);
+            for (int64_t r = r0; r <= r1; ++r) sc.row_edges[fill[(size_t)(r - wj0)]++] = (uint32_t)k;
+        }
+    }
+    auto inside = [&](uint32_t i, uint32_t j) -> bool {
+        if ((int64_t)i < wi0 || (int64_t)i > wi1 || (int64_t)j < wj0 || (int64_t)j > wj1) return false;
+        const int64_t xc = ox + (int64_t)i * h + h / 2, yc = oy + (int64_t)j * h + h / 2;
+        const size_t r = (size_t)((int64_t)j - wj0);
+        bool in = false;
+        for (uint32_t e = sc.row_start[r]; e < sc.row_start[r + 1]; ++e) {
+            uint32_t k = sc.row_edges[e];
+            if (turn(sc.ex0[k], sc.ey0[k], sc.ex1[k], sc.ey1[k], xc, yc) > 0) in = !in;
+        }
+        return in;
+    };
+    auto gap_is_full = [&](uint64_t first) -> bool {
+        uint32_t x, y;
+        hilbert_cell(g.order, first, x, y);
+        return inside(x, y);
+    };
+
+    // 2+3. walk touched ids and the gaps between them
+    RunSink A{&out.A}, F{&out.F};
+    const uint64_t ncells = (uint64_t)G * (uint64_t)G;
+    uint64_t next = 0;  // first id not yet classified
+    size_t k = 0;
+    const size_t nk = sc.keys.size();
+    while (k < nk) {
+        const uint64_t d = sc.keys[k] >> 1;
+        bool crossed = false;
+        while (k < nk && (sc.keys[k] >> 1) == d) crossed |= (sc.keys[k++] & 1u) != 0;
+        if (d > next) {  // gap [next, d)
+            if (gap_is_full(next)) {
+                A.add(next, d);
+                F.add(next, d);
+            }
+        }
+        A.add(d, d + 1);
+        if (!crossed) {
+            uint32_t x, y;
+            hilbert_cell(g.order, d, x, y);
+            if (inside(x, y)) F.add(d, d + 1);
+        }
+        next = d + 1;
+    }
+    if (next < ncells && gap_is_full(next)) {
+        A.add(next, ncells);
+        F.add(next, ncells);
+    }
+    A.flush();
+    F.flush();
+    if (out.A.empty()) return fail(APRIL_ERR_GEOMETRY, "polygon meets no cell");
+    return APRIL_OK;
+}
+
+april_status check_grid(const april_grid *grid, GridI &g) {
+    if (!grid) return fail(APRIL_ERR_INVALID_ARG, "grid is NULL");
+    if (grid->order < 1 || grid->order > 16) return fail(APRIL_ERR_INVALID_ARG, "grid order must be 1..16");
+    if (grid->log2_cell < 1 || grid->log2_cell > 30) return fail(APRIL_ERR_INVALID_ARG, "log2_cell must be 1..30");
+    g.ox = grid->ox;
+    g.oy = grid->oy;
+    g.h = (int64_t)1 << grid->log2_cell;
+    g.order = grid->order;
+    g.G = (int64_t)1 << grid->order;
+    // keep every int64 product in the predicates exact
+    const int64_t lim = (int64_t)1 << 26;
+    if (g.ox < -lim || g.ox > lim || g.oy < -lim || g.oy > lim || g.h * g.G > lim)
+        return fail(APRIL_ERR_INVALID_ARG, "grid outside the supported coordinate range");
+    return APRIL_OK;
+}
+
+template <class F>
+void parallel_for(uint64_t n, uint32_t n_threads, uint64_t chunk, F &&fn) {
+    if (n_threads == 0) n_threads = std::max(1u, std::thread::hardware_concurrency());
+    n_threads = (uint32_t)std::min<uint64_t>(n_threads, std::max<uint64_t>(1, (n + chunk - 1) / chunk));
+    std::atomic<uint64_t> next{0};
+    auto worker = [&](uint32_t tid) {
+        for (;;) {
+            uint64_t b = next.fetch_add(chunk);
+            if (b >= n) break;
+            uint64_t e = std::min(n, b + chunk);
+            fn(tid, b, e);
+        }
+    };
+    if (n_threads <= 1) {
+        worker(0);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve(n_threads);
+    for (uint32_t t = 0; t < n_threads; ++t) th.emplace_back(worker, t);
+    for (auto &t : th) t.join();
+}
+
+uint32_t resolve_threads(uint32_t n) {
+    return n ? n : std::max(1u, std::thread::hardware_concurrency());
+}
+
+}  // namespace
+
+}  // namespace april
+
+using namespace april;
+
+extern "C" april_status april_last_error(char *buf, size_t buf_size) {
+    if (!buf || buf_size == 0) return APRIL_ERR_INVALID_ARG;
+    std::snprintf(buf, buf_size, "%s", g_last_error.c_str());
+    return APRIL_OK;
+}
+
+extern "C" april_status april_build_sets(const int32_t *xy, const uint64_t *vert_off, uint32_t n_polys,
+                                         const april_grid *grid, uint32_t n_threads, april_sets **out) {
+    if (!out) return fail(APRIL_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if ((!xy || !vert_off) && n_polys) return fail(APRIL_ERR_INVALID_ARG, "xy/vert_off is NULL");
+    GridI g;
+    april_status st = check_grid(grid, g);
+    if (st) return st;
+    for (uint32_t p = 0; p < n_polys; ++p)
+        if (vert_off[p + 1] < vert_off[p]) return fail(APRIL_ERR_INVALID_ARG, "vert_off is not monotone");
+    try {
+        std::vector<PolyLists> lists(n_polys);
+        uint32_t nt = resolve_threads(n_threads);
+        std::vector<Scratch> scratch(nt);
+        std::atomic<int> err{0};
+        std::vector<std::string> errmsg(nt);
+        parallel_for(n_polys, nt, 64, [&](uint32_t tid, uint64_t b, uint64_t e) {
+            for (uint64_t p = b; p < e && !err.load(std::memory_order_relaxed); ++p) {
+                april_status s = build_one(xy + 2 * vert_off[p], vert_off[p + 1] - vert_off[p], g, scratch[tid],
+                                           lists[p]);
+                if (s) {
+                    char m[160];
+                    std::snprintf(m, sizeof m, "polygon %llu: ", (unsigned long long)p);
+                    errmsg[tid] = std::string(m) + g_last_error;
+                    int zero = 0;
+                    err.compare_exchange_strong(zero, s);
+                }
+            }
+        });
+        if (err.load()) {
+            for (auto &m : errmsg)
+                if (!m.empty()) return fail(err.load(), m);
+            return fail(err.load(), "construction failed");
+        }
+        auto *S = new april_sets();
+        S->n = n_polys;
+        S->order = g.order;
+        S->desc.resize((size_t)n_polys * 4);
+        uint64_t slot = 0;
+        for (uint32_t p = 0; p < n_polys; ++p) {
+            uint64_t na = lists[p].A.size() / 2, nf = lists[p].F.size() / 2;
+            S->desc[4 * (size_t)p + 0] = (uint32_t)slot;
+            S->desc[4 * (size_t)p + 1] = (uint32_t)na;
+            slot += (na + 1) & ~1ull;  // next list starts 16-byte aligned
+            S->desc[4 * (size_t)p + 2] = (uint32_t)slot;
+            S->desc[4 * (size_t)p + 3] = (uint32_t)nf;
+            slot += (nf + 1) & ~1ull;
+            S->a_total += na;
+            S->f_total += nf;
+            if (slot > 0xFFFFFFF0ull) {
+                delete S;
+                return fail(APRIL_ERR_INVALID_ARG, "more than 2^32 interval slots in one set");
+            }
+        }
+        S->iv.assign((size_t)slot * 2, 0u);
+        parallel_for(n_polys, nt, 256, [&](uint32_t, uint64_t b, uint64_t e) {
+            for (uint64_t p = b; p < e; ++p) {
+                const auto &L = lists[p];
+                if (!L.A.empty())
+                    std::memcpy(&S->iv[2 * (size_t)S->desc[4 * p + 0]], L.A.data(), L.A.size() * 4);
+                if (!L.F.empty())
+                    std::memcpy(&S->iv[2 * (size_t)S->desc[4 * p + 2]], L.F.data(), L.F.size() * 4);
+            }
+        });
+        *out = S;
+        return APRIL_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(APRIL_ERR_NO_MEMORY, "host allocation failed while building sets");
+    }
+}
+
+extern "C" void april_sets_destroy(april_sets *sets) { delete sets; }
+
+extern "C" april_status april_sets_get_info(const april_sets *S, april_sets_info *info) {
+    if (!S || !info) return fail(APRIL_ERR_INVALID_ARG, "NULL argument");
+    info->n_objects = S->n;
+    info->order = S->order;
+    info->a_intervals = S->a_total;
+    info->f_intervals = S->f_total;
+    info->iv_slots = S->iv.size() / 2;
+    info->device_bytes = april_desc_bytes(S->n) + (uint64_t)S->iv.size() * 4;
+    return APRIL_OK;
+}
+
+extern "C" april_status april_sets_list(const april_sets *S, uint32_t obj, int which, const uint32_t **iv,
+                                        uint32_t *n) {
+    if (!S || !iv || !n || (which != 0 && which != 1)) return fail(APRIL_ERR_INVALID_ARG, "bad argument");
+    if (obj >= S->n) return fail(APRIL_ERR_OUT_OF_RANGE_ID, "object id out of range");
+    uint32_t off = S->desc[4 * (size_t)obj + 2 * which], len = S->desc[4 * (size_t)obj + 2 * which + 1];
+    *iv = S->iv.data() + 2 * (size_t)off;
+    *n = len;
+    return APRIL_OK;
+}
+
+namespace {
+
+// IntervalJoin of Algorithm 2 with early exit.  Intervals are [st, end) with
+// end stored mod 2^32, so comparisons use last = end - 1.  *used receives the
+// number of intervals read on both sides.
+bool host_join(const uint32_t *X, uint32_t nx, const uint32_t *Y, uint32_t ny, uint64_t *used) {
+    uint32_t i = 0, j = 0;
+    while (i < nx && j < ny) {
+        uint32_t xs = X[2 * i], xl = X[2 * i + 1] - 1u, ys = Y[2 * j], yl = Y[2 * j + 1] - 1u;
+        if (xs <= yl && ys <= xl) {
+            *used += (uint64_t)i + 1 + j + 1;
+            return true;
+        }
+        if (xl <= yl) ++i;
+        else ++j;
+    }
+    *used += (uint64_t)std::min(i + 1, nx) + std::min(j + 1, ny);
+    return false;
+}
+
+}  // namespace
+
+extern "C" april_status april_host_filter(const april_sets *R, const april_sets *S, const uint32_t *pr,
+                                          const uint32_t *ps, uint64_t n, uint32_t n_threads, uint8_t *verdict,
+                                          uint64_t *consumed) {
+    if (!R || !S || (n && (!pr || !ps || !verdict))) return fail(APRIL_ERR_INVALID_ARG, "NULL argument");
+    parallel_for(n, resolve_threads(n_threads), 4096, [&](uint32_t, uint64_t b, uint64_t e) {
+        for (uint64_t k = b; k < e; ++k) {
+            uint32_t r = pr[k], s = ps[k];
+            uint64_t used = 0;
+            uint8_t v;
+            if (r >= R->n || s >= S->n) {
+                v = APRIL_VERDICT_ERROR;
+            } else {
+                const uint32_t *dr = &R->desc[4 * (size_t)r], *ds = &S->desc[4 * (size_t)s];
+                const uint32_t *Ar = &R->iv[2 * (size_t)dr[0]], *Fr = &R->iv[2 * (size_t)dr[2]];
+                const uint32_t *As = &S->iv[2 * (size_t)ds[0]], *Fs = &S->iv[2 * (size_t)ds[2]];
+                if (!host_join(Ar, dr[1], As, ds[1], &used)) v = APRIL_TRUE_NEGATIVE;
+                else if (host_join(Ar, dr[1], Fs, ds[3], &used)) v = APRIL_TRUE_HIT;
+                else if (host_join(Fr, dr[3], As, ds[1], &used)) v = APRIL_TRUE_HIT;
+                else v = APRIL_INCONCLUSIVE;
+            }
+            verdict[k] = v;
+            if (consumed) consumed[k] = used;
+        }
+    });
+    return APRIL_OK;
+}

@@ -23,6 +23,8 @@ distributions are unchanged.
 """
 from __future__ import annotations
 
+import os
+import tempfile
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -32,7 +34,7 @@ from .mbrjoin import mbr_join
 
 HOTSPOT_FRAC = 0.05
 HOTSPOTS = 32
-HOTSPOT_SIGMA = 1.5e-3
+HOTSPOT_SIGMA = 2.5e-4  # tuned so that the full config-2 join yields 2-5M candidates
 RADIUS_CAP_SKEWED = 0.02
 PARETO_ALPHA = 1.3
 PARETO_XM = 2e-4 / 2 ** (1 / 1.3)
@@ -110,7 +112,44 @@ def _hot(seed):
     return 0.1 + 0.8 * _rng(seed, 1000).random((HOTSPOTS, 2))
 
 
-def make(cfg: int, scale: float = 1.0, max_pairs: int | None = None) -> Workload:
+RECIPE_VERSION = 2
+
+
+def _cache_path(cfg, scale, max_pairs):
+    d = os.environ.get("APRIL_SYNTH_CACHE", os.path.join(tempfile.gettempdir(), "april_synth_cache"))
+    return os.path.join(d, f"cfg{cfg}_s{scale:g}_m{max_pairs}_v{RECIPE_VERSION}.npz")
+
+
+def make(cfg: int, scale: float = 1.0, max_pairs: int | None = None, cache: bool = True) -> Workload:
+    """Build (or load from the on-disk cache) workload `cfg` at `scale`."""
+    use_cache = cache and scale >= 0.05
+    if use_cache:
+        path = _cache_path(cfg, scale, max_pairs)
+        if os.path.exists(path):
+            try:
+                z = np.load(path)
+                R = PolySet(z["rxy"].astype(np.int64), z["roff"], z["rmbr"])
+                S = PolySet(z["sxy"].astype(np.int64), z["soff"], z["smbr"])
+                return Workload(name=str(z["name"]), order=int(z["order"]), R=R, S=S, pr=z["pr"], ps=z["ps"],
+                                partitions=int(z["parts"]), meta=dict(zip(z["mk"].tolist(), z["mv"].tolist())))
+            except Exception:
+                pass
+    w = _make(cfg, scale, max_pairs)
+    if use_cache:
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            tmp = path + f".tmp{os.getpid()}.npz"
+            np.savez(tmp, rxy=w.R.xy.astype(np.int32), roff=w.R.off, rmbr=w.R.mbr,
+                     sxy=w.S.xy.astype(np.int32), soff=w.S.off, smbr=w.S.mbr, pr=w.pr, ps=w.ps,
+                     name=w.name, order=w.order, parts=w.partitions,
+                     mk=np.array(list(w.meta.keys())), mv=np.array(list(w.meta.values())))
+            os.replace(tmp, path)
+        except OSError:
+            pass
+    return w
+
+
+def _make(cfg: int, scale: float, max_pairs: int | None) -> Workload:
     seed = cfg - 1
     if cfg == 1:
         n = max(int(round(1000 * scale)), 2)

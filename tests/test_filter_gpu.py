@@ -1,0 +1,133 @@
+"""Parity of the CUDA filter with the oracle, through the C ABI (GPU only).
+
+Verdicts are integers, so the bar is bit-exact equality with the oracle's
+cell-set verdicts.  Sizes: config 1 in full; configs 2 and 3 at reduced
+polygon counts (lists span many 32-interval windows and end in ragged
+tails); config 2 at full size in the benchmark's launch configuration,
+checked on a seeded sample of pairs the oracle computes one by one; and edge
+cases (no pairs, one pair, out-of-range ids, the last Hilbert cell)."""
+import numpy as np
+import pytest
+
+import oracle
+from tests import _data
+from paper_2307_01716_gb300 import april as A
+
+pytestmark = pytest.mark.gpu
+
+MODES = ["plain", "warp"]
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def ctx(torch_cuda):
+    return A.Context(0)
+
+
+def _device_sets(w):
+    g = A.global_grid(w.order)
+    R = A.april_build_sets(w.R.xy, w.R.off, g)
+    S = A.april_build_sets(w.S.xy, w.S.off, g)
+    return R, S, A.april_upload(R), A.april_upload(S)
+
+
+def run_filter(torch, ctx, dR, dS, pr, ps, mode):
+    n = len(pr)
+    d_r = torch.from_numpy(np.ascontiguousarray(pr, dtype=np.uint32).view(np.int32)).cuda()
+    d_s = torch.from_numpy(np.ascontiguousarray(ps, dtype=np.uint32).view(np.int32)).cuda()
+    out = torch.full((max(n, 1),), 0xEE, dtype=torch.uint8, device="cuda")
+    m = A.MODES[mode]
+    sb = ctx.scratch_bytes(m, n)
+    scratch = torch.empty(max(sb, 256), dtype=torch.uint8, device="cuda") if sb else None
+    ctx.april_filter_pairs(dR, dS, d_r, d_s, n, out, m, scratch)
+    ctx.april_sync_status()
+    return out[:n].cpu().numpy()
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_config1_all_pairs(torch_cuda, ctx, mode):
+    w = _data.workload(1, 1.0)
+    _, _, dR, dS = _device_sets(w)
+    got = run_filter(torch_cuda, ctx, dR, dS, w.pr, w.ps, mode)
+    want = _data.oracle_verdicts(1, 1.0)
+    assert np.array_equal(got, want), np.nonzero(got != want)[0][:10]
+
+
+@pytest.mark.parametrize("cfg,scale", [(2, 0.01), (3, 0.01)])
+@pytest.mark.parametrize("mode", MODES)
+def test_reduced_configs(torch_cuda, ctx, cfg, scale, mode):
+    w = _data.workload(cfg, scale)
+    _, _, dR, dS = _device_sets(w)
+    got = run_filter(torch_cuda, ctx, dR, dS, w.pr, w.ps, mode)
+    want = _data.oracle_verdicts(cfg, scale)
+    assert len(want) > 200
+    assert np.array_equal(got, want), np.nonzero(got != want)[0][:10]
+
+
+def _rect(x0, y0, x1, y1):
+    return np.array([[x0, y0], [x1, y0], [x1, y1], [x0, y1]], dtype=np.int64)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_edge_cases(torch_cuda, ctx, mode):
+    order = 16
+    h = 1 << (24 - order)
+    L = 1 << 24
+    polys = [_rect(L - 3 * h, 0, L, 3 * h), _rect(L - h, 0, L, h), _rect(0, 0, 2 * h, 2 * h),
+             _rect(10 * h, 10 * h, 20 * h, 30 * h), _rect(19 * h, 29 * h, 40 * h, 40 * h)]
+    xy = np.concatenate(polys)
+    off = np.zeros(len(polys) + 1, dtype=np.int64)
+    off[1:] = np.cumsum([len(p) for p in polys])
+    S = A.april_build_sets(xy, off, A.global_grid(order))
+    dS = A.april_upload(S)
+    n = len(polys)
+    pr, ps = np.meshgrid(np.arange(n, dtype=np.uint32), np.arange(n, dtype=np.uint32), indexing="ij")
+    pr, ps = pr.ravel(), ps.ravel()
+    got = run_filter(torch_cuda, ctx, dS, dS, pr, ps, mode)
+    assert np.array_equal(got, oracle.verdicts(xy, off, xy, off, pr, ps, oracle.Grid(order)))
+    # one pair
+    got = run_filter(torch_cuda, ctx, dS, dS, pr[1:2], ps[1:2], mode)
+    assert got.tolist() == [1]
+    # no pairs: a no-op
+    assert run_filter(torch_cuda, ctx, dS, dS, pr[:0], ps[:0], mode).size == 0
+    # out-of-range ids: error verdict and an OUT_OF_RANGE_ID status
+    bad_r = np.array([0, 7, 1], dtype=np.uint32)
+    bad_s = np.array([0, 0, 99], dtype=np.uint32)
+    import torch
+    d_r = torch.from_numpy(bad_r.view(np.int32)).cuda()
+    d_s = torch.from_numpy(bad_s.view(np.int32)).cuda()
+    out = torch.zeros(3, dtype=torch.uint8, device="cuda")
+    m = A.MODES[mode]
+    sb = ctx.scratch_bytes(m, 3)
+    scratch = torch.empty(max(sb, 256), dtype=torch.uint8, device="cuda") if sb else None
+    ctx.april_filter_pairs(dS, dS, d_r, d_s, 3, out, m, scratch)
+    with pytest.raises(A.AprilError) as e:
+        ctx.april_sync_status()
+    assert e.value.status == -2
+    assert out.cpu().tolist() == [1, 0xFF, 0xFF]
+    ctx.april_sync_status()  # the status was cleared
+
+
+@pytest.fixture(scope="module")
+def full_config2(torch_cuda):
+    w = _data.workload(2, 1.0)
+    return (w,) + _device_sets(w)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_full_size_config2_sampled(torch_cuda, ctx, full_config2, mode):
+    w, R, S, dR, dS = full_config2
+    got = run_filter(torch_cuda, ctx, dR, dS, w.pr, w.ps, mode)
+    rng = np.random.default_rng(77)
+    idx = np.sort(rng.choice(len(w.pr), 1500, replace=False))
+    assert np.array_equal(got[idx], _data.oracle_sample(w, idx))
+    # every verdict agrees with the host execution of Algorithm 2 on the same lists
+    hv, _ = A.april_host_filter(R, S, w.pr, w.ps)
+    assert np.array_equal(got, hv)
