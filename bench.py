@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--mode", default="batched", choices=["batched", "warp", "plain"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default tuning (profiling runs)")
     return ap.parse_args()
 
 
@@ -244,15 +245,18 @@ def main():
         return [a.elapsed_time(b) for a, b in evs]
 
     mode = args.mode
-    try:
-        ctx.scratch_bytes(A.MODES[mode], n)
-    except A.AprilError:
-        mode = "warp"
+    tune = None
+    if mode == "batched" and not args.no_autotune:
+        # the project's autotuner picks the CTA threshold and first warp window
+        m = A.MODE_BATCHED
+        scratch = torch.empty(ctx.scratch_bytes(m, n), dtype=torch.uint8, device=dev)
+        tune = ctx.april_autotune(dR, dS, d_r, d_s, n, out, scratch, stream).as_dict()
+        del scratch
     clocks = Clocks()
     clocks.start()
     t_main = time_mode(mode, args.steps, args.warmup)
-    clk = clocks.stop(local)
     t_plain = time_mode("plain", max(3, args.steps // 2), args.warmup) if mode != "plain" else t_main
+    t_warp = time_mode("warp", args.steps, args.warmup) if mode == "batched" else None
 
     ms = statistics.mean(t_main)
     ms_t = torch.tensor([ms], device=dev)
@@ -278,15 +282,16 @@ def main():
         t0 = time.perf_counter()
         ctx.april_filter_pairs_host(dR, dS, h_r, h_s, n, h_v, m, work, stream)
         e2e_t.append(time.perf_counter() - t0)
+    clk = clocks.stop(local)
     if not np.array_equal(h_v.numpy(), host_v):
         raise SystemExit("end-to-end verdicts differ")
     e2e_s = statistics.mean(e2e_t)
 
     peak, peak_kind = peaks()
     achieved = b_alg / (ms * 1e-3) / 1e9
-    kernel_name = {"plain": "k_plain", "warp": "k_warp", "batched": "k_batched"}[mode]
+    kernel_name = {"plain": "k_plain", "warp": "k_warp", "batched": "k_persistent"}[mode]
     traffic = kernel_traffic(kernel_name, w.name)
-    launches = {"plain": 1, "warp": 1, "batched": 1}[mode]
+    launches = {"plain": 1, "warp": 1, "batched": 2}[mode]  # batched: binning + persistent kernel
 
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
@@ -297,6 +302,8 @@ def main():
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "plain": {"pairs_per_s": n / (plain_ms * 1e-3), "ms_per_step": plain_ms,
                   "speedup_of_mode": plain_ms / ms},
+        "warp": None if t_warp is None else {"pairs_per_s": n / (statistics.mean(t_warp) * 1e-3),
+                                             "ms_per_step": statistics.mean(t_warp)},
         "useful_GBps": achieved,
         "algorithmic_bytes_per_step": b_alg,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -305,6 +312,7 @@ def main():
         "e2e": {"value": n / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": n},
         "gpu_launches": launches * args.steps,
         "clocks": clk,
+        "tune": tune,
         "verdict_mix": (np.bincount(host_v, minlength=3)[:3] / n).round(4).tolist(),
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -157,10 +157,38 @@ typedef struct april_ctx april_ctx;
 april_status april_ctx_create(int device, april_ctx **out);
 void april_ctx_destroy(april_ctx *ctx);
 
+/* ------------------------------------------------------------------ tuning */
+
+/* Knobs of APRIL_MODE_BATCHED (a build-side addition; the paper's CPU
+ * filter has none).  Defaults: {8192, 8, 16, 256, 0}. */
+typedef struct april_tune {
+    uint32_t cta_threshold;  /* pairs with |A(r)| + |A(s)| above this are joined by a whole CTA */
+    uint32_t group_lanes;    /* lanes that share one pair below the threshold: 4, 8, 16 or 32 */
+    uint32_t group_window;   /* first window of such a join, intervals per list: a power of two
+                                in [group_lanes, 8 * group_lanes]; later windows double */
+    uint32_t cta_window;     /* first window of a CTA join: 256..2048, power of 2 */
+    uint32_t blocks_per_sm;  /* persistent grid: CTAs per SM (0 = as many as fit) */
+    float ms;                /* output of april_autotune: best time of the sample (ms) */
+} april_tune;
+
+april_status april_set_tune(april_ctx *ctx, const april_tune *tune);
+april_status april_get_tune(const april_ctx *ctx, april_tune *tune);
+
+/* Times APRIL_MODE_BATCHED on the given pairs (typically a sample of the
+ * workload) for a grid of candidate tunings, keeps the
+ * fastest in the context, and returns it in *out (candidates: cta_threshold in
+ * {2048, 4096, 8192, 16384, none} x (group_lanes, group_window) in
+ * {(4,8), (4,16), (8,16), (8,32), (16,32), (16,64), (32,64)}).  Arguments as for
+ * april_filter_pairs; synchronizes `stream`. */
+april_status april_autotune(april_ctx *ctx, const april_dev_sets *R, const april_dev_sets *S,
+                            const uint32_t *d_r, const uint32_t *d_s, uint64_t n, uint8_t *d_verdict,
+                            void *d_scratch, size_t scratch_bytes, void *stream, april_tune *out);
+
 /* ------------------------------------------------------------------ filter */
 
 /* Device scratch (bytes) april_filter_pairs needs for `mode` and n pairs.
- * PLAIN and WARP need none. */
+ * PLAIN and WARP need none; BATCHED needs 256 bytes of work counters plus
+ * 4 bytes per pair for the list of long pairs. */
 april_status april_filter_scratch_bytes(int mode, uint64_t n, size_t *bytes);
 
 /* Runs the APRIL intermediate filter (Algorithm 2) on n candidate pairs.
@@ -174,6 +202,12 @@ april_status april_filter_scratch_bytes(int mode, uint64_t n, size_t *bytes);
  *   d_scratch  device scratch of april_filter_scratch_bytes() bytes
  *              (256-byte aligned), or NULL when that is 0.
  *   stream     cudaStream_t (void*); all work is enqueued on it.
+ *
+ * APRIL_MODE_BATCHED enqueues a CUDA graph (counter reset, length binning,
+ * persistent filter) that is captured on first use of an argument set and
+ * replayed afterwards; the context's tuning (april_set_tune /
+ * april_autotune) applies.  Calls on one context must not overlap in time
+ * from several host threads.
  *
  * Asynchronous: launch errors are returned at once; device-side errors (an
  * out-of-range id, an exhausted bounded wait) are recorded in the context and

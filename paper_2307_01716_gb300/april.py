@@ -44,6 +44,15 @@ class april_sets_info(ctypes.Structure):
                 ("iv_slots", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64)]
 
 
+class april_tune(ctypes.Structure):
+    _fields_ = [("cta_threshold", ctypes.c_uint32), ("group_lanes", ctypes.c_uint32),
+                ("group_window", ctypes.c_uint32), ("cta_window", ctypes.c_uint32),
+                ("blocks_per_sm", ctypes.c_uint32), ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class april_dev_sets(ctypes.Structure):
     _fields_ = [("desc", ctypes.c_void_p), ("iv", ctypes.c_void_p), ("n_objects", ctypes.c_uint32),
                 ("order", ctypes.c_uint32), ("iv_slots", ctypes.c_uint64)]
@@ -73,6 +82,10 @@ SIGNATURES = {
     "april_filter_pairs_host": (_st, [_vp, ctypes.POINTER(april_dev_sets), ctypes.POINTER(april_dev_sets), _vp, _vp,
                                       _u64, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
     "april_host_filter": (_st, [_vp, _vp, _vp, _vp, _u64, _u32, _vp, _vp]),
+    "april_set_tune": (_st, [_vp, ctypes.POINTER(april_tune)]),
+    "april_get_tune": (_st, [_vp, ctypes.POINTER(april_tune)]),
+    "april_autotune": (_st, [_vp, ctypes.POINTER(april_dev_sets), ctypes.POINTER(april_dev_sets), _vp, _vp, _u64,
+                             _vp, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(april_tune)]),
 }
 
 _lib = None
@@ -208,6 +221,23 @@ class Context:
         sb = 0 if scratch is None else int(scratch.numel() * scratch.element_size())
         check(load().april_filter_pairs(self.handle, ctypes.byref(R.c), ctypes.byref(S.c), _ptr(d_r), _ptr(d_s),
                                         n, _ptr(d_verdict), mode, _ptr(scratch), sb, st.cuda_stream))
+
+    def get_tune(self) -> april_tune:
+        t = april_tune()
+        check(load().april_get_tune(self.handle, ctypes.byref(t)))
+        return t
+
+    def set_tune(self, t: april_tune) -> None:
+        check(load().april_set_tune(self.handle, ctypes.byref(t)))
+
+    def april_autotune(self, R: DevSets, S: DevSets, d_r, d_s, n: int, d_verdict, scratch, stream=None) -> april_tune:
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream()
+        t = april_tune()
+        check(load().april_autotune(self.handle, ctypes.byref(R.c), ctypes.byref(S.c), _ptr(d_r), _ptr(d_s), n,
+                                    _ptr(d_verdict), _ptr(scratch), int(scratch.numel()), st.cuda_stream,
+                                    ctypes.byref(t)))
+        return t
 
     def host_work_bytes(self, mode: int, n: int) -> int:
         b = ctypes.c_size_t()

@@ -26,47 +26,39 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <string>
+#include <vector>
 
 #include "april_internal.h"
+#include "join_device.cuh"
+
+using namespace april_dev;
 
 namespace {
-
-constexpr unsigned FULL = 0xffffffffu;
-
-struct DevSet {
-    const uint4 *desc;  // {a_off, a_len, f_off, f_len}
-    const uint2 *iv;    // {st, end}
-    uint32_t n;
-};
 
 // status bits in the context's device status block
 constexpr uint32_t ST_BAD_ID = 1u;
 constexpr uint32_t ST_TIMEOUT = 2u;
 
-__device__ __forceinline__ uint2 ld_iv(const uint2 *p) { return __ldg(p); }
+constexpr uint32_t kBlock = 256;                 // threads per CTA for K1/K3
+constexpr uint32_t kWarpsPerBlock = kBlock / 32;
+constexpr uint32_t kWarpWMax = 256;              // largest warp window per list
+constexpr uint32_t kCtaWMax = 2048;              // largest CTA window per list
+constexpr uint32_t kWarpFirstWindow = 64;        // first window of a join in APRIL_MODE_WARP
+constexpr uint32_t kWarpBuf = kWarpWMax + 2;     // staging buffer per list (odd start + rounding)
+constexpr uint32_t kCtaBuf = kCtaWMax + 2;
+constexpr uint32_t kWarpShare = 544;             // intervals of shared staging per warp (all group sizes fit)
+constexpr uint32_t kSharedIv = kWarpsPerBlock * kWarpShare;  // one buffer serves both phases
+static_assert(2 * kCtaBuf <= kSharedIv, "CTA windows must fit in the warps' buffers");
+static_assert(kWarpBuf % 2 == 0 && kCtaBuf % 2 == 0, "buffers must stay 16-byte aligned");
+
+// scratch of the batched mode: counters, then the list of long pairs
+constexpr uint32_t C_BIG_COUNT = 0, C_BIG_HEAD = 1, C_CHUNK_HEAD = 2;
+constexpr size_t kCounterBytes = 256;
 
 // ------------------------------------------------------- K0: thread/pair
-// IntervalJoin of Algorithm 2 as written: one thread walks both lists.
-__device__ __forceinline__ bool seq_join(const uint2 *__restrict__ X, uint32_t nx, const uint2 *__restrict__ Y,
-                                         uint32_t ny) {
-    uint32_t i = 0, j = 0;
-    if (nx == 0 || ny == 0) return false;
-    uint2 x = ld_iv(X), y = ld_iv(Y);
-    for (;;) {
-        const uint32_t xl = x.y - 1u, yl = y.y - 1u;
-        if (x.x <= yl && y.x <= xl) return true;
-        if (xl <= yl) {
-            if (++i == nx) return false;
-            x = ld_iv(X + i);
-        } else {
-            if (++j == ny) return false;
-            y = ld_iv(Y + j);
-        }
-    }
-}
-
 __global__ void __launch_bounds__(256) k_plain(DevSet R, DevSet S, const uint32_t *__restrict__ pr,
                                                const uint32_t *__restrict__ ps, uint64_t n,
                                                uint8_t *__restrict__ out, uint32_t *status) {
@@ -88,71 +80,307 @@ __global__ void __launch_bounds__(256) k_plain(DevSet R, DevSet S, const uint32_
     }
 }
 
-// -------------------------------------------------------- K1: warp/pair
-// Number of elements among the first `cnt` lanes' values `v` (sorted
-// ascending across lanes) that are < key (strict) or <= key (!strict).
-template <bool kStrict>
-__device__ __forceinline__ uint32_t warp_rank(uint32_t v, uint32_t cnt, uint32_t key) {
-    uint32_t r = 0;
-#pragma unroll
-    for (uint32_t step = 16; step >= 1; step >>= 1) {
-        const uint32_t probe = r + step - 1;
-        const uint32_t pv = __shfl_sync(FULL, v, probe);
-        const bool below = kStrict ? (pv < key) : (pv <= key);
-        if (probe < cnt && below) r += step;
-    }
-    const uint32_t v31 = __shfl_sync(FULL, v, 31);
-    const bool below31 = kStrict ? (v31 < key) : (v31 <= key);
-    if (r == 31 && cnt == 32 && below31) r = 32;
-    return r;
+// Algorithm 2 for one pair by one warp.
+__device__ __forceinline__ uint8_t warp_verdict(const DevSet &R, const DevSet &S, const uint4 &dr, const uint4 &ds,
+                                                uint2 *xs, uint2 *ys, uint32_t lane, uint32_t w0) {
+    if (!tile_join<WarpScope, 32, kWarpWMax>(R.iv + dr.x, dr.y, S.iv + ds.x, ds.y, xs, ys, nullptr, lane, w0))
+        return APRIL_TRUE_NEGATIVE;
+    if (tile_join<WarpScope, 32, kWarpWMax>(R.iv + dr.x, dr.y, S.iv + ds.z, ds.w, xs, ys, nullptr, lane, w0))
+        return APRIL_TRUE_HIT;
+    if (tile_join<WarpScope, 32, kWarpWMax>(R.iv + dr.z, dr.w, S.iv + ds.x, ds.y, xs, ys, nullptr, lane, w0))
+        return APRIL_TRUE_HIT;
+    return APRIL_INCONCLUSIVE;
 }
 
-// Any overlap between X[0..n) and Y[0..m), one full warp, window of 32.
-__device__ __noinline__ bool warp_join(const uint2 *__restrict__ X, uint32_t n, const uint2 *__restrict__ Y,
-                                       uint32_t m, uint32_t lane) {
-    uint32_t i0 = 0, j0 = 0;
-    while (i0 < n && j0 < m) {
-        const uint32_t nx = min(32u, n - i0), ny = min(32u, m - j0);
-        uint2 x = make_uint2(0u, 0u), y = make_uint2(0u, 0u);
-        if (lane < nx) x = ld_iv(X + i0 + lane);
-        if (lane < ny) y = ld_iv(Y + j0 + lane);
-        const uint32_t xl = x.y - 1u, yl = y.y - 1u;
-        // X side: X_lane is emitted against Y_r
-        const uint32_t r = warp_rank<true>(yl, ny, xl);
-        const uint32_t ys = __shfl_sync(FULL, y.x, r & 31u), ylr = __shfl_sync(FULL, yl, r & 31u);
-        bool hit = lane < nx && r < ny && ys <= xl && x.x <= ylr;
-        // Y side: Y_lane is emitted against X_q
-        const uint32_t q = warp_rank<false>(xl, nx, yl);
-        const uint32_t xs = __shfl_sync(FULL, x.x, q & 31u), xlq = __shfl_sync(FULL, xl, q & 31u);
-        hit |= lane < ny && q < nx && xs <= yl && y.x <= xlq;
-        if (__any_sync(FULL, hit)) return true;
-        i0 += __popc(__ballot_sync(FULL, lane < nx && lane + r < 32u));
-        j0 += __popc(__ballot_sync(FULL, lane < ny && lane + q < 32u));
-    }
-    return false;
+// Algorithm 2 for one pair by the whole CTA.
+__device__ __forceinline__ uint8_t cta_verdict(const DevSet &R, const DevSet &S, const uint4 &dr, const uint4 &ds,
+                                               uint2 *xs, uint2 *ys, uint32_t *slot, uint32_t tid, uint32_t w0) {
+    if (!tile_join<CtaScope, kBlock, kCtaWMax>(R.iv + dr.x, dr.y, S.iv + ds.x, ds.y, xs, ys, slot, tid, w0))
+        return APRIL_TRUE_NEGATIVE;
+    if (tile_join<CtaScope, kBlock, kCtaWMax>(R.iv + dr.x, dr.y, S.iv + ds.z, ds.w, xs, ys, slot, tid, w0))
+        return APRIL_TRUE_HIT;
+    if (tile_join<CtaScope, kBlock, kCtaWMax>(R.iv + dr.z, dr.w, S.iv + ds.x, ds.y, xs, ys, slot, tid, w0))
+        return APRIL_TRUE_HIT;
+    return APRIL_INCONCLUSIVE;
 }
 
-__global__ void __launch_bounds__(256) k_warp(DevSet R, DevSet S, const uint32_t *__restrict__ pr,
-                                              const uint32_t *__restrict__ ps, uint64_t n,
-                                              uint8_t *__restrict__ out, uint32_t *status) {
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-    for (uint64_t k = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < n; k += warps) {
+__device__ __forceinline__ uint4 shfl4(const uint4 &v, uint32_t src) {
+    return make_uint4(__shfl_sync(kFull, v.x, src), __shfl_sync(kFull, v.y, src), __shfl_sync(kFull, v.z, src),
+                      __shfl_sync(kFull, v.w, src));
+}
+
+// One warp filters the 32 pairs starting at `base`: every lane fetches the
+// ids and descriptors of its own pair at once (coalesced ids, 32 descriptor
+// gathers in flight), then the warp joins the pairs one after another.  Pairs
+// whose cost |A(r)| + |A(s)| exceeds cta_threshold are left to the CTA phase
+// (pass UINT32_MAX to take every pair).
+__device__ __forceinline__ void warp_chunk(const DevSet &R, const DevSet &S, const uint32_t *__restrict__ pr,
+                                           const uint32_t *__restrict__ ps, uint64_t n, uint64_t base,
+                                           uint8_t *__restrict__ out, uint32_t *status, uint2 *xs, uint2 *ys,
+                                           uint32_t lane, uint32_t w0, uint32_t cta_threshold, bool flag_bad) {
+    const uint64_t k = base + lane;
+    uint4 dr = make_uint4(0, 0, 0, 0), ds = make_uint4(0, 0, 0, 0);
+    bool take = false;
+    if (k < n) {
         const uint32_t r = __ldg(pr + k), s = __ldg(ps + k);
-        if (r >= R.n || s >= S.n) {
-            if (lane == 0) {
+        if (r < R.n && s < S.n) {
+            dr = __ldg(R.desc + r);
+            ds = __ldg(S.desc + s);
+            take = (uint64_t)dr.y + ds.y <= (uint64_t)cta_threshold;
+        } else if (flag_bad) {
+            out[k] = APRIL_VERDICT_ERROR;
+            atomicOr(status, ST_BAD_ID);
+        }
+    }
+    uint32_t todo = __ballot_sync(kFull, take);
+    uint8_t mine = 0;
+    while (todo) {
+        const uint32_t t = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const uint4 a = shfl4(dr, t), b = shfl4(ds, t);
+        const uint8_t v = warp_verdict(R, S, a, b, xs, ys, lane, w0);
+        if (lane == t) mine = v;
+    }
+    if (take) out[k] = mine;
+}
+
+// ------------------------------------------------------- K1: warp/pair
+__global__ void __launch_bounds__(kBlock) k_warp(DevSet R, DevSet S, const uint32_t *__restrict__ pr,
+                                                 const uint32_t *__restrict__ ps, uint64_t n,
+                                                 uint8_t *__restrict__ out, uint32_t *status, uint32_t w0) {
+    __shared__ __align__(16) uint2 sm[kWarpsPerBlock][2][kWarpBuf];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint64_t stride = (uint64_t)gridDim.x * kWarpsPerBlock * 32;
+    for (uint64_t base = ((uint64_t)blockIdx.x * kWarpsPerBlock + warp) * 32; base < n; base += stride)
+        warp_chunk(R, S, pr, ps, n, base, out, status, sm[warp][0], sm[warp][1], lane, w0, 0xffffffffu, true);
+}
+
+// --------------------------------------------- K4: length binning (batched)
+// Validates ids (error verdicts), and appends every pair whose cost
+// |A(r)| + |A(s)| exceeds the threshold to the long-pair list (warp-
+// aggregated atomics).
+__global__ void __launch_bounds__(256) k_bin(DevSet R, DevSet S, const uint32_t *__restrict__ pr,
+                                             const uint32_t *__restrict__ ps, uint64_t n, uint8_t *__restrict__ out,
+                                             uint32_t *status, uint32_t cta_threshold, uint32_t *big_list,
+                                             uint32_t *counters) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t kb = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); kb < n; kb += stride) {
+        const uint64_t k = kb + lane;
+        bool big = false;
+        if (k < n) {
+            const uint32_t r = __ldg(pr + k), s = __ldg(ps + k);
+            if (r < R.n && s < S.n) {
+                big = (uint64_t)__ldg(&R.desc[r].y) + __ldg(&S.desc[s].y) > (uint64_t)cta_threshold;
+            } else {
                 out[k] = APRIL_VERDICT_ERROR;
                 atomicOr(status, ST_BAD_ID);
             }
-            continue;
         }
-        const uint4 dr = __ldg(R.desc + r), ds = __ldg(S.desc + s);
-        uint8_t v;
-        if (!warp_join(R.iv + dr.x, dr.y, S.iv + ds.x, ds.y, lane)) v = APRIL_TRUE_NEGATIVE;
-        else if (warp_join(R.iv + dr.x, dr.y, S.iv + ds.z, ds.w, lane)) v = APRIL_TRUE_HIT;
-        else if (warp_join(R.iv + dr.z, dr.w, S.iv + ds.x, ds.y, lane)) v = APRIL_TRUE_HIT;
-        else v = APRIL_INCONCLUSIVE;
-        if (lane == 0) out[k] = v;
+        const uint32_t mask = __ballot_sync(kFull, big);
+        if (mask) {
+            const uint32_t leader = __ffs(mask) - 1;
+            uint32_t pos = 0;
+            if (lane == leader) pos = atomicAdd(&counters[C_BIG_COUNT], __popc(mask));
+            pos = __shfl_sync(kFull, pos, leader) + __popc(mask & ((1u << lane) - 1u));
+            if (big) big_list[pos] = (uint32_t)k;
+        }
+    }
+}
+
+// ------------------------------------------ K3: persistent filter (batched)
+// Group engine.  A warp is split into 32/G groups of G lanes; each group
+// filters one pair at a time (its three joins in Algorithm 2's order), with
+// its own window of at most 8*G intervals per list staged in shared memory.
+// One pass of the loop below advances every group's current join by one
+// window, so the fixed cost of a window step (staging, the per-thread merge-
+// path search, the vote) is shared by 32/G joins.  When a group finishes its
+// pair it takes the next one from the 32-pair chunk the warp holds in its
+// lanes; the warp pops a new chunk from a global counter when the chunk is
+// used up.  Pairs above the CTA threshold are skipped here (phase 1 did them).
+template <uint32_t G>
+struct GroupCfg {
+    static constexpr uint32_t NG = 32 / G;
+    static constexpr uint32_t WMAX = 8 * G;
+    static constexpr uint32_t BUF = WMAX + 2;
+    static constexpr uint32_t LEADS = G == 32 ? 1u : G == 16 ? 0x00010001u : G == 8 ? 0x01010101u : 0x11111111u;
+};
+static_assert(GroupCfg<4>::NG * 2 * GroupCfg<4>::BUF <= kWarpShare, "group buffers fit in a warp's share");
+static_assert(GroupCfg<8>::NG * 2 * GroupCfg<8>::BUF <= kWarpShare, "group buffers fit in a warp's share");
+static_assert(GroupCfg<16>::NG * 2 * GroupCfg<16>::BUF <= kWarpShare, "group buffers fit in a warp's share");
+static_assert(2 * kWarpBuf <= kWarpShare, "warp buffers fit in a warp's share");
+
+// Lists of join `stage` of a pair: 0 = A(r) x A(s), 1 = A(r) x F(s), 2 = F(r) x A(s).
+__device__ __forceinline__ bool join_lists(const DevSet &R, const DevSet &S, const uint4 &dr, const uint4 &ds,
+                                           uint32_t stage, const uint2 *&X, uint32_t &nX, const uint2 *&Y,
+                                           uint32_t &nY) {
+    X = R.iv + (stage == 2 ? dr.z : dr.x);
+    nX = stage == 2 ? dr.w : dr.y;
+    Y = S.iv + (stage == 1 ? ds.z : ds.x);
+    nY = stage == 1 ? ds.w : ds.y;
+    return nX != 0 && nY != 0;
+}
+
+template <uint32_t G>
+__device__ __forceinline__ void group_engine(const DevSet &R, const DevSet &S, const uint32_t *__restrict__ pr,
+                                             const uint32_t *__restrict__ ps, uint64_t n, uint8_t *__restrict__ out,
+                                             uint32_t *counters, uint32_t cta_threshold, uint2 *wbuf, uint32_t lane,
+                                             uint32_t w0) {
+    using C = GroupCfg<G>;
+    const uint32_t g = lane / G, t = lane % G, glead = g * G;
+    const uint32_t gbits = (G == 32 ? kFull : ((1u << G) - 1u)) << glead;
+    uint2 *xb = wbuf + g * 2 * C::BUF, *yb = xb + C::BUF;
+    const uint64_t nchunks = (n + 31) / 32;
+    // the warp's chunk: lane l holds pair base + l
+    uint64_t qk = 0;
+    uint4 qdr = make_uint4(0, 0, 0, 0), qds = make_uint4(0, 0, 0, 0);
+    uint32_t avail = 0;
+    bool exhausted = false;
+    // this group's pair and join
+    bool active = false;
+    uint64_t k = 0;
+    uint4 dr = make_uint4(0, 0, 0, 0), ds = make_uint4(0, 0, 0, 0);
+    uint32_t stage = 0, nX = 0, nY = 0, i0 = 0, j0 = 0, w = w0;
+    const uint2 *X = nullptr, *Y = nullptr;
+
+    for (;;) {
+        // -------- hand pairs to idle groups
+        uint32_t needg = __ballot_sync(kFull, !active) & C::LEADS;
+        while (needg && !exhausted) {
+            if (!avail) {
+                uint32_t c = 0;
+                if (lane == 0) c = atomicAdd(&counters[C_CHUNK_HEAD], 1u);
+                c = __shfl_sync(kFull, c, 0);
+                if (c >= nchunks) {
+                    exhausted = true;
+                    break;
+                }
+                qk = (uint64_t)c * 32 + lane;
+                bool take = false;
+                if (qk < n) {
+                    const uint32_t r = __ldg(pr + qk), s2 = __ldg(ps + qk);
+                    if (r < R.n && s2 < S.n) {  // out-of-range ids were reported by the binning kernel
+                        qdr = __ldg(R.desc + r);
+                        qds = __ldg(S.desc + s2);
+                        take = (uint64_t)qdr.y + qds.y <= (uint64_t)cta_threshold;
+                    }
+                }
+                avail = __ballot_sync(kFull, take);
+                continue;
+            }
+            const uint32_t cnt = min((uint32_t)__popc(needg), (uint32_t)__popc(avail));
+            const uint32_t grank = __popc(needg & ((1u << glead) - 1u));
+            const bool gets = ((needg >> glead) & 1u) && grank < cnt;
+            const uint32_t src = gets ? __fns(avail, 0, (int)grank + 1) : lane;
+            const uint32_t klo = __shfl_sync(kFull, (uint32_t)qk, src);
+            const uint32_t khi = __shfl_sync(kFull, (uint32_t)(qk >> 32), src);
+            const uint4 a = shfl4(qdr, src), b = shfl4(qds, src);
+            if (gets) {
+                k = ((uint64_t)khi << 32) | klo;
+                dr = a;
+                ds = b;
+                stage = 0;
+                i0 = j0 = 0;
+                w = w0;
+                active = join_lists(R, S, dr, ds, 0, X, nX, Y, nY);
+                if (!active && t == 0) out[k] = APRIL_TRUE_NEGATIVE;  // an empty A-list meets nothing
+            }
+            const uint32_t lastbit = __fns(avail, 0, (int)cnt);
+            avail &= (lastbit >= 31) ? 0u : ~((2u << lastbit) - 1u);
+            needg = __ballot_sync(kFull, !active) & C::LEADS;
+        }
+        if (!__any_sync(kFull, active)) break;  // only reachable once the pairs are exhausted
+
+        // -------- one window of every active group's join
+        uint32_t nx = 0, ny = 0, xa = 0, ya = 0;
+        if (active) {
+            nx = min(w, nX - i0);
+            ny = min(w, nY - j0);
+            xa = smem_addr(stage_window<G>(xb, X + i0, nx, t));
+            ya = smem_addr(stage_window<G>(yb, Y + j0, ny, t));
+        }
+        cp_async_wait_all();
+        __syncwarp();
+        bool found = false;
+        uint32_t state = 0xffffffffu, D = 0, owner = 0;
+        if (active) {
+            D = min(w, nx + ny);
+            const uint32_t per = w / G;
+            owner = (D - 1) / per;
+            found = window_walk(xa, nx, ya, ny, w, D, per, t * per, state);
+        }
+        const uint32_t fmask = __ballot_sync(kFull, found);  // every read of the windows is done here
+        const uint32_t split = __shfl_sync(kFull, state, glead + owner);
+        if (active) {
+            int res = -1;  // -1: join continues, 0: no overlap, 1: overlap
+            if (fmask & gbits) res = 1;
+            else if (D == nx + ny || split == 0xffffffffu) res = 0;
+            else {
+                i0 += split;
+                j0 += D - split;
+                w = min(w * 2u, C::WMAX);
+            }
+            if (res >= 0) {
+                // Algorithm 2: AA false -> TN; AF or FA true -> TH; else INC
+                int verdict = -1;
+                if (stage == 0) verdict = res ? -1 : APRIL_TRUE_NEGATIVE;
+                else if (res) verdict = APRIL_TRUE_HIT;
+                else if (stage == 2) verdict = APRIL_INCONCLUSIVE;
+                while (verdict < 0) {
+                    ++stage;
+                    i0 = j0 = 0;
+                    w = w0;
+                    if (join_lists(R, S, dr, ds, stage, X, nX, Y, nY)) break;
+                    if (stage == 2) verdict = APRIL_INCONCLUSIVE;
+                }
+                if (verdict >= 0) {
+                    if (t == 0) out[k] = (uint8_t)verdict;
+                    active = false;
+                }
+            }
+        }
+    }
+}
+
+// Phase 1: each CTA pops long pairs and joins each with all its warps (the
+// merge path of one join split over 256 threads).  Phase 2: the group engine
+// on the short pairs.  Work is handed out by atomic counters; nothing waits
+// on another CTA.
+template <uint32_t G>
+__global__ void __launch_bounds__(kBlock) k_persistent(DevSet R, DevSet S, const uint32_t *__restrict__ pr,
+                                                       const uint32_t *__restrict__ ps, uint64_t n,
+                                                       uint8_t *__restrict__ out, uint32_t *status,
+                                                       uint32_t cta_threshold, const uint32_t *__restrict__ big_list,
+                                                       uint32_t *counters, uint32_t w0_group, uint32_t w0_cta) {
+    __shared__ __align__(16) uint2 sm[kSharedIv];
+    __shared__ uint32_t s_item, s_slot;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t nbig = *((volatile uint32_t *)&counters[C_BIG_COUNT]);
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(&counters[C_BIG_HEAD], 1u);
+        __syncthreads();
+        const uint32_t it = s_item;
+        __syncthreads();
+        if (it >= nbig) break;
+        const uint64_t k = big_list[it];
+        const uint4 dr = __ldg(R.desc + __ldg(pr + k)), ds = __ldg(S.desc + __ldg(ps + k));
+        const uint8_t v = cta_verdict(R, S, dr, ds, sm, sm + kCtaBuf, &s_slot, tid, w0_cta);
+        if (tid == 0) out[k] = v;
+    }
+    __syncthreads();
+    uint2 *wbuf = sm + warp * kWarpShare;
+    if (G == 32) {
+        const uint64_t nchunks = (n + 31) / 32;
+        for (;;) {
+            uint32_t c = 0;
+            if (lane == 0) c = atomicAdd(&counters[C_CHUNK_HEAD], 1u);
+            c = __shfl_sync(kFull, c, 0);
+            if (c >= nchunks) break;
+            warp_chunk(R, S, pr, ps, n, (uint64_t)c * 32, out, status, wbuf, wbuf + kWarpBuf, lane, w0_group,
+                       cta_threshold, false);
+        }
+    } else {
+        group_engine<G>(R, S, pr, ps, n, out, counters, cta_threshold, wbuf, lane, w0_group);
     }
 }
 
@@ -160,16 +388,60 @@ int g_num_sms = 0;
 
 }  // namespace
 
+struct GraphKey {
+    const void *r_desc, *r_iv, *s_desc, *s_iv;
+    uint32_t rn, sn;
+    const void *d_r, *d_s, *out, *scratch;
+    uint64_t n;
+    april_tune tune;
+    unsigned grid_bin, grid_main;
+    bool operator==(const GraphKey &o) const {
+        return r_desc == o.r_desc && r_iv == o.r_iv && s_desc == o.s_desc && s_iv == o.s_iv && rn == o.rn &&
+               sn == o.sn && d_r == o.d_r && d_s == o.d_s && out == o.out && scratch == o.scratch && n == o.n &&
+               tune.cta_threshold == o.tune.cta_threshold && tune.group_lanes == o.tune.group_lanes &&
+               tune.group_window == o.tune.group_window && tune.cta_window == o.tune.cta_window &&
+               grid_bin == o.grid_bin && grid_main == o.grid_main;
+    }
+};
+
 struct april_ctx {
     int device = 0;
     uint32_t *d_status = nullptr;  // 256-byte status block (word 0: ST_* bits)
     int num_sms = 0;
+    int persistent_blocks_per_sm[4] = {1, 1, 1, 1};  // occupancy of k_persistent<4, 8, 16, 32>
+    april_tune tune{};
+    cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+    cudaGraphExec_t graph = nullptr;    // the batched pipeline, captured once per argument set
+    GraphKey key{};
+    uint64_t graph_launches = 0;
+    uint64_t graph_captures = 0;
 };
 
 using april::fail;
 
 static april_status cuda_fail(cudaError_t e, const char *what) {
     return fail(APRIL_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static april_tune default_tune() {
+    april_tune t{};
+    t.cta_threshold = 8192;
+    t.group_lanes = 8;
+    t.group_window = 16;
+    t.cta_window = 256;
+    t.blocks_per_sm = 0;
+    t.ms = 0.f;
+    return t;
+}
+
+static april_status check_tune(const april_tune &t) {
+    const uint32_t G = t.group_lanes;
+    if (G != 4 && G != 8 && G != 16 && G != 32) return fail(APRIL_ERR_INVALID_ARG, "group_lanes must be 4, 8, 16 or 32");
+    if (t.group_window < G || t.group_window > 8 * G || (t.group_window & (t.group_window - 1)))
+        return fail(APRIL_ERR_INVALID_ARG, "group_window must be a power of two in [group_lanes, 8*group_lanes]");
+    if (t.cta_window < kBlock || t.cta_window > kCtaWMax || (t.cta_window & (t.cta_window - 1)))
+        return fail(APRIL_ERR_INVALID_ARG, "cta_window must be a power of two in [256, 2048]");
+    return APRIL_OK;
 }
 
 extern "C" april_status april_ctx_create(int device, april_ctx **out) {
@@ -179,22 +451,26 @@ extern "C" april_status april_ctx_create(int device, april_ctx **out) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     auto *c = new april_ctx();
     c->device = device;
+    c->tune = default_tune();
     e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->persistent_blocks_per_sm[0], k_persistent<4>, kBlock, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->persistent_blocks_per_sm[1], k_persistent<8>, kBlock, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->persistent_blocks_per_sm[2], k_persistent<16>, kBlock, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->persistent_blocks_per_sm[3], k_persistent<32>, kBlock, 0);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_status, 256);
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, 256);
     if (e != cudaSuccess) {
+        if (c->d_status) cudaFree(c->d_status);
+        if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
         delete c;
-        return cuda_fail(e, "cudaDeviceGetAttribute");
+        return cuda_fail(e, "april_ctx_create");
     }
-    e = cudaMalloc(&c->d_status, 256);
-    if (e != cudaSuccess) {
-        delete c;
-        return cuda_fail(e, "cudaMalloc(status)");
-    }
-    e = cudaMemset(c->d_status, 0, 256);
-    if (e != cudaSuccess) {
-        cudaFree(c->d_status);
-        delete c;
-        return cuda_fail(e, "cudaMemset(status)");
-    }
+    for (int &b : c->persistent_blocks_per_sm) b = b < 1 ? 1 : b;
     g_num_sms = c->num_sms;
     *out = c;
     return APRIL_OK;
@@ -202,8 +478,24 @@ extern "C" april_status april_ctx_create(int device, april_ctx **out) {
 
 extern "C" void april_ctx_destroy(april_ctx *ctx) {
     if (!ctx) return;
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->d_status) cudaFree(ctx->d_status);
     delete ctx;
+}
+
+extern "C" april_status april_set_tune(april_ctx *ctx, const april_tune *t) {
+    if (!ctx || !t) return fail(APRIL_ERR_INVALID_ARG, "NULL argument");
+    april_status st = check_tune(*t);
+    if (st) return st;
+    ctx->tune = *t;
+    return APRIL_OK;
+}
+
+extern "C" april_status april_get_tune(const april_ctx *ctx, april_tune *t) {
+    if (!ctx || !t) return fail(APRIL_ERR_INVALID_ARG, "NULL argument");
+    *t = ctx->tune;
+    return APRIL_OK;
 }
 
 extern "C" april_status april_upload(const april_sets *S, void *dev_buf, size_t dev_bytes, void *stream,
@@ -226,18 +518,85 @@ extern "C" april_status april_upload(const april_sets *S, void *dev_buf, size_t 
     return APRIL_OK;
 }
 
+static inline uint64_t round256(uint64_t b) { return (b + 255) / 256 * 256; }
+
 extern "C" april_status april_filter_scratch_bytes(int mode, uint64_t n, size_t *bytes) {
     if (!bytes) return fail(APRIL_ERR_INVALID_ARG, "bytes is NULL");
-    (void)n;
     switch (mode) {
         case APRIL_MODE_PLAIN:
         case APRIL_MODE_WARP: *bytes = 0; return APRIL_OK;
+        case APRIL_MODE_BATCHED: *bytes = (size_t)(kCounterBytes + round256(4 * n)); return APRIL_OK;
         default: return fail(APRIL_ERR_INVALID_ARG, "unknown mode");
     }
 }
 
 static inline DevSet dev_set(const april_dev_sets *d) {
     return DevSet{(const uint4 *)d->desc, (const uint2 *)d->iv, d->n_objects};
+}
+
+// Enqueues the batched pipeline (counter reset, K4 binning, K3 persistent
+// filter) on `st`.
+static cudaError_t enqueue_batched(april_ctx *ctx, const DevSet &R, const DevSet &S, const uint32_t *d_r,
+                                   const uint32_t *d_s, uint64_t n, uint8_t *out, void *scratch, unsigned grid_bin,
+                                   unsigned grid_main, cudaStream_t st) {
+    uint32_t *counters = (uint32_t *)scratch;
+    uint32_t *big_list = (uint32_t *)((char *)scratch + kCounterBytes);
+    const april_tune &t = ctx->tune;
+    cudaError_t e = cudaMemsetAsync(counters, 0, kCounterBytes, st);
+    if (e != cudaSuccess) return e;
+    k_bin<<<grid_bin, 256, 0, st>>>(R, S, d_r, d_s, n, out, ctx->d_status, t.cta_threshold, big_list, counters);
+#define APRIL_LAUNCH_PERSISTENT(G)                                                                             \
+    k_persistent<G><<<grid_main, kBlock, 0, st>>>(R, S, d_r, d_s, n, out, ctx->d_status, t.cta_threshold, big_list, \
+                                                  counters, t.group_window, t.cta_window)
+    switch (t.group_lanes) {
+        case 4: APRIL_LAUNCH_PERSISTENT(4); break;
+        case 8: APRIL_LAUNCH_PERSISTENT(8); break;
+        case 16: APRIL_LAUNCH_PERSISTENT(16); break;
+        default: APRIL_LAUNCH_PERSISTENT(32); break;
+    }
+#undef APRIL_LAUNCH_PERSISTENT
+    return cudaGetLastError();
+}
+
+// The batched pipeline runs as one CUDA graph: captured on the context's
+// private stream the first time an argument set is seen, then replayed on the
+// caller's stream.
+static april_status launch_batched(april_ctx *ctx, const april_dev_sets *R, const april_dev_sets *S,
+                                   const uint32_t *d_r, const uint32_t *d_s, uint64_t n, uint8_t *out,
+                                   void *scratch, cudaStream_t st) {
+    const DevSet dR = dev_set(R), dS = dev_set(S);
+    const unsigned grid_bin = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx->num_sms * 8);
+    const uint32_t gl = ctx->tune.group_lanes;
+    const int occ = ctx->persistent_blocks_per_sm[gl == 4 ? 0 : gl == 8 ? 1 : gl == 16 ? 2 : 3];
+    const int bps = ctx->tune.blocks_per_sm ? (int)std::min<uint32_t>(ctx->tune.blocks_per_sm, (uint32_t)occ) : occ;
+    const unsigned grid_main = (unsigned)std::max(1, ctx->num_sms * bps);
+    GraphKey key{R->desc, R->iv, S->desc, S->iv, R->n_objects, S->n_objects, d_r, d_s, out, scratch, n,
+                 ctx->tune, grid_bin, grid_main};
+    cudaError_t e;
+    if (!ctx->graph || !(key == ctx->key)) {
+        if (ctx->graph) {
+            cudaGraphExecDestroy(ctx->graph);
+            ctx->graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+        cudaError_t e1 = enqueue_batched(ctx, dR, dS, d_r, d_s, n, out, scratch, grid_bin, grid_main, ctx->cap_stream);
+        e = cudaStreamEndCapture(ctx->cap_stream, &g);
+        if (e1 != cudaSuccess) e = e1;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            ctx->graph = nullptr;
+            return cuda_fail(e, "capturing the batched pipeline");
+        }
+        ctx->key = key;
+        ctx->graph_captures++;
+    }
+    e = cudaGraphLaunch(ctx->graph, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    ctx->graph_launches++;
+    return APRIL_OK;
 }
 
 extern "C" april_status april_filter_pairs(april_ctx *ctx, const april_dev_sets *R, const april_dev_sets *S,
@@ -248,8 +607,7 @@ extern "C" april_status april_filter_pairs(april_ctx *ctx, const april_dev_sets 
     if (n == 0) return APRIL_OK;
     if (!d_r || !d_s || !d_verdict) return fail(APRIL_ERR_INVALID_ARG, "NULL pair or verdict array");
     if (R->order != S->order) return fail(APRIL_ERR_INVALID_ARG, "R and S are on different grids");
-    (void)d_scratch;
-    (void)scratch_bytes;
+    if (n > 0xFFFFFFFFull) return fail(APRIL_ERR_INVALID_ARG, "at most 2^32-1 pairs per call");
     cudaStream_t st = (cudaStream_t)stream;
     const DevSet dR = dev_set(R), dS = dev_set(S);
     const int sms = ctx->num_sms;
@@ -261,10 +619,17 @@ extern "C" april_status april_filter_pairs(april_ctx *ctx, const april_dev_sets 
             break;
         }
         case APRIL_MODE_WARP: {
-            uint64_t blocks = (n + 7) / 8;
-            unsigned grid = (unsigned)std::min<uint64_t>(blocks, (uint64_t)sms * 8);
-            k_warp<<<grid, 256, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, ctx->d_status);
+            uint64_t blocks = (n + kBlock - 1) / kBlock;
+            unsigned grid = (unsigned)std::min<uint64_t>(blocks, (uint64_t)sms * 16);
+            k_warp<<<grid, kBlock, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, ctx->d_status, kWarpFirstWindow);
             break;
+        }
+        case APRIL_MODE_BATCHED: {
+            size_t need = 0;
+            april_filter_scratch_bytes(mode, n, &need);
+            if (!d_scratch || scratch_bytes < need) return fail(APRIL_ERR_INVALID_ARG, "scratch missing or too small");
+            if (((uintptr_t)d_scratch) & 255u) return fail(APRIL_ERR_INVALID_ARG, "scratch must be 256-byte aligned");
+            return launch_batched(ctx, R, S, d_r, d_s, n, d_verdict, d_scratch, st);
         }
         default: return fail(APRIL_ERR_INVALID_ARG, "unknown mode");
     }
@@ -273,7 +638,65 @@ extern "C" april_status april_filter_pairs(april_ctx *ctx, const april_dev_sets 
     return APRIL_OK;
 }
 
-static inline uint64_t round256(uint64_t b) { return (b + 255) / 256 * 256; }
+extern "C" april_status april_autotune(april_ctx *ctx, const april_dev_sets *R, const april_dev_sets *S,
+                                       const uint32_t *d_r, const uint32_t *d_s, uint64_t n, uint8_t *d_verdict,
+                                       void *d_scratch, size_t scratch_bytes, void *stream, april_tune *out) {
+    if (!ctx || !R || !S || !out) return fail(APRIL_ERR_INVALID_ARG, "NULL argument");
+    if (n == 0) {
+        *out = ctx->tune;
+        return APRIL_OK;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint32_t thresholds[] = {2048, 4096, 8192, 16384, 0xffffffffu};
+    const uint32_t groups[][2] = {{4, 8}, {4, 16}, {8, 16}, {8, 32}, {16, 32}, {16, 64}, {32, 64}};
+    const april_tune saved = ctx->tune;
+    april_tune best = saved;
+    float best_ms = 1e30f;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    april_status rc = APRIL_OK;
+    for (uint32_t T : thresholds) {
+        for (const auto &gw : groups) {
+            april_tune t = saved;
+            t.cta_threshold = T;
+            t.group_lanes = gw[0];
+            t.group_window = gw[1];
+            ctx->tune = t;
+            float best_here = 1e30f;
+            for (int rep = 0; rep < 3 && rc == APRIL_OK; ++rep) {
+                e = cudaEventRecord(a, st);
+                if (e != cudaSuccess) { rc = cuda_fail(e, "cudaEventRecord"); break; }
+                rc = april_filter_pairs(ctx, R, S, d_r, d_s, n, d_verdict, APRIL_MODE_BATCHED, d_scratch,
+                                        scratch_bytes, stream);
+                if (rc) break;
+                e = cudaEventRecord(b, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(b);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+                if (e != cudaSuccess) { rc = cuda_fail(e, "timing an autotune candidate"); break; }
+                if (rep > 0) best_here = std::min(best_here, ms);  // rep 0 captures the graph
+            }
+            if (rc) break;
+            if (best_here < best_ms) {
+                best_ms = best_here;
+                best = t;
+            }
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc) {
+        ctx->tune = saved;
+        return rc;
+    }
+    best.ms = best_ms;
+    ctx->tune = best;
+    *out = best;
+    return APRIL_OK;
+}
 
 extern "C" april_status april_filter_host_work_bytes(int mode, uint64_t n, size_t *bytes) {
     if (!bytes) return fail(APRIL_ERR_INVALID_ARG, "bytes is NULL");

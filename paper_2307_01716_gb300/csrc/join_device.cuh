@@ -1,0 +1,227 @@
+// Device-side interval joins of the APRIL filter (paper Sec. 4.2,
+// Algorithm 2: IntervalJoin and its use in the AA, AF, FA sequence).
+//
+// Interval convention: [st, end) with end stored mod 2^32; comparisons use
+// last = end - 1 in uint32, so an interval holding cell 2^32-1 (end 2^32,
+// stored as 0) compares correctly.
+//   X_i overlaps Y_j  <=>  X_i.st <= Y_j.last  and  Y_j.st <= X_i.last
+//   merge step        :    advance X if X_i.last <= Y_j.last, else Y.
+//
+// Parallel join.  The sequential merge walks the merge path of X and Y
+// ordered by `last` (ties: X first).  At diagonal d (d elements emitted) it
+// sits at state (i, d - i) and tests X_i against Y_{d-i}.  "Some test
+// succeeds" is the answer, so any split of the diagonals gives the same
+// boolean.  A group (a warp or a CTA) stages a window of each list in shared
+// memory, every thread finds the merge-path state at its first diagonal by
+// binary search in the window and then walks a few diagonals serially, doing
+// exactly the tests the sequential merge does there.  The group ORs the
+// results, advances both lists by the split at the window's last diagonal,
+// and doubles the window (up to a maximum) so that joins that stop early read
+// little while long scans keep many bytes in flight.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace april_dev {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+struct DevSet {
+    const uint4 *desc;  // per object {a_off, a_len, f_off, f_len}
+    const uint2 *iv;    // intervals {st, end}
+    uint32_t n;
+};
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// IntervalJoin as written in Algorithm 2: one thread walks both lists.
+__device__ __forceinline__ bool seq_join(const uint2 *__restrict__ X, uint32_t nx, const uint2 *__restrict__ Y,
+                                         uint32_t ny) {
+    if (nx == 0 || ny == 0) return false;
+    uint32_t i = 0, j = 0;
+    uint2 x = __ldg(X), y = __ldg(Y);
+    for (;;) {
+        const uint32_t xl = x.y - 1u, yl = y.y - 1u;
+        if (x.x <= yl && y.x <= xl) return true;
+        if (xl <= yl) {
+            if (++i == nx) return false;
+            x = __ldg(X + i);
+        } else {
+            if (++j == ny) return false;
+            y = __ldg(Y + j);
+        }
+    }
+}
+
+// Shared-memory accesses on 32-bit shared-window addresses (the windows
+// always live in shared memory; explicit ld.shared avoids generic addressing).
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint2 lds2(uint32_t a) {
+    uint2 v;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];\n" : "=r"(v.x), "=r"(v.y) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t lds1(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];\n" : "=r"(v) : "r"(a));
+    return v;
+}
+
+// Merge-path split of the windows at shared addresses xa (nx intervals) and
+// ya (ny intervals) at diagonal d: the number of X elements among the first
+// d merged elements (X first on equal `last`).
+__device__ __forceinline__ uint32_t merge_split(uint32_t xa, uint32_t nx, uint32_t ya, uint32_t ny, uint32_t d) {
+    uint32_t lo = d > ny ? d - ny : 0u, hi = min(d, nx);
+    // compares X[mid].last <= Y[d-mid-1].last; the byte offsets of the two
+    // `end` words move in opposite directions as mid changes
+    const uint32_t yb = ya + 8u * (d - 1u) + 4u;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        const uint32_t xl = lds1(xa + 8u * mid + 4u) - 1u;
+        const uint32_t yl = lds1(yb - 8u * mid) - 1u;
+        if (xl <= yl) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Walks `steps` diagonals of the window from state (i, j): the tests of the
+// sequential merge at those states.  `full` windows (neither list ends in
+// them) need no bound checks.  Returns the OR of the tests; *state receives
+// i after the last step, or 0xffffffff if a list ran out first.
+template <uint32_t PER>
+__device__ __forceinline__ bool walk_fixed(uint32_t xa, uint32_t ya, uint32_t i, uint32_t j, uint32_t &state) {
+    uint2 x = lds2(xa + 8u * i), y = lds2(ya + 8u * j);
+    bool found = false;
+#pragma unroll
+    for (uint32_t q = 0; q < PER; ++q) {
+        const uint32_t xl = x.y - 1u, yl = y.y - 1u;
+        found |= (x.x <= yl) & (y.x <= xl);
+        const bool ax = xl <= yl;
+        i += ax;
+        j += !ax;
+        if (q + 1 < PER) {
+            const uint2 v = lds2(ax ? xa + 8u * i : ya + 8u * j);
+            x = ax ? v : x;
+            y = ax ? y : v;
+        }
+    }
+    state = i;
+    return found;
+}
+
+__device__ __forceinline__ bool walk_checked(uint32_t xa, uint32_t nx, uint32_t ya, uint32_t ny, uint32_t i,
+                                             uint32_t j, uint32_t steps, uint32_t &state) {
+    bool found = false;
+    uint32_t q = 0;
+    for (; q < steps && i < nx && j < ny; ++q) {
+        const uint2 x = lds2(xa + 8u * i), y = lds2(ya + 8u * j);
+        const uint32_t xl = x.y - 1u, yl = y.y - 1u;
+        found |= (x.x <= yl) & (y.x <= xl);
+        const bool ax = xl <= yl;
+        i += ax;
+        j += !ax;
+    }
+    state = (q == steps) ? i : 0xffffffffu;
+    return found;
+}
+
+// The merge-path work of one thread in a window of D diagonals (w per list,
+// nx/ny staged): diagonals [d0, d0 + per).
+__device__ __forceinline__ bool window_walk(uint32_t xa, uint32_t nx, uint32_t ya, uint32_t ny, uint32_t w,
+                                            uint32_t D, uint32_t per, uint32_t d0, uint32_t &state) {
+    state = 0xffffffffu;
+    if (d0 >= D) return false;
+    const uint32_t i = merge_split(xa, nx, ya, ny, d0);
+    const uint32_t j = d0 - i;
+    if (nx == w && ny == w) {
+        switch (per) {
+            case 1: return walk_fixed<1>(xa, ya, i, j, state);
+            case 2: return walk_fixed<2>(xa, ya, i, j, state);
+            case 4: return walk_fixed<4>(xa, ya, i, j, state);
+            default: return walk_fixed<8>(xa, ya, i, j, state);
+        }
+    }
+    return walk_checked(xa, nx, ya, ny, i, j, min(per, D - d0), state);
+}
+
+struct WarpScope {
+    static __device__ __forceinline__ void sync() { __syncwarp(); }
+    // OR of `b` over the group; `v` from thread `src` is returned to all.
+    // Doubles as the point after which the window may be overwritten.
+    static __device__ __forceinline__ bool vote(bool b, uint32_t &v, uint32_t src, uint32_t *) {
+        v = __shfl_sync(kFull, v, src);
+        return __any_sync(kFull, b) != 0;
+    }
+};
+
+struct CtaScope {
+    static __device__ __forceinline__ void sync() { __syncthreads(); }
+    static __device__ __forceinline__ bool vote(bool b, uint32_t &v, uint32_t src, uint32_t *slot) {
+        if (threadIdx.x == src) *slot = v;
+        const bool any = __syncthreads_or(b) != 0;
+        v = *slot;
+        return any;
+    }
+};
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+// Copies src[0..cnt) into shared memory so that the returned pointer p has
+// p[k] == src[k].  Lists start 16-byte aligned, so src - (src odd) is too;
+// the copy runs in 16-byte pieces from there (buf holds WMAX + 2 intervals,
+// 16-byte aligned).  Elements outside [src-1, src+cnt) are never read.
+template <uint32_t NT>
+__device__ __forceinline__ uint2 *stage_window(uint2 *buf, const uint2 *src, uint32_t cnt, uint32_t tid) {
+    const uint32_t odd = (uint32_t)(((uintptr_t)src >> 3) & 1u);
+    const uint2 *a = src - odd;
+    const uint32_t tot = cnt + odd, full = tot >> 1;
+    for (uint32_t c = tid; c < full; c += NT) cp_async16(buf + 2 * c, a + 2 * c);
+    if ((tot & 1u) && tid == full % NT) cp_async8(buf + tot - 1, a + tot - 1);
+    return buf + odd;
+}
+
+// Any overlap between X[0..n) and Y[0..m), by a group of NT threads (thread
+// index tid) with shared buffers xb, yb of WMAX + 2 intervals each (16-byte
+// aligned) and, for a CTA group, one shared word `slot`.  The first window
+// holds w0 intervals per list (a multiple of NT); later windows double up to
+// WMAX.  Every thread of the group must call it with the same arguments.
+template <class Scope, uint32_t NT, uint32_t WMAX>
+__device__ __noinline__ bool tile_join(const uint2 *__restrict__ X, uint32_t n, const uint2 *__restrict__ Y,
+                                       uint32_t m, uint2 *xb, uint2 *yb, uint32_t *slot, uint32_t tid,
+                                       uint32_t w0) {
+    uint32_t i0 = 0, j0 = 0, w = w0;
+    while (i0 < n && j0 < m) {
+        const uint32_t nx = min(w, n - i0), ny = min(w, m - j0);
+        const uint32_t xa = smem_addr(stage_window<NT>(xb, X + i0, nx, tid));
+        const uint32_t ya = smem_addr(stage_window<NT>(yb, Y + j0, ny, tid));
+        cp_async_wait_all();
+        Scope::sync();
+        // D diagonals of the merge path lie in this window; thread tid walks
+        // [d0, d0 + per).  No list can run out inside a full window.
+        const uint32_t D = min(w, nx + ny);
+        const uint32_t per = w / NT;
+        const uint32_t owner = (D - 1) / per;  // walks the window's last diagonal
+        uint32_t state;
+        const bool found = window_walk(xa, nx, ya, ny, w, D, per, tid * per, state);
+        if (Scope::vote(found, state, owner, slot)) return true;
+        if (D == nx + ny || state == 0xffffffffu) return false;  // a list is exhausted
+        i0 += state;
+        j0 += D - state;
+        w = min(w * 2u, WMAX);
+    }
+    return false;
+}
+
+}  // namespace april_dev

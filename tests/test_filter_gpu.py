@@ -15,7 +15,7 @@ from paper_2307_01716_gb300 import april as A
 
 pytestmark = pytest.mark.gpu
 
-MODES = ["plain", "warp"]
+MODES = ["plain", "warp", "batched"]
 
 
 @pytest.fixture(scope="module")
@@ -131,3 +131,62 @@ def test_full_size_config2_sampled(torch_cuda, ctx, full_config2, mode):
     # every verdict agrees with the host execution of Algorithm 2 on the same lists
     hv, _ = A.april_host_filter(R, S, w.pr, w.ps)
     assert np.array_equal(got, hv)
+
+
+@pytest.mark.parametrize("threshold", [0, 64, 0xFFFFFFFF])
+@pytest.mark.parametrize("group", [(4, 4), (4, 32), (8, 8), (8, 64), (16, 16), (16, 128), (32, 32), (32, 256)])
+def test_batched_tunings(torch_cuda, ctx, threshold, group):
+    """Every pair joined by a whole CTA (threshold 0), a mix, or none; every
+    group size with its smallest and largest first window."""
+    w = _data.workload(3, 0.01)
+    _, _, dR, dS = _device_sets(w)
+    saved = ctx.get_tune()
+    t = A.april_tune(threshold, group[0], group[1], 256, 0, 0.0)
+    ctx.set_tune(t)
+    try:
+        got = run_filter(torch_cuda, ctx, dR, dS, w.pr, w.ps, "batched")
+    finally:
+        ctx.set_tune(saved)
+    assert np.array_equal(got, _data.oracle_verdicts(3, 0.01))
+
+
+def test_autotune_then_batched(torch_cuda, ctx):
+    torch = torch_cuda
+    w = _data.workload(3, 0.01)
+    _, _, dR, dS = _device_sets(w)
+    n = len(w.pr)
+    d_r = torch.from_numpy(w.pr.view(np.int32)).cuda()
+    d_s = torch.from_numpy(w.ps.view(np.int32)).cuda()
+    out = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    scratch = torch.empty(ctx.scratch_bytes(A.MODE_BATCHED, n), dtype=torch.uint8, device="cuda")
+    saved = ctx.get_tune()
+    try:
+        t = ctx.april_autotune(dR, dS, d_r, d_s, n, out, scratch)
+        assert t.ms > 0 and t.group_lanes in (4, 8, 16, 32)
+        assert ctx.get_tune().cta_threshold == t.cta_threshold
+        for _ in range(2):  # the second call replays the captured graph
+            out.fill_(0xEE)
+            ctx.april_filter_pairs(dR, dS, d_r, d_s, n, out, A.MODE_BATCHED, scratch)
+            ctx.april_sync_status()
+            assert np.array_equal(out.cpu().numpy(), _data.oracle_verdicts(3, 0.01))
+    finally:
+        ctx.set_tune(saved)
+
+
+def test_tune_validation(ctx):
+    for bad in [(100, 6, 8, 256), (100, 8, 4, 256), (100, 8, 128, 256), (100, 8, 24, 256), (100, 32, 64, 4096)]:
+        with pytest.raises(A.AprilError):
+            ctx.set_tune(A.april_tune(*bad, 0, 0.0))
+
+
+def test_batched_scratch_checks(torch_cuda, ctx):
+    w = _data.workload(1, 1.0)
+    _, _, dR, dS = _device_sets(w)
+    n = len(w.pr)
+    d_r = torch_cuda.from_numpy(w.pr.view(np.int32)).cuda()
+    d_s = torch_cuda.from_numpy(w.ps.view(np.int32)).cuda()
+    out = torch_cuda.zeros(n, dtype=torch_cuda.uint8, device="cuda")
+    small = torch_cuda.empty(256, dtype=torch_cuda.uint8, device="cuda")
+    with pytest.raises(A.AprilError) as e:
+        ctx.april_filter_pairs(dR, dS, d_r, d_s, n, out, A.MODE_BATCHED, small)
+    assert e.value.status == -1
