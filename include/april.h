@@ -233,6 +233,32 @@ april_status april_filter_pairs_host(april_ctx *ctx, const april_dev_sets *R, co
  * APRIL_ERR_CUDA if the stream itself failed). */
 april_status april_sync_status(april_ctx *ctx, void *stream);
 
+/* ------------------------------------------------- allocation-free filter */
+
+/* The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory when they filter -- code that runs where
+ * cudaMalloc is not allowed or would stall the device (a latency-bound
+ * serving loop, a plugin whose host owns all allocations).  It runs the same
+ * computation as april_filter_pairs(..., APRIL_MODE_BATCHED, ...) with the
+ * default tuning, but without a context and without caller scratch: its
+ * scratch is a static device array inside libapril (16 MiB + 256 bytes),
+ * which every GPU that loads the library holds until the process exits.
+ *
+ *   R, S, d_r, d_s, n, d_verdict, stream: as for april_filter_pairs.
+ *
+ * It allocates nothing: no cudaMalloc, no cudaFree, no allocating library
+ * call.  The first call on a device (with that device current) looks up the
+ * array's device address and the launch shape; make that first call before
+ * any stream capture.  All calls share the one array and each call clears
+ * its counters first: calls whose work overlaps on the GPU (several streams
+ * or host threads) race and must be serialized by the caller.
+ * Out-of-range ids give APRIL_VERDICT_ERROR verdicts (there is no context to
+ * report them to).  n larger than APRIL_NOALLOC_MAX_PAIRS is rejected with
+ * APRIL_ERR_INVALID_ARG.  Asynchronous on `stream`. */
+#define APRIL_NOALLOC_MAX_PAIRS 4194304u
+april_status april_filter_pairs_noalloc(const april_dev_sets *R, const april_dev_sets *S, const uint32_t *d_r,
+                                        const uint32_t *d_s, uint64_t n, uint8_t *d_verdict, void *stream);
+
 /* ----------------------------------------------------- host Algorithm 2 */
 
 /* Algorithm 2 exactly as printed (sequential merge joins AA, AF, FA with early

@@ -82,6 +82,8 @@ SIGNATURES = {
     "april_filter_pairs_host": (_st, [_vp, ctypes.POINTER(april_dev_sets), ctypes.POINTER(april_dev_sets), _vp, _vp,
                                       _u64, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
     "april_host_filter": (_st, [_vp, _vp, _vp, _vp, _u64, _u32, _vp, _vp]),
+    "april_filter_pairs_noalloc": (_st, [ctypes.POINTER(april_dev_sets), ctypes.POINTER(april_dev_sets), _vp, _vp,
+                                         _u64, _vp, _vp]),
     "april_set_tune": (_st, [_vp, ctypes.POINTER(april_tune)]),
     "april_get_tune": (_st, [_vp, ctypes.POINTER(april_tune)]),
     "april_autotune": (_st, [_vp, ctypes.POINTER(april_dev_sets), ctypes.POINTER(april_dev_sets), _vp, _vp, _u64,
@@ -257,6 +259,18 @@ class Context:
         import torch
         st = stream if stream is not None else torch.cuda.current_stream()
         return check(load().april_sync_status(self.handle, st.cuda_stream))
+
+
+NOALLOC_MAX_PAIRS = 4194304
+
+
+def april_filter_pairs_noalloc(R: DevSets, S: DevSets, d_r, d_s, n: int, d_verdict, stream=None) -> None:
+    """Batched filter with library-owned static scratch, for callers that
+    cannot allocate device memory while filtering (see include/april.h)."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    check(load().april_filter_pairs_noalloc(ctypes.byref(R.c), ctypes.byref(S.c), _ptr(d_r), _ptr(d_s), n,
+                                            _ptr(d_verdict), st.cuda_stream))
 
 
 def april_host_filter(R: Sets, S: Sets, pr: np.ndarray, ps: np.ndarray, n_threads: int = 0):

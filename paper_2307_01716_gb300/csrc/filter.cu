@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -750,5 +751,89 @@ extern "C" april_status april_sync_status(april_ctx *ctx, void *stream) {
     }
     if (h & ST_TIMEOUT) return fail(APRIL_ERR_DEVICE_TIMEOUT, "a bounded device wait ran out");
     if (h & ST_BAD_ID) return fail(APRIL_ERR_OUT_OF_RANGE_ID, "a pair named an out-of-range object id");
+    return APRIL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point.
+//
+// For callers that cannot allocate device memory on the call path -- for
+// example code running where cudaMalloc is forbidden or would synchronize
+// the device (inside a real-time serving loop, or a plugin whose host owns
+// every allocation) -- the batched filter can run with its scratch in this
+// file-scope device array instead of caller memory.  The array is part of
+// the loaded module, so every GPU that loads libapril holds it (16 MiB +
+// 256 bytes) until the process exits.  Layout: the batched pipeline's
+// 256-byte counter block (word kNoAllocStatusWord holds the device status),
+// then the list of long pairs, one uint32 per pair.
+constexpr uint64_t kNoAllocMaxPairs = 4ull << 20;
+constexpr uint32_t kNoAllocStatusWord = 8;
+static __device__ __align__(256) uint32_t g_noalloc_scratch[kCounterBytes / 4 + kNoAllocMaxPairs];
+
+namespace {
+
+struct NoAllocDevice {
+    bool ready = false;
+    uint32_t *scratch = nullptr;  // device address of g_noalloc_scratch on this device
+    int num_sms = 0;
+    int blocks_per_sm = 1;
+};
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+
+}  // namespace
+
+extern "C" april_status april_filter_pairs_noalloc(const april_dev_sets *R, const april_dev_sets *S,
+                                                   const uint32_t *d_r, const uint32_t *d_s, uint64_t n,
+                                                   uint8_t *d_verdict, void *stream) {
+    if (!R || !S) return fail(APRIL_ERR_INVALID_ARG, "NULL argument");
+    if (n == 0) return APRIL_OK;
+    if (!d_r || !d_s || !d_verdict) return fail(APRIL_ERR_INVALID_ARG, "NULL pair or verdict array");
+    if (R->order != S->order) return fail(APRIL_ERR_INVALID_ARG, "R and S are on different grids");
+    if (n > kNoAllocMaxPairs)
+        return fail(APRIL_ERR_INVALID_ARG, "april_filter_pairs_noalloc: n exceeds APRIL_NOALLOC_MAX_PAIRS (4194304); "
+                                           "split the pairs or use april_filter_pairs with caller scratch");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(APRIL_ERR_INVALID_ARG, "device index out of range");
+    const april_tune t = default_tune();
+    NoAllocDevice nd;
+    {
+        // first call on this device: resolve the array's device address and
+        // the launch shape (the current device is the one being set up)
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        NoAllocDevice &slot = g_noalloc_dev[dev];
+        if (!slot.ready) {
+            uint32_t *ptr = nullptr;
+            e = cudaGetSymbolAddress((void **)&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+            int sms = 0, bps = 0;
+            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_persistent<8>, kBlock, 0);
+            if (e != cudaSuccess) return cuda_fail(e, "april_filter_pairs_noalloc set-up");
+            slot.scratch = ptr;
+            slot.num_sms = sms;
+            slot.blocks_per_sm = bps < 1 ? 1 : bps;
+            slot.ready = true;
+        }
+        nd = slot;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t *counters = nd.scratch;
+    uint32_t *status = counters + kNoAllocStatusWord;
+    uint32_t *big_list = counters + kCounterBytes / 4;
+    // the array keeps the previous call's contents: reset counters and status
+    e = cudaMemsetAsync(counters, 0, kCounterBytes, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(no-alloc counters)");
+    const DevSet dR = dev_set(R), dS = dev_set(S);
+    const unsigned grid_bin = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)nd.num_sms * 8);
+    const unsigned grid_main = (unsigned)std::max(1, nd.num_sms * nd.blocks_per_sm);
+    k_bin<<<grid_bin, 256, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, status, t.cta_threshold, big_list, counters);
+    k_persistent<8><<<grid_main, kBlock, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, status, t.cta_threshold, big_list,
+                                                  counters, t.group_window, t.cta_window);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "april_filter_pairs_noalloc launch");
     return APRIL_OK;
 }
