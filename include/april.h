@@ -64,6 +64,7 @@ typedef int32_t april_status;
 #define APRIL_MODE_PLAIN 0    /* one pair per thread, Algorithm 2 as written */
 #define APRIL_MODE_WARP 1     /* one pair per warp, windowed parallel merge */
 #define APRIL_MODE_BATCHED 2  /* length-binned persistent kernel, long pairs split over a CTA */
+#define APRIL_MODE_BATCHED_PACKED 3 /* as BATCHED, decoding the compressed lists (Sec. 5.1) while joining */
 
 /* A 2^order x 2^order grid of square cells of side 2^log2_cell lattice units
  * with lower-left corner (ox, oy) (Sec. 3.1: one global grid per data space;
@@ -113,32 +114,86 @@ void april_sets_destroy(april_sets *sets);
 typedef struct april_sets_info {
     uint32_t n_objects;
     uint32_t order;
-    uint64_t a_intervals;    /* total A intervals */
-    uint64_t f_intervals;    /* total F intervals */
-    uint64_t iv_slots;       /* interval slots in the device image (with alignment padding) */
-    uint64_t device_bytes;   /* bytes april_upload needs */
+    uint64_t a_intervals;        /* total A intervals */
+    uint64_t f_intervals;        /* total F intervals */
+    uint64_t iv_slots;           /* interval slots in the device image (with alignment padding) */
+    uint64_t device_bytes;       /* bytes april_upload needs */
+    uint32_t parts;              /* partitions per dimension (0: one global grid) */
+    uint32_t n_entries;          /* approximations: one per object, or one per (object, partition) */
+    uint32_t packed;             /* 1 after april_sets_compress */
+    uint32_t reserved;
+    uint64_t raw_list_bytes;     /* descriptors + intervals */
+    uint64_t packed_list_bytes;  /* compressed descriptors + anchors + gaps (0 if not packed) */
 } april_sets_info;
 
 april_status april_sets_get_info(const april_sets *sets, april_sets_info *info);
 
-/* Host view of one list: *iv points to 2*(*n) uint32 values st0,end0,st1,...
- * owned by the sets.  which: 0 = A-list, 1 = F-list. */
-april_status april_sets_list(const april_sets *sets, uint32_t obj, int which, const uint32_t **iv,
+/* Host view of one list of entry `entry` (the object id for sets on one
+ * grid): *iv points to 2*(*n) uint32 values st0,end0,st1,... owned by the
+ * sets.  which: 0 = A-list, 1 = F-list. */
+april_status april_sets_list(const april_sets *sets, uint32_t entry, int which, const uint32_t **iv,
                              uint32_t *n);
+
+/* Entries of object `obj`: *first .. *first + *count - 1 (one entry, the
+ * object itself, for sets on one grid). */
+april_status april_sets_object_entries(const april_sets *sets, uint32_t obj, uint32_t *first, uint32_t *count);
+
+/* Partition id and grid of an entry of partitioned sets. */
+april_status april_sets_entry_grid(const april_sets *sets, uint32_t entry, uint32_t *pid, april_grid *grid);
+
+/* Builds partitioned sets for both join inputs (Sec. 5.2, "Partitioning").
+ * The data space [0, 2^24]^2 is split into parts x parts equal partitions
+ * (parts a power of two, 1..4096).  Each polygon gets one approximation (an
+ * "entry") for every partition its closed MBR meets, on that partition's own
+ * grid of the given order.  A partition's raster area is the smallest square
+ * of power-of-two side, with its corner on a multiple of its cell side, that
+ * covers the MBRs of all polygons of R and S that meet the partition.  A
+ * candidate pair is evaluated in the partition holding the lower-left corner
+ * of MBR(r) n MBR(s) (reference-point duplicate avoidance), which
+ * april_filter_pairs and april_host_filter apply by themselves.  Polygon
+ * arguments as for april_build_sets; both sets are returned. */
+april_status april_build_partitioned_sets(const int32_t *r_xy, const uint64_t *r_vert_off, uint32_t r_n,
+                                          const int32_t *s_xy, const uint64_t *s_vert_off, uint32_t s_n,
+                                          uint32_t parts, uint32_t order, uint32_t n_threads, april_sets **out_r,
+                                          april_sets **out_s);
+
+/* Adds compressed copies of every list (Sec. 5.1, "Compression": delta
+ * encoding, decoded while joining): the endpoint sequence
+ * st_0 < end_0 < st_1 < ... of a list is cut into blocks of 32 endpoints.  A
+ * block is its first endpoint (uint32 anchor) and the 31 gaps to the next
+ * endpoints, stored as uint16 when all 31 fit, else as uint32.  The kernels
+ * of APRIL_MODE_BATCHED_PACKED decode the blocks in registers while joining.
+ * The raw lists stay available. */
+april_status april_sets_compress(april_sets *sets);
+
+/* Host view of a compressed list of n intervals: blocks[2b] is block b's
+ * anchor and blocks[2b+1] = off | wide << 31 locates its 32 gap slots at
+ * gaps + 64 * off (uint32 slots when wide, else uint16; slot 0 unused). */
+april_status april_sets_packed_list(const april_sets *sets, uint32_t entry, int which, const uint32_t **blocks,
+                                    const uint8_t **gaps, uint32_t *n);
 
 /* ------------------------------------------------------------ device sets */
 
 /* Device image of a set, as written by april_upload.
- *   desc: n_objects records of 4 uint32 {a_off, a_len, f_off, f_len};
+ *   desc: n_entries records of 4 uint32 {a_off, a_len, f_off, f_len};
  *         offsets count intervals from iv and are even (16-byte aligned).
  *   iv:   iv_slots intervals of 2 uint32 {st, end}.
- * Both pointers are device addresses inside the caller's buffer. */
+ *   The partition and compressed arrays are set when the sets have them,
+ *   else NULL.  All pointers are device addresses inside the caller's buffer. */
 typedef struct april_dev_sets {
-    const uint32_t *desc;
-    const uint32_t *iv;
+    const uint32_t *desc;       /* per entry {a_off, a_len, f_off, f_len} */
+    const uint32_t *iv;         /* intervals {st, end} */
     uint32_t n_objects;
     uint32_t order;
     uint64_t iv_slots;
+    uint32_t n_entries;         /* entries (== n_objects on one grid) */
+    uint32_t parts;             /* partitions per dimension, 0 = one grid */
+    const int32_t *obj_ll;      /* parts > 0: per object (x0, y0), lower-left MBR corner */
+    const uint32_t *obj_entry;  /* parts > 0: n_objects + 1 entry offsets */
+    const uint32_t *entry_pid;  /* parts > 0: partition id of every entry */
+    const uint32_t *pdesc;      /* compressed: per entry {a_block, a_len, f_block, f_len} */
+    const uint32_t *anchors;    /* compressed: block table, per block {anchor, gap_off64 | wide << 31} */
+    const uint8_t *gaps;        /* compressed: gap blocks (64 or 128 bytes each) */
 } april_dev_sets;
 
 /* Copies the sets into a caller-allocated device buffer of at least
@@ -187,8 +242,10 @@ april_status april_autotune(april_ctx *ctx, const april_dev_sets *R, const april
 /* ------------------------------------------------------------------ filter */
 
 /* Device scratch (bytes) april_filter_pairs needs for `mode` and n pairs.
- * PLAIN and WARP need none; BATCHED needs 256 bytes of work counters plus
- * 4 bytes per pair for the list of long pairs. */
+ * PLAIN and WARP need none; BATCHED and BATCHED_PACKED need 256 bytes of
+ * work counters plus 12 bytes per pair (the list of long pairs and, for
+ * partitioned sets, each pair's two routed entries), each part rounded up to
+ * 256 bytes. */
 april_status april_filter_scratch_bytes(int mode, uint64_t n, size_t *bytes);
 
 /* Runs the APRIL intermediate filter (Algorithm 2) on n candidate pairs.
@@ -198,7 +255,12 @@ april_status april_filter_scratch_bytes(int mode, uint64_t n, size_t *bytes);
  *   d_verdict  device array of n bytes; receives APRIL_TRUE_NEGATIVE,
  *              APRIL_TRUE_HIT, APRIL_INCONCLUSIVE, or APRIL_VERDICT_ERROR for
  *              a pair with an out-of-range id.
- *   mode       APRIL_MODE_PLAIN / _WARP / _BATCHED.
+ *   mode       APRIL_MODE_PLAIN / _WARP / _BATCHED / _BATCHED_PACKED.  Partitioned
+ *              sets (april_build_partitioned_sets) need one of the BATCHED
+ *              modes: each pair is first routed to the partition of the
+ *              lower-left corner of MBR(r) n MBR(s) (Sec. 5.2).  BATCHED_PACKED
+ *              needs compressed sets (april_sets_compress) and joins with
+ *              whole warps (groups of 32 lanes) and CTAs.
  *   d_scratch  device scratch of april_filter_scratch_bytes() bytes
  *              (256-byte aligned), or NULL when that is 0.
  *   stream     cudaStream_t (void*); all work is enqueued on it.

@@ -23,7 +23,7 @@ ERRORS = {
     -5: "DEVICE_TIMEOUT", -6: "CANCELLED", -7: "NO_MEMORY", -8: "GEOMETRY",
 }
 TRUE_NEGATIVE, TRUE_HIT, INCONCLUSIVE, VERDICT_ERROR = 0, 1, 2, 0xFF
-MODE_PLAIN, MODE_WARP, MODE_BATCHED = 0, 1, 2
+MODE_PLAIN, MODE_WARP, MODE_BATCHED, MODE_BATCHED_PACKED = 0, 1, 2, 3
 MODES = {"plain": MODE_PLAIN, "warp": MODE_WARP, "batched": MODE_BATCHED}
 
 
@@ -41,7 +41,10 @@ class april_grid(ctypes.Structure):
 class april_sets_info(ctypes.Structure):
     _fields_ = [("n_objects", ctypes.c_uint32), ("order", ctypes.c_uint32),
                 ("a_intervals", ctypes.c_uint64), ("f_intervals", ctypes.c_uint64),
-                ("iv_slots", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64)]
+                ("iv_slots", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
+                ("parts", ctypes.c_uint32), ("n_entries", ctypes.c_uint32), ("packed", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("raw_list_bytes", ctypes.c_uint64),
+                ("packed_list_bytes", ctypes.c_uint64)]
 
 
 class april_tune(ctypes.Structure):
@@ -55,7 +58,10 @@ class april_tune(ctypes.Structure):
 
 class april_dev_sets(ctypes.Structure):
     _fields_ = [("desc", ctypes.c_void_p), ("iv", ctypes.c_void_p), ("n_objects", ctypes.c_uint32),
-                ("order", ctypes.c_uint32), ("iv_slots", ctypes.c_uint64)]
+                ("order", ctypes.c_uint32), ("iv_slots", ctypes.c_uint64), ("n_entries", ctypes.c_uint32),
+                ("parts", ctypes.c_uint32), ("obj_ll", ctypes.c_void_p), ("obj_entry", ctypes.c_void_p),
+                ("entry_pid", ctypes.c_void_p), ("pdesc", ctypes.c_void_p), ("anchors", ctypes.c_void_p),
+                ("gaps", ctypes.c_void_p)]
 
 
 _vp = ctypes.c_void_p
@@ -82,6 +88,13 @@ SIGNATURES = {
     "april_filter_pairs_host": (_st, [_vp, ctypes.POINTER(april_dev_sets), ctypes.POINTER(april_dev_sets), _vp, _vp,
                                       _u64, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
     "april_host_filter": (_st, [_vp, _vp, _vp, _vp, _u64, _u32, _vp, _vp]),
+    "april_sets_object_entries": (_st, [_vp, _u32, ctypes.POINTER(_u32), ctypes.POINTER(_u32)]),
+    "april_sets_entry_grid": (_st, [_vp, _u32, ctypes.POINTER(_u32), ctypes.POINTER(april_grid)]),
+    "april_build_partitioned_sets": (_st, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _u32, ctypes.POINTER(_vp),
+                                           ctypes.POINTER(_vp)]),
+    "april_sets_compress": (_st, [_vp]),
+    "april_sets_packed_list": (_st, [_vp, _u32, ctypes.c_int, ctypes.POINTER(ctypes.POINTER(_u32)),
+                                     ctypes.POINTER(ctypes.POINTER(ctypes.c_uint8)), ctypes.POINTER(_u32)]),
     "april_filter_pairs_noalloc": (_st, [ctypes.POINTER(april_dev_sets), ctypes.POINTER(april_dev_sets), _vp, _vp,
                                          _u64, _vp, _vp]),
     "april_set_tune": (_st, [_vp, ctypes.POINTER(april_tune)]),
@@ -156,8 +169,43 @@ class Sets:
         check(load().april_sets_get_info(self.handle, ctypes.byref(inf)))
         return inf
 
+    def entries(self, obj: int):
+        """(first, count) of the object's entries."""
+        f, c = _u32(), _u32()
+        check(load().april_sets_object_entries(self.handle, obj, ctypes.byref(f), ctypes.byref(c)))
+        return f.value, c.value
+
+    def entry_grid(self, entry: int):
+        """(partition id, april_grid) of an entry of partitioned sets."""
+        pid, g = _u32(), april_grid()
+        check(load().april_sets_entry_grid(self.handle, entry, ctypes.byref(pid), ctypes.byref(g)))
+        return pid.value, g
+
+    def compress(self) -> None:
+        check(load().april_sets_compress(self.handle))
+
+    def packed_list(self, entry: int, which: int):
+        """(n, [(anchor, wide, gap slots uint8[64 or 128]) per block]) of a compressed list."""
+        b = ctypes.POINTER(_u32)()
+        g = ctypes.POINTER(ctypes.c_uint8)()
+        n = _u32()
+        check(load().april_sets_packed_list(self.handle, entry, which, ctypes.byref(b), ctypes.byref(g),
+                                            ctypes.byref(n)))
+        nb = (2 * n.value + 31) // 32
+        table = np.ctypeslib.as_array(b, shape=(2 * nb,)).reshape(nb, 2).copy() if nb else np.zeros((0, 2), np.uint32)
+        base = ctypes.addressof(g.contents) if nb else 0
+        out = []
+        for anchor, meta in table:
+            wide = int(meta) >> 31
+            off = int(meta) & 0x7FFFFFFF
+            size = 128 if wide else 64
+            slots = np.ctypeslib.as_array((ctypes.c_uint8 * size).from_address(base + 64 * off)).copy()
+            out.append((int(anchor), wide, slots))
+        return n.value, out
+
     def list(self, obj: int, which: int) -> np.ndarray:
-        """(n, 2) uint32 array [st, end) of the A (which=0) or F (1) list."""
+        """(n, 2) uint32 array [st, end) of the A (which=0) or F (1) list of an
+        entry (the object itself for sets on one grid)."""
         p = ctypes.POINTER(_u32)()
         n = _u32()
         check(load().april_sets_list(self.handle, obj, which, ctypes.byref(p), ctypes.byref(n)))
@@ -173,6 +221,18 @@ def april_build_sets(xy: np.ndarray, vert_off: np.ndarray, grd: april_grid, n_th
     check(load().april_build_sets(_ptr(xy32), _ptr(off), len(off) - 1, ctypes.byref(grd), n_threads,
                                   ctypes.byref(h)))
     return Sets(h.value)
+
+
+def april_build_partitioned_sets(R_xy, R_off, S_xy, S_off, parts: int, order: int, n_threads: int = 0):
+    rxy = np.ascontiguousarray(R_xy, dtype=np.int32).reshape(-1)
+    sxy = np.ascontiguousarray(S_xy, dtype=np.int32).reshape(-1)
+    roff = np.ascontiguousarray(R_off, dtype=np.uint64)
+    soff = np.ascontiguousarray(S_off, dtype=np.uint64)
+    hr, hs = _vp(), _vp()
+    check(load().april_build_partitioned_sets(_ptr(rxy), _ptr(roff), len(roff) - 1, _ptr(sxy), _ptr(soff),
+                                              len(soff) - 1, parts, order, n_threads, ctypes.byref(hr),
+                                              ctypes.byref(hs)))
+    return Sets(hr.value), Sets(hs.value)
 
 
 @dataclass

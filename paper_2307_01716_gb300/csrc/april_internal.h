@@ -15,16 +15,59 @@ april_status fail(april_status code, const std::string &msg);
 
 }  // namespace april
 
-// Host-side sets: per-object descriptors and the interval slots exactly as
-// they are laid out in device memory by april_upload.
+// Host-side sets: per-entry descriptors and the interval slots exactly as
+// they are laid out in device memory by april_upload.  An entry is one
+// object's approximation on one grid: for sets built on one global grid the
+// entries are the objects; for partitioned sets (Sec. 5.2) an object has one
+// entry per partition its MBR meets.
 struct april_sets {
-    uint32_t n = 0;
+    uint32_t n = 0;          // objects
     uint32_t order = 0;
+    uint32_t parts = 0;      // partitions per dimension (0: one global grid)
+    uint32_t n_entries = 0;  // == n when parts == 0
     uint64_t a_total = 0;
     uint64_t f_total = 0;
-    std::vector<uint32_t> desc;  // 4 per object: a_off, a_len, f_off, f_len (in intervals)
-    std::vector<uint32_t> iv;    // 2 per slot: st, end
+    std::vector<uint32_t> desc;       // 4 per entry: a_off, a_len, f_off, f_len (in intervals)
+    std::vector<uint32_t> iv;         // 2 per slot: st, end
+    std::vector<int32_t> obj_ll;      // parts > 0: 2 per object, lower-left corner of its MBR
+    std::vector<uint32_t> obj_entry;  // parts > 0: n + 1 entry offsets (entries of an object are contiguous)
+    std::vector<uint32_t> entry_pid;  // parts > 0: partition id of each entry (ascending within an object)
+    std::vector<int64_t> part_grid;   // parts > 0: 4 per partition: ox, oy, log2_cell, used(0/1)
+    // compressed lists (Sec. 5.1), see april_sets_compress
+    bool packed = false;
+    std::vector<uint32_t> pdesc;      // 4 per entry: {a_block, a_len, f_block, f_len} (block-table indices)
+    std::vector<uint32_t> anchors;    // block table, 2 per block: {anchor, gap_off64 | wide << 31}
+    std::vector<uint8_t> gaps;        // per block 32 gap slots (slot 0 unused): 64 B (uint16) or 128 B (uint32)
 };
 
-// Device image layout: [desc (16 B per object)] [pad to 256 B] [iv (8 B per slot)]
-inline uint64_t april_desc_bytes(uint32_t n) { return ((uint64_t)n * 16 + 255) / 256 * 256; }
+inline uint64_t april_round256(uint64_t b) { return (b + 255) / 256 * 256; }
+
+// Device image layout (each section starts 256-byte aligned):
+//   desc (16 B/entry) | iv (8 B/slot) | obj_ll (8 B/object) | obj_entry (4 B x (n+1))
+//   | entry_pid (4 B/entry) | pdesc (16 B/entry) | block table (8 B/block) | gaps
+struct april_image_layout {
+    uint64_t desc, iv, obj_ll, obj_entry, entry_pid, pdesc, anchors, gaps, total;
+};
+
+inline april_image_layout april_layout(const april_sets &S) {
+    april_image_layout L{};
+    uint64_t o = 0;
+    L.desc = o;
+    o += april_round256((uint64_t)S.n_entries * 16);
+    L.iv = o;
+    o += april_round256((uint64_t)S.iv.size() * 4);
+    L.obj_ll = o;
+    o += april_round256((uint64_t)S.obj_ll.size() * 4);
+    L.obj_entry = o;
+    o += april_round256((uint64_t)S.obj_entry.size() * 4);
+    L.entry_pid = o;
+    o += april_round256((uint64_t)S.entry_pid.size() * 4);
+    L.pdesc = o;
+    o += april_round256((uint64_t)S.pdesc.size() * 4);
+    L.anchors = o;
+    o += april_round256((uint64_t)S.anchors.size() * 4);
+    L.gaps = o;
+    o += april_round256((uint64_t)S.gaps.size());
+    L.total = o;
+    return L;
+}

@@ -345,6 +345,58 @@ uint32_t resolve_threads(uint32_t n) {
     return n ? n : std::max(1u, std::thread::hardware_concurrency());
 }
 
+
+// Lays out per-entry lists as the device image: each list starts at an even
+// interval slot (16-byte aligned), and the entry descriptors point at them.
+april_status assemble_lists(april_sets *S, const std::vector<PolyLists> &lists, uint32_t nt) {
+    const size_t E = lists.size();
+    S->desc.assign(E * 4, 0u);
+    uint64_t slot = 0;
+    S->a_total = S->f_total = 0;
+    for (size_t p = 0; p < E; ++p) {
+        uint64_t na = lists[p].A.size() / 2, nf = lists[p].F.size() / 2;
+        S->desc[4 * p + 0] = (uint32_t)slot;
+        S->desc[4 * p + 1] = (uint32_t)na;
+        slot += (na + 1) & ~1ull;
+        S->desc[4 * p + 2] = (uint32_t)slot;
+        S->desc[4 * p + 3] = (uint32_t)nf;
+        slot += (nf + 1) & ~1ull;
+        S->a_total += na;
+        S->f_total += nf;
+        if (slot > 0xFFFFFFF0ull) return fail(APRIL_ERR_INVALID_ARG, "more than 2^32 interval slots in one set");
+    }
+    S->iv.assign((size_t)slot * 2, 0u);
+    parallel_for(E, nt, 256, [&](uint32_t, uint64_t b, uint64_t e) {
+        for (uint64_t p = b; p < e; ++p) {
+            const auto &L = lists[p];
+            if (!L.A.empty()) std::memcpy(&S->iv[2 * (size_t)S->desc[4 * p + 0]], L.A.data(), L.A.size() * 4);
+            if (!L.F.empty()) std::memcpy(&S->iv[2 * (size_t)S->desc[4 * p + 2]], L.F.data(), L.F.size() * 4);
+        }
+    });
+    return APRIL_OK;
+}
+
+struct Mbr {
+    int64_t x0, y0, x1, y1;
+};
+
+Mbr poly_mbr(const int32_t *xy, uint64_t nv) {
+    Mbr m{xy[0], xy[1], xy[0], xy[1]};
+    for (uint64_t k = 1; k < nv; ++k) {
+        m.x0 = std::min<int64_t>(m.x0, xy[2 * k]);
+        m.y0 = std::min<int64_t>(m.y0, xy[2 * k + 1]);
+        m.x1 = std::max<int64_t>(m.x1, xy[2 * k]);
+        m.y1 = std::max<int64_t>(m.y1, xy[2 * k + 1]);
+    }
+    return m;
+}
+
+// Closed partition squares [k*side, (k+1)*side] met by the closed range [lo, hi].
+inline void part_range(int64_t lo, int64_t hi, int64_t side, int64_t parts, int64_t &k0, int64_t &k1) {
+    k0 = std::max<int64_t>(ceil_div(lo, side) - 1, 0);
+    k1 = std::min<int64_t>(floor_div(hi, side), parts - 1);
+}
+
 }  // namespace
 
 }  // namespace april
@@ -393,34 +445,13 @@ extern "C" april_status april_build_sets(const int32_t *xy, const uint64_t *vert
         }
         auto *S = new april_sets();
         S->n = n_polys;
+        S->n_entries = n_polys;
         S->order = g.order;
-        S->desc.resize((size_t)n_polys * 4);
-        uint64_t slot = 0;
-        for (uint32_t p = 0; p < n_polys; ++p) {
-            uint64_t na = lists[p].A.size() / 2, nf = lists[p].F.size() / 2;
-            S->desc[4 * (size_t)p + 0] = (uint32_t)slot;
-            S->desc[4 * (size_t)p + 1] = (uint32_t)na;
-            slot += (na + 1) & ~1ull;  // next list starts 16-byte aligned
-            S->desc[4 * (size_t)p + 2] = (uint32_t)slot;
-            S->desc[4 * (size_t)p + 3] = (uint32_t)nf;
-            slot += (nf + 1) & ~1ull;
-            S->a_total += na;
-            S->f_total += nf;
-            if (slot > 0xFFFFFFF0ull) {
-                delete S;
-                return fail(APRIL_ERR_INVALID_ARG, "more than 2^32 interval slots in one set");
-            }
+        st = assemble_lists(S, lists, nt);
+        if (st) {
+            delete S;
+            return st;
         }
-        S->iv.assign((size_t)slot * 2, 0u);
-        parallel_for(n_polys, nt, 256, [&](uint32_t, uint64_t b, uint64_t e) {
-            for (uint64_t p = b; p < e; ++p) {
-                const auto &L = lists[p];
-                if (!L.A.empty())
-                    std::memcpy(&S->iv[2 * (size_t)S->desc[4 * p + 0]], L.A.data(), L.A.size() * 4);
-                if (!L.F.empty())
-                    std::memcpy(&S->iv[2 * (size_t)S->desc[4 * p + 2]], L.F.data(), L.F.size() * 4);
-            }
-        });
         *out = S;
         return APRIL_OK;
     } catch (const std::bad_alloc &) {
@@ -432,23 +463,246 @@ extern "C" void april_sets_destroy(april_sets *sets) { delete sets; }
 
 extern "C" april_status april_sets_get_info(const april_sets *S, april_sets_info *info) {
     if (!S || !info) return fail(APRIL_ERR_INVALID_ARG, "NULL argument");
+    const april_image_layout L = april_layout(*S);
     info->n_objects = S->n;
     info->order = S->order;
     info->a_intervals = S->a_total;
     info->f_intervals = S->f_total;
     info->iv_slots = S->iv.size() / 2;
-    info->device_bytes = april_desc_bytes(S->n) + (uint64_t)S->iv.size() * 4;
+    info->device_bytes = L.total;
+    info->parts = S->parts;
+    info->n_entries = S->n_entries;
+    info->packed = S->packed ? 1u : 0u;
+    info->reserved = 0;
+    info->raw_list_bytes = (uint64_t)S->n_entries * 16 + (uint64_t)S->iv.size() * 4;
+    info->packed_list_bytes = S->packed ? (uint64_t)S->pdesc.size() * 4 + (uint64_t)S->anchors.size() * 4 +
+                                              (uint64_t)S->gaps.size()
+                                        : 0;
     return APRIL_OK;
 }
 
-extern "C" april_status april_sets_list(const april_sets *S, uint32_t obj, int which, const uint32_t **iv,
+extern "C" april_status april_sets_list(const april_sets *S, uint32_t entry, int which, const uint32_t **iv,
                                         uint32_t *n) {
     if (!S || !iv || !n || (which != 0 && which != 1)) return fail(APRIL_ERR_INVALID_ARG, "bad argument");
-    if (obj >= S->n) return fail(APRIL_ERR_OUT_OF_RANGE_ID, "object id out of range");
-    uint32_t off = S->desc[4 * (size_t)obj + 2 * which], len = S->desc[4 * (size_t)obj + 2 * which + 1];
+    if (entry >= S->n_entries) return fail(APRIL_ERR_OUT_OF_RANGE_ID, "entry out of range");
+    uint32_t off = S->desc[4 * (size_t)entry + 2 * which], len = S->desc[4 * (size_t)entry + 2 * which + 1];
     *iv = S->iv.data() + 2 * (size_t)off;
     *n = len;
     return APRIL_OK;
+}
+
+extern "C" april_status april_sets_object_entries(const april_sets *S, uint32_t obj, uint32_t *first,
+                                                  uint32_t *count) {
+    if (!S || !first || !count) return fail(APRIL_ERR_INVALID_ARG, "NULL argument");
+    if (obj >= S->n) return fail(APRIL_ERR_OUT_OF_RANGE_ID, "object id out of range");
+    if (S->parts == 0) {
+        *first = obj;
+        *count = 1;
+    } else {
+        *first = S->obj_entry[obj];
+        *count = S->obj_entry[obj + 1] - S->obj_entry[obj];
+    }
+    return APRIL_OK;
+}
+
+extern "C" april_status april_sets_entry_grid(const april_sets *S, uint32_t entry, uint32_t *pid, april_grid *grid) {
+    if (!S || !pid || !grid) return fail(APRIL_ERR_INVALID_ARG, "NULL argument");
+    if (entry >= S->n_entries) return fail(APRIL_ERR_OUT_OF_RANGE_ID, "entry out of range");
+    if (S->parts == 0) return fail(APRIL_ERR_INVALID_ARG, "sets are not partitioned");
+    const uint32_t p = S->entry_pid[entry];
+    *pid = p;
+    grid->ox = S->part_grid[4 * (size_t)p];
+    grid->oy = S->part_grid[4 * (size_t)p + 1];
+    grid->log2_cell = (uint32_t)S->part_grid[4 * (size_t)p + 2];
+    grid->order = S->order;
+    return APRIL_OK;
+}
+
+extern "C" april_status april_sets_packed_list(const april_sets *S, uint32_t entry, int which,
+                                               const uint32_t **blocks, const uint8_t **gaps, uint32_t *n) {
+    if (!S || !blocks || !gaps || !n || (which != 0 && which != 1)) return fail(APRIL_ERR_INVALID_ARG, "bad argument");
+    if (!S->packed) return fail(APRIL_ERR_INVALID_ARG, "sets are not compressed");
+    if (entry >= S->n_entries) return fail(APRIL_ERR_OUT_OF_RANGE_ID, "entry out of range");
+    *blocks = S->anchors.data() + 2 * (size_t)S->pdesc[4 * (size_t)entry + 2 * which];
+    *gaps = S->gaps.data();
+    *n = S->pdesc[4 * (size_t)entry + 2 * which + 1];
+    return APRIL_OK;
+}
+
+// Partitioned sets (Sec. 5.2).  The data space [0, 2^24]^2 is split into
+// parts x parts equal partitions.  An object is approximated once for every
+// partition its (closed) MBR meets, on that partition's own grid of `order`.
+// The partition's raster area is the smallest square of power-of-two side
+// whose corner is a multiple of its cell side and which covers the MBRs of all
+// objects of both inputs that meet the partition (the paper defines it by
+// "the MBR of these objects").
+extern "C" april_status april_build_partitioned_sets(const int32_t *r_xy, const uint64_t *r_off, uint32_t r_n,
+                                                     const int32_t *s_xy, const uint64_t *s_off, uint32_t s_n,
+                                                     uint32_t parts, uint32_t order, uint32_t n_threads,
+                                                     april_sets **out_r, april_sets **out_s) {
+    if (!out_r || !out_s) return fail(APRIL_ERR_INVALID_ARG, "out is NULL");
+    *out_r = *out_s = nullptr;
+    if ((r_n && (!r_xy || !r_off)) || (s_n && (!s_xy || !s_off))) return fail(APRIL_ERR_INVALID_ARG, "NULL polygons");
+    if (parts < 1 || parts > 4096 || (parts & (parts - 1)))
+        return fail(APRIL_ERR_INVALID_ARG, "parts must be a power of two in [1, 4096]");
+    if (order < 1 || order > 16) return fail(APRIL_ERR_INVALID_ARG, "order must be 1..16");
+    const int64_t L = (int64_t)1 << 24, side = L / parts;
+    const uint32_t nt = resolve_threads(n_threads);
+    try {
+        const int32_t *xys[2] = {r_xy, s_xy};
+        const uint64_t *offs[2] = {r_off, s_off};
+        const uint32_t ns[2] = {r_n, s_n};
+        std::vector<Mbr> mbr[2];
+        for (int side_i = 0; side_i < 2; ++side_i) {
+            mbr[side_i].resize(ns[side_i]);
+            for (uint32_t p = 0; p < ns[side_i]; ++p) {
+                const uint64_t nv = offs[side_i][p + 1] - offs[side_i][p];
+                if (offs[side_i][p + 1] < offs[side_i][p] || nv < 3)
+                    return fail(APRIL_ERR_GEOMETRY, "polygon with fewer than 3 vertices");
+                Mbr m = poly_mbr(xys[side_i] + 2 * offs[side_i][p], nv);
+                if (m.x0 < 0 || m.y0 < 0 || m.x1 > L || m.y1 > L)
+                    return fail(APRIL_ERR_GEOMETRY, "polygon outside the data space [0, 2^24]^2");
+                mbr[side_i][p] = m;
+            }
+        }
+        // bounds of every partition's members
+        const size_t P = (size_t)parts * parts;
+        std::vector<int64_t> lo_x(P, INT64_MAX), lo_y(P, INT64_MAX), hi_x(P, INT64_MIN), hi_y(P, INT64_MIN);
+        for (int side_i = 0; side_i < 2; ++side_i)
+            for (const Mbr &m : mbr[side_i]) {
+                int64_t kx0, kx1, ky0, ky1;
+                part_range(m.x0, m.x1, side, parts, kx0, kx1);
+                part_range(m.y0, m.y1, side, parts, ky0, ky1);
+                for (int64_t ky = ky0; ky <= ky1; ++ky)
+                    for (int64_t kx = kx0; kx <= kx1; ++kx) {
+                        const size_t q = (size_t)(ky * parts + kx);
+                        lo_x[q] = std::min(lo_x[q], m.x0);
+                        lo_y[q] = std::min(lo_y[q], m.y0);
+                        hi_x[q] = std::max(hi_x[q], m.x1);
+                        hi_y[q] = std::max(hi_y[q], m.y1);
+                    }
+            }
+        std::vector<int64_t> grid_desc(4 * P, 0);
+        std::vector<GridI> grids(P);
+        for (size_t q = 0; q < P; ++q) {
+            if (lo_x[q] == INT64_MAX) continue;
+            for (uint32_t k = order + 1; k < 40; ++k) {
+                const int64_t size = (int64_t)1 << k, h = size >> order;
+                const int64_t ox = floor_div(lo_x[q], h) * h, oy = floor_div(lo_y[q], h) * h;
+                if (ox + size >= hi_x[q] && oy + size >= hi_y[q]) {
+                    grids[q] = GridI{ox, oy, h, order, (int64_t)1 << order};
+                    grid_desc[4 * q] = ox;
+                    grid_desc[4 * q + 1] = oy;
+                    grid_desc[4 * q + 2] = (int64_t)(k - order);
+                    grid_desc[4 * q + 3] = 1;
+                    break;
+                }
+            }
+        }
+        april_sets *out[2] = {nullptr, nullptr};
+        for (int side_i = 0; side_i < 2; ++side_i) {
+            auto *S = new april_sets();
+            S->n = ns[side_i];
+            S->order = order;
+            S->parts = parts;
+            S->part_grid = grid_desc;
+            S->obj_ll.resize(2 * (size_t)S->n);
+            S->obj_entry.assign((size_t)S->n + 1, 0u);
+            std::vector<uint32_t> ent_obj;
+            for (uint32_t p = 0; p < S->n; ++p) {
+                const Mbr &m = mbr[side_i][p];
+                S->obj_ll[2 * (size_t)p] = (int32_t)m.x0;
+                S->obj_ll[2 * (size_t)p + 1] = (int32_t)m.y0;
+                int64_t kx0, kx1, ky0, ky1;
+                part_range(m.x0, m.x1, side, parts, kx0, kx1);
+                part_range(m.y0, m.y1, side, parts, ky0, ky1);
+                for (int64_t ky = ky0; ky <= ky1; ++ky)
+                    for (int64_t kx = kx0; kx <= kx1; ++kx) {
+                        S->entry_pid.push_back((uint32_t)(ky * parts + kx));
+                        ent_obj.push_back(p);
+                    }
+                S->obj_entry[(size_t)p + 1] = (uint32_t)S->entry_pid.size();
+            }
+            S->n_entries = (uint32_t)S->entry_pid.size();
+            std::vector<PolyLists> lists(S->n_entries);
+            std::vector<Scratch> scratch(nt);
+            std::atomic<int> err{0};
+            parallel_for(S->n_entries, nt, 64, [&](uint32_t tid, uint64_t b, uint64_t e) {
+                for (uint64_t q = b; q < e && !err.load(std::memory_order_relaxed); ++q) {
+                    const uint32_t p = ent_obj[q];
+                    const uint64_t o = offs[side_i][p];
+                    april_status st = build_one(xys[side_i] + 2 * o, offs[side_i][p + 1] - o,
+                                                grids[S->entry_pid[q]], scratch[tid], lists[q]);
+                    if (st) {
+                        int zero = 0;
+                        err.compare_exchange_strong(zero, st);
+                    }
+                }
+            });
+            april_status st = err.load() ? (april_status)err.load() : assemble_lists(S, lists, nt);
+            if (st) {
+                delete S;
+                if (out[0]) delete out[0];
+                return st;
+            }
+            out[side_i] = S;
+        }
+        *out_r = out[0];
+        *out_s = out[1];
+        return APRIL_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(APRIL_ERR_NO_MEMORY, "host allocation failed while building partitioned sets");
+    }
+}
+
+// Compressed lists (Sec. 5.1: delta encoding, decoded while joining).  A list
+// of n intervals is the strictly increasing endpoint sequence
+// st_0 < end_0 < st_1 < ... (lists are maximal, so end_i < st_{i+1}), cut into
+// blocks of 32 endpoints.  Each block has an 8-byte table entry {anchor = its
+// first endpoint, offset of its gap block in 64-byte units | wide << 31} and
+// a gap block of 32 slots (slot 0 unused) holding the 31 gaps to the
+// following endpoints: uint16 slots (64 bytes) when all 31 gaps fit, else
+// uint32 slots (128 bytes).  Gaps are taken mod 2^32, so an end stored as 0
+// (2^32) decodes back to 0.
+extern "C" april_status april_sets_compress(april_sets *S) {
+    if (!S) return fail(APRIL_ERR_INVALID_ARG, "sets is NULL");
+    if (S->packed) return APRIL_OK;
+    try {
+        S->pdesc.assign((size_t)S->n_entries * 4, 0u);
+        S->anchors.clear();
+        S->gaps.clear();
+        for (uint32_t e = 0; e < S->n_entries; ++e) {
+            for (int which = 0; which < 2; ++which) {
+                const uint32_t off = S->desc[4 * (size_t)e + 2 * which], n = S->desc[4 * (size_t)e + 2 * which + 1];
+                const uint32_t *v = &S->iv[2 * (size_t)off];  // endpoints v[0 .. 2n)
+                const uint32_t ne = 2 * n, nb = (ne + 31) / 32;
+                S->pdesc[4 * (size_t)e + 2 * which] = (uint32_t)(S->anchors.size() / 2);
+                S->pdesc[4 * (size_t)e + 2 * which + 1] = n;
+                for (uint32_t b = 0; b < nb; ++b) {
+                    bool wide = false;
+                    for (uint32_t k = 1; k < 32 && 32 * b + k < ne; ++k)
+                        if ((uint32_t)(v[32 * b + k] - v[32 * b + k - 1]) > 0xFFFFu) wide = true;
+                    const size_t base = S->gaps.size();
+                    if (base / 64 > 0x7FFFFFF0ull) return fail(APRIL_ERR_INVALID_ARG, "gap stream too large");
+                    S->anchors.push_back(v[32 * b]);
+                    S->anchors.push_back((uint32_t)(base / 64) | (wide ? 0x80000000u : 0u));
+                    S->gaps.resize(base + (wide ? 128 : 64), 0);
+                    for (uint32_t k = 1; k < 32 && 32 * b + k < ne; ++k) {
+                        const uint32_t g = v[32 * b + k] - v[32 * b + k - 1];
+                        if (wide) std::memcpy(&S->gaps[base + 4 * k], &g, 4);
+                        else {
+                            const uint16_t g16 = (uint16_t)g;
+                            std::memcpy(&S->gaps[base + 2 * k], &g16, 2);
+                        }
+                    }
+                }
+            }
+        }
+        S->packed = true;
+        return APRIL_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(APRIL_ERR_NO_MEMORY, "host allocation failed while compressing");
+    }
 }
 
 namespace {
@@ -473,16 +727,34 @@ bool host_join(const uint32_t *X, uint32_t nx, const uint32_t *Y, uint32_t ny, u
 
 }  // namespace
 
+// Entry of object `obj` for partition `pid` (Sec. 5.2 routing), or UINT32_MAX.
+static uint32_t find_entry(const april_sets *S, uint32_t obj, uint32_t pid) {
+    for (uint32_t e = S->obj_entry[obj]; e < S->obj_entry[obj + 1]; ++e)
+        if (S->entry_pid[e] == pid) return e;
+    return 0xffffffffu;
+}
+
 extern "C" april_status april_host_filter(const april_sets *R, const april_sets *S, const uint32_t *pr,
                                           const uint32_t *ps, uint64_t n, uint32_t n_threads, uint8_t *verdict,
                                           uint64_t *consumed) {
     if (!R || !S || (n && (!pr || !ps || !verdict))) return fail(APRIL_ERR_INVALID_ARG, "NULL argument");
+    if (R->parts != S->parts || R->order != S->order) return fail(APRIL_ERR_INVALID_ARG, "R and S use different grids");
+    const int64_t side = R->parts ? ((int64_t)1 << 24) / R->parts : 0;
     parallel_for(n, resolve_threads(n_threads), 4096, [&](uint32_t, uint64_t b, uint64_t e) {
         for (uint64_t k = b; k < e; ++k) {
             uint32_t r = pr[k], s = ps[k];
             uint64_t used = 0;
             uint8_t v;
-            if (r >= R->n || s >= S->n) {
+            if (r < R->n && s < S->n && R->parts) {
+                // evaluate the pair in the partition of the lower-left corner of MBR(r) n MBR(s)
+                const int64_t x = std::max(R->obj_ll[2 * (size_t)r], S->obj_ll[2 * (size_t)s]);
+                const int64_t y = std::max(R->obj_ll[2 * (size_t)r + 1], S->obj_ll[2 * (size_t)s + 1]);
+                const int64_t P = R->parts;
+                const uint32_t pid = (uint32_t)(std::min(y / side, P - 1) * P + std::min(x / side, P - 1));
+                r = find_entry(R, r, pid);
+                s = find_entry(S, s, pid);
+            }
+            if (r >= R->n_entries || s >= S->n_entries) {
                 v = APRIL_VERDICT_ERROR;
             } else {
                 const uint32_t *dr = &R->desc[4 * (size_t)r], *ds = &S->desc[4 * (size_t)s];

@@ -59,6 +59,42 @@ static_assert(kWarpBuf % 2 == 0 && kCtaBuf % 2 == 0, "buffers must stay 16-byte 
 constexpr uint32_t C_BIG_COUNT = 0, C_BIG_HEAD = 1, C_CHUNK_HEAD = 2;
 constexpr size_t kCounterBytes = 256;
 
+__device__ __forceinline__ uint4 shfl4(const uint4 &v, uint32_t src) {
+    return make_uint4(__shfl_sync(kFull, v.x, src), __shfl_sync(kFull, v.y, src), __shfl_sync(kFull, v.z, src),
+                      __shfl_sync(kFull, v.w, src));
+}
+
+// Entry-level views of a set for the warp and CTA joins.  RawSets reads the
+// interval lists; PackedSets reads the compressed lists of Sec. 5.1.
+struct RawSets {
+    static constexpr bool kPacked = false;
+    DevSet s;
+    using Desc = uint4;  // {a_off, a_len, f_off, f_len}
+    __device__ __forceinline__ uint32_t n() const { return s.n; }
+    __device__ __forceinline__ Desc load(uint32_t e) const { return __ldg(s.desc + e); }
+    static __device__ __forceinline__ uint32_t a_len(const Desc &d) { return d.y; }
+    static __device__ __forceinline__ Desc shfl(const Desc &d, uint32_t src) { return shfl4(d, src); }
+    __device__ __forceinline__ RawList list(const Desc &d, bool f) const {
+        return f ? RawList{s.iv + d.z, d.w} : RawList{s.iv + d.x, d.y};
+    }
+};
+
+struct PackedSets {
+    static constexpr bool kPacked = true;
+    const uint4 *pdesc;    // per entry {a_block, a_len, f_block, f_len}
+    const uint2 *blocks;   // block table {anchor, gap_off64 | wide << 31}
+    const uint8_t *gaps;
+    uint32_t nent;
+    using Desc = uint4;
+    __device__ __forceinline__ uint32_t n() const { return nent; }
+    __device__ __forceinline__ Desc load(uint32_t e) const { return __ldg(pdesc + e); }
+    static __device__ __forceinline__ uint32_t a_len(const Desc &d) { return d.y; }
+    static __device__ __forceinline__ Desc shfl(const Desc &d, uint32_t src) { return shfl4(d, src); }
+    __device__ __forceinline__ PackedList list(const Desc &d, bool f) const {
+        return f ? PackedList{blocks + d.z, gaps, d.w} : PackedList{blocks + d.x, gaps, d.y};
+    }
+};
+
 // ------------------------------------------------------- K0: thread/pair
 __global__ void __launch_bounds__(256) k_plain(DevSet R, DevSet S, const uint32_t *__restrict__ pr,
                                                const uint32_t *__restrict__ ps, uint64_t n,
@@ -81,33 +117,33 @@ __global__ void __launch_bounds__(256) k_plain(DevSet R, DevSet S, const uint32_
     }
 }
 
-// Algorithm 2 for one pair by one warp.
-__device__ __forceinline__ uint8_t warp_verdict(const DevSet &R, const DevSet &S, const uint4 &dr, const uint4 &ds,
-                                                uint2 *xs, uint2 *ys, uint32_t lane, uint32_t w0) {
-    if (!tile_join<WarpScope, 32, kWarpWMax>(R.iv + dr.x, dr.y, S.iv + ds.x, ds.y, xs, ys, nullptr, lane, w0))
+// Algorithm 2 for one pair by one warp: AA; if no overlap, a true negative;
+// else AF, then FA.
+template <class SetsT>
+__device__ __forceinline__ uint8_t warp_verdict(const SetsT &R, const SetsT &S, const typename SetsT::Desc &dr,
+                                                const typename SetsT::Desc &ds, uint2 *xs, uint2 *ys, uint32_t lane,
+                                                uint32_t w0) {
+    if (!tile_join<WarpScope, 32, kWarpWMax>(R.list(dr, false), S.list(ds, false), xs, ys, nullptr, lane, w0))
         return APRIL_TRUE_NEGATIVE;
-    if (tile_join<WarpScope, 32, kWarpWMax>(R.iv + dr.x, dr.y, S.iv + ds.z, ds.w, xs, ys, nullptr, lane, w0))
+    if (tile_join<WarpScope, 32, kWarpWMax>(R.list(dr, false), S.list(ds, true), xs, ys, nullptr, lane, w0))
         return APRIL_TRUE_HIT;
-    if (tile_join<WarpScope, 32, kWarpWMax>(R.iv + dr.z, dr.w, S.iv + ds.x, ds.y, xs, ys, nullptr, lane, w0))
+    if (tile_join<WarpScope, 32, kWarpWMax>(R.list(dr, true), S.list(ds, false), xs, ys, nullptr, lane, w0))
         return APRIL_TRUE_HIT;
     return APRIL_INCONCLUSIVE;
 }
 
 // Algorithm 2 for one pair by the whole CTA.
-__device__ __forceinline__ uint8_t cta_verdict(const DevSet &R, const DevSet &S, const uint4 &dr, const uint4 &ds,
-                                               uint2 *xs, uint2 *ys, uint32_t *slot, uint32_t tid, uint32_t w0) {
-    if (!tile_join<CtaScope, kBlock, kCtaWMax>(R.iv + dr.x, dr.y, S.iv + ds.x, ds.y, xs, ys, slot, tid, w0))
+template <class SetsT>
+__device__ __forceinline__ uint8_t cta_verdict(const SetsT &R, const SetsT &S, const typename SetsT::Desc &dr,
+                                               const typename SetsT::Desc &ds, uint2 *xs, uint2 *ys, uint32_t *slot,
+                                               uint32_t tid, uint32_t w0) {
+    if (!tile_join<CtaScope, kBlock, kCtaWMax>(R.list(dr, false), S.list(ds, false), xs, ys, slot, tid, w0))
         return APRIL_TRUE_NEGATIVE;
-    if (tile_join<CtaScope, kBlock, kCtaWMax>(R.iv + dr.x, dr.y, S.iv + ds.z, ds.w, xs, ys, slot, tid, w0))
+    if (tile_join<CtaScope, kBlock, kCtaWMax>(R.list(dr, false), S.list(ds, true), xs, ys, slot, tid, w0))
         return APRIL_TRUE_HIT;
-    if (tile_join<CtaScope, kBlock, kCtaWMax>(R.iv + dr.z, dr.w, S.iv + ds.x, ds.y, xs, ys, slot, tid, w0))
+    if (tile_join<CtaScope, kBlock, kCtaWMax>(R.list(dr, true), S.list(ds, false), xs, ys, slot, tid, w0))
         return APRIL_TRUE_HIT;
     return APRIL_INCONCLUSIVE;
-}
-
-__device__ __forceinline__ uint4 shfl4(const uint4 &v, uint32_t src) {
-    return make_uint4(__shfl_sync(kFull, v.x, src), __shfl_sync(kFull, v.y, src), __shfl_sync(kFull, v.z, src),
-                      __shfl_sync(kFull, v.w, src));
 }
 
 // One warp filters the 32 pairs starting at `base`: every lane fetches the
@@ -115,19 +151,20 @@ __device__ __forceinline__ uint4 shfl4(const uint4 &v, uint32_t src) {
 // gathers in flight), then the warp joins the pairs one after another.  Pairs
 // whose cost |A(r)| + |A(s)| exceeds cta_threshold are left to the CTA phase
 // (pass UINT32_MAX to take every pair).
-__device__ __forceinline__ void warp_chunk(const DevSet &R, const DevSet &S, const uint32_t *__restrict__ pr,
+template <class SetsT>
+__device__ __forceinline__ void warp_chunk(const SetsT &R, const SetsT &S, const uint32_t *__restrict__ pr,
                                            const uint32_t *__restrict__ ps, uint64_t n, uint64_t base,
                                            uint8_t *__restrict__ out, uint32_t *status, uint2 *xs, uint2 *ys,
                                            uint32_t lane, uint32_t w0, uint32_t cta_threshold, bool flag_bad) {
     const uint64_t k = base + lane;
-    uint4 dr = make_uint4(0, 0, 0, 0), ds = make_uint4(0, 0, 0, 0);
+    typename SetsT::Desc dr{}, ds{};
     bool take = false;
     if (k < n) {
         const uint32_t r = __ldg(pr + k), s = __ldg(ps + k);
-        if (r < R.n && s < S.n) {
-            dr = __ldg(R.desc + r);
-            ds = __ldg(S.desc + s);
-            take = (uint64_t)dr.y + ds.y <= (uint64_t)cta_threshold;
+        if (r < R.n() && s < S.n()) {
+            dr = R.load(r);
+            ds = S.load(s);
+            take = (uint64_t)SetsT::a_len(dr) + SetsT::a_len(ds) <= (uint64_t)cta_threshold;
         } else if (flag_bad) {
             out[k] = APRIL_VERDICT_ERROR;
             atomicOr(status, ST_BAD_ID);
@@ -138,7 +175,7 @@ __device__ __forceinline__ void warp_chunk(const DevSet &R, const DevSet &S, con
     while (todo) {
         const uint32_t t = __ffs(todo) - 1;
         todo &= todo - 1;
-        const uint4 a = shfl4(dr, t), b = shfl4(ds, t);
+        const typename SetsT::Desc a = SetsT::shfl(dr, t), b = SetsT::shfl(ds, t);
         const uint8_t v = warp_verdict(R, S, a, b, xs, ys, lane, w0);
         if (lane == t) mine = v;
     }
@@ -153,14 +190,16 @@ __global__ void __launch_bounds__(kBlock) k_warp(DevSet R, DevSet S, const uint3
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint64_t stride = (uint64_t)gridDim.x * kWarpsPerBlock * 32;
     for (uint64_t base = ((uint64_t)blockIdx.x * kWarpsPerBlock + warp) * 32; base < n; base += stride)
-        warp_chunk(R, S, pr, ps, n, base, out, status, sm[warp][0], sm[warp][1], lane, w0, 0xffffffffu, true);
+        warp_chunk(RawSets{R}, RawSets{S}, pr, ps, n, base, out, status, sm[warp][0], sm[warp][1], lane, w0,
+                   0xffffffffu, true);
 }
 
 // --------------------------------------------- K4: length binning (batched)
 // Validates ids (error verdicts), and appends every pair whose cost
 // |A(r)| + |A(s)| exceeds the threshold to the long-pair list (warp-
 // aggregated atomics).
-__global__ void __launch_bounds__(256) k_bin(DevSet R, DevSet S, const uint32_t *__restrict__ pr,
+template <class SetsT>
+__global__ void __launch_bounds__(256) k_bin(SetsT R, SetsT S, const uint32_t *__restrict__ pr,
                                              const uint32_t *__restrict__ ps, uint64_t n, uint8_t *__restrict__ out,
                                              uint32_t *status, uint32_t cta_threshold, uint32_t *big_list,
                                              uint32_t *counters) {
@@ -171,8 +210,8 @@ __global__ void __launch_bounds__(256) k_bin(DevSet R, DevSet S, const uint32_t 
         bool big = false;
         if (k < n) {
             const uint32_t r = __ldg(pr + k), s = __ldg(ps + k);
-            if (r < R.n && s < S.n) {
-                big = (uint64_t)__ldg(&R.desc[r].y) + __ldg(&S.desc[s].y) > (uint64_t)cta_threshold;
+            if (r < R.n() && s < S.n()) {
+                big = (uint64_t)SetsT::a_len(R.load(r)) + SetsT::a_len(S.load(s)) > (uint64_t)cta_threshold;
             } else {
                 out[k] = APRIL_VERDICT_ERROR;
                 atomicOr(status, ST_BAD_ID);
@@ -347,8 +386,8 @@ __device__ __forceinline__ void group_engine(const DevSet &R, const DevSet &S, c
 // merge path of one join split over 256 threads).  Phase 2: the group engine
 // on the short pairs.  Work is handed out by atomic counters; nothing waits
 // on another CTA.
-template <uint32_t G>
-__global__ void __launch_bounds__(kBlock) k_persistent(DevSet R, DevSet S, const uint32_t *__restrict__ pr,
+template <uint32_t G, class SetsT>
+__global__ void __launch_bounds__(kBlock) k_persistent(SetsT R, SetsT S, const uint32_t *__restrict__ pr,
                                                        const uint32_t *__restrict__ ps, uint64_t n,
                                                        uint8_t *__restrict__ out, uint32_t *status,
                                                        uint32_t cta_threshold, const uint32_t *__restrict__ big_list,
@@ -364,13 +403,13 @@ __global__ void __launch_bounds__(kBlock) k_persistent(DevSet R, DevSet S, const
         __syncthreads();
         if (it >= nbig) break;
         const uint64_t k = big_list[it];
-        const uint4 dr = __ldg(R.desc + __ldg(pr + k)), ds = __ldg(S.desc + __ldg(ps + k));
+        const typename SetsT::Desc dr = R.load(__ldg(pr + k)), ds = S.load(__ldg(ps + k));
         const uint8_t v = cta_verdict(R, S, dr, ds, sm, sm + kCtaBuf, &s_slot, tid, w0_cta);
         if (tid == 0) out[k] = v;
     }
     __syncthreads();
     uint2 *wbuf = sm + warp * kWarpShare;
-    if (G == 32) {
+    if constexpr (G == 32 || SetsT::kPacked) {
         const uint64_t nchunks = (n + 31) / 32;
         for (;;) {
             uint32_t c = 0;
@@ -381,7 +420,46 @@ __global__ void __launch_bounds__(kBlock) k_persistent(DevSet R, DevSet S, const
                        cta_threshold, false);
         }
     } else {
-        group_engine<G>(R, S, pr, ps, n, out, counters, cta_threshold, wbuf, lane, w0_group);
+        group_engine<G>(R.s, S.s, pr, ps, n, out, counters, cta_threshold, wbuf, lane, w0_group);
+    }
+}
+
+// ------------------------------------------- K6: partition routing (a-8)
+// Sec. 5.2: a candidate pair is evaluated in the one partition that holds the
+// lower-left corner of MBR(r) n MBR(s).  Writes the two entries (object
+// approximations on that partition's grid) of every pair; an out-of-range id
+// or a missing entry yields UINT32_MAX, which the filter reports as an error.
+struct PartView {
+    const int2 *ll;
+    const uint32_t *obj_entry;
+    const uint32_t *entry_pid;
+    uint32_t n;
+};
+
+__device__ __forceinline__ uint32_t find_entry(const PartView &P, uint32_t obj, uint32_t pid) {
+    const uint32_t e1 = __ldg(P.obj_entry + obj + 1);
+    for (uint32_t e = __ldg(P.obj_entry + obj); e < e1; ++e)
+        if (__ldg(P.entry_pid + e) == pid) return e;
+    return 0xffffffffu;
+}
+
+__global__ void __launch_bounds__(256) k_route(PartView R, PartView S, uint32_t parts_log2,
+                                               const uint32_t *__restrict__ pr, const uint32_t *__restrict__ ps,
+                                               uint64_t n, uint32_t *__restrict__ er, uint32_t *__restrict__ es) {
+    const uint32_t side_log2 = 24 - parts_log2, pmax = (1u << parts_log2) - 1u;
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t r = __ldg(pr + k), s = __ldg(ps + k);
+        uint32_t a = 0xffffffffu, b = 0xffffffffu;
+        if (r < R.n && s < S.n) {
+            const int2 lr = __ldg(R.ll + r), ls = __ldg(S.ll + s);
+            const uint32_t x = (uint32_t)max(lr.x, ls.x), y = (uint32_t)max(lr.y, ls.y);
+            const uint32_t pid = (min(y >> side_log2, pmax) << parts_log2) + min(x >> side_log2, pmax);
+            a = find_entry(R, r, pid);
+            b = find_entry(S, s, pid);
+        }
+        er[k] = a;
+        es[k] = b;
     }
 }
 
@@ -396,8 +474,12 @@ struct GraphKey {
     uint64_t n;
     april_tune tune;
     unsigned grid_bin, grid_main;
+    bool packed;
+    uint32_t parts;
+    const void *r_pdesc, *s_pdesc;
     bool operator==(const GraphKey &o) const {
-        return r_desc == o.r_desc && r_iv == o.r_iv && s_desc == o.s_desc && s_iv == o.s_iv && rn == o.rn &&
+        return packed == o.packed && parts == o.parts && r_pdesc == o.r_pdesc && s_pdesc == o.s_pdesc &&
+               r_desc == o.r_desc && r_iv == o.r_iv && s_desc == o.s_desc && s_iv == o.s_iv && rn == o.rn &&
                sn == o.sn && d_r == o.d_r && d_s == o.d_s && out == o.out && scratch == o.scratch && n == o.n &&
                tune.cta_threshold == o.tune.cta_threshold && tune.group_lanes == o.tune.group_lanes &&
                tune.group_window == o.tune.group_window && tune.cta_window == o.tune.cta_window &&
@@ -409,7 +491,7 @@ struct april_ctx {
     int device = 0;
     uint32_t *d_status = nullptr;  // 256-byte status block (word 0: ST_* bits)
     int num_sms = 0;
-    int persistent_blocks_per_sm[4] = {1, 1, 1, 1};  // occupancy of k_persistent<4, 8, 16, 32>
+    int persistent_blocks_per_sm[5] = {1, 1, 1, 1, 1};  // occupancy of k_persistent<4, 8, 16, 32>, packed
     april_tune tune{};
     cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
     cudaGraphExec_t graph = nullptr;    // the batched pipeline, captured once per argument set
@@ -455,13 +537,20 @@ extern "C" april_status april_ctx_create(int device, april_ctx **out) {
     c->tune = default_tune();
     e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->persistent_blocks_per_sm[0], k_persistent<4>, kBlock, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->persistent_blocks_per_sm[0], k_persistent<4, RawSets>,
+                                                          kBlock, 0);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->persistent_blocks_per_sm[1], k_persistent<8>, kBlock, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->persistent_blocks_per_sm[1], k_persistent<8, RawSets>,
+                                                          kBlock, 0);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->persistent_blocks_per_sm[2], k_persistent<16>, kBlock, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->persistent_blocks_per_sm[2], k_persistent<16, RawSets>,
+                                                          kBlock, 0);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->persistent_blocks_per_sm[3], k_persistent<32>, kBlock, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->persistent_blocks_per_sm[3], k_persistent<32, RawSets>,
+                                                          kBlock, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->persistent_blocks_per_sm[4],
+                                                          k_persistent<32, PackedSets>, kBlock, 0);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_status, 256);
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, 256);
@@ -503,19 +592,41 @@ extern "C" april_status april_upload(const april_sets *S, void *dev_buf, size_t 
                                      april_dev_sets *out) {
     if (!S || !dev_buf || !out) return fail(APRIL_ERR_INVALID_ARG, "NULL argument");
     if (((uintptr_t)dev_buf) & 255u) return fail(APRIL_ERR_INVALID_ARG, "device buffer must be 256-byte aligned");
-    const uint64_t db = april_desc_bytes(S->n), ivb = (uint64_t)S->iv.size() * 4;
-    if (dev_bytes < db + ivb) return fail(APRIL_ERR_INVALID_ARG, "device buffer too small");
+    const april_image_layout L = april_layout(*S);
+    if (dev_bytes < L.total) return fail(APRIL_ERR_INVALID_ARG, "device buffer too small");
     cudaStream_t st = (cudaStream_t)stream;
     char *base = (char *)dev_buf;
     cudaError_t e = cudaSuccess;
-    if (S->n) e = cudaMemcpyAsync(base, S->desc.data(), (size_t)S->n * 16, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && ivb) e = cudaMemcpyAsync(base + db, S->iv.data(), ivb, cudaMemcpyHostToDevice, st);
+    auto put = [&](uint64_t off, const void *src, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(base + off, src, bytes, cudaMemcpyHostToDevice, st);
+    };
+    put(L.desc, S->desc.data(), S->desc.size() * 4);
+    put(L.iv, S->iv.data(), S->iv.size() * 4);
+    put(L.obj_ll, S->obj_ll.data(), S->obj_ll.size() * 4);
+    put(L.obj_entry, S->obj_entry.data(), S->obj_entry.size() * 4);
+    put(L.entry_pid, S->entry_pid.data(), S->entry_pid.size() * 4);
+    put(L.pdesc, S->pdesc.data(), S->pdesc.size() * 4);
+    put(L.anchors, S->anchors.data(), S->anchors.size() * 4);
+    put(L.gaps, S->gaps.data(), S->gaps.size());
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(upload)");
-    out->desc = (const uint32_t *)base;
-    out->iv = (const uint32_t *)(base + db);
+    *out = april_dev_sets{};
+    out->desc = (const uint32_t *)(base + L.desc);
+    out->iv = (const uint32_t *)(base + L.iv);
     out->n_objects = S->n;
     out->order = S->order;
     out->iv_slots = S->iv.size() / 2;
+    out->n_entries = S->n_entries;
+    out->parts = S->parts;
+    if (S->parts) {
+        out->obj_ll = (const int32_t *)(base + L.obj_ll);
+        out->obj_entry = (const uint32_t *)(base + L.obj_entry);
+        out->entry_pid = (const uint32_t *)(base + L.entry_pid);
+    }
+    if (S->packed) {
+        out->pdesc = (const uint32_t *)(base + L.pdesc);
+        out->anchors = (const uint32_t *)(base + L.anchors);
+        out->gaps = (const uint8_t *)(base + L.gaps);
+    }
     return APRIL_OK;
 }
 
@@ -526,29 +637,57 @@ extern "C" april_status april_filter_scratch_bytes(int mode, uint64_t n, size_t 
     switch (mode) {
         case APRIL_MODE_PLAIN:
         case APRIL_MODE_WARP: *bytes = 0; return APRIL_OK;
-        case APRIL_MODE_BATCHED: *bytes = (size_t)(kCounterBytes + round256(4 * n)); return APRIL_OK;
+        case APRIL_MODE_BATCHED:
+        case APRIL_MODE_BATCHED_PACKED: *bytes = (size_t)(kCounterBytes + 3 * round256(4 * n)); return APRIL_OK;
         default: return fail(APRIL_ERR_INVALID_ARG, "unknown mode");
     }
 }
 
 static inline DevSet dev_set(const april_dev_sets *d) {
-    return DevSet{(const uint4 *)d->desc, (const uint2 *)d->iv, d->n_objects};
+    return DevSet{(const uint4 *)d->desc, (const uint2 *)d->iv, d->n_entries ? d->n_entries : d->n_objects};
 }
 
-// Enqueues the batched pipeline (counter reset, K4 binning, K3 persistent
-// filter) on `st`.
-static cudaError_t enqueue_batched(april_ctx *ctx, const DevSet &R, const DevSet &S, const uint32_t *d_r,
-                                   const uint32_t *d_s, uint64_t n, uint8_t *out, void *scratch, unsigned grid_bin,
-                                   unsigned grid_main, cudaStream_t st) {
+static inline PackedSets packed_set(const april_dev_sets *d) {
+    return PackedSets{(const uint4 *)d->pdesc, (const uint2 *)d->anchors, d->gaps,
+                      d->n_entries ? d->n_entries : d->n_objects};
+}
+
+static inline PartView part_view(const april_dev_sets *d) {
+    return PartView{(const int2 *)d->obj_ll, d->obj_entry, d->entry_pid, d->n_objects};
+}
+
+// Enqueues the batched pipeline on `st`: counter reset, partition routing
+// (partitioned sets only), K4 binning, K3 persistent filter.
+static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, const april_dev_sets *Sd,
+                                   const uint32_t *d_r, const uint32_t *d_s, uint64_t n, uint8_t *out, void *scratch,
+                                   bool packed, unsigned grid_bin, unsigned grid_main, cudaStream_t st) {
     uint32_t *counters = (uint32_t *)scratch;
     uint32_t *big_list = (uint32_t *)((char *)scratch + kCounterBytes);
     const april_tune &t = ctx->tune;
     cudaError_t e = cudaMemsetAsync(counters, 0, kCounterBytes, st);
     if (e != cudaSuccess) return e;
+    if (Rd->parts) {
+        uint32_t *er = (uint32_t *)((char *)scratch + kCounterBytes + round256(4 * n));
+        uint32_t *es = (uint32_t *)((char *)scratch + kCounterBytes + 2 * round256(4 * n));
+        uint32_t lg = 0;
+        while ((1u << lg) < Rd->parts) ++lg;
+        k_route<<<grid_bin, 256, 0, st>>>(part_view(Rd), part_view(Sd), lg, d_r, d_s, n, er, es);
+        d_r = er;
+        d_s = es;
+    }
+    if (packed) {
+        const PackedSets R = packed_set(Rd), S = packed_set(Sd);
+        k_bin<<<grid_bin, 256, 0, st>>>(R, S, d_r, d_s, n, out, ctx->d_status, t.cta_threshold, big_list, counters);
+        k_persistent<32, PackedSets><<<grid_main, kBlock, 0, st>>>(R, S, d_r, d_s, n, out, ctx->d_status,
+                                                                   t.cta_threshold, big_list, counters, 64u,
+                                                                   t.cta_window);
+        return cudaGetLastError();
+    }
+    const RawSets R{dev_set(Rd)}, S{dev_set(Sd)};
     k_bin<<<grid_bin, 256, 0, st>>>(R, S, d_r, d_s, n, out, ctx->d_status, t.cta_threshold, big_list, counters);
-#define APRIL_LAUNCH_PERSISTENT(G)                                                                             \
-    k_persistent<G><<<grid_main, kBlock, 0, st>>>(R, S, d_r, d_s, n, out, ctx->d_status, t.cta_threshold, big_list, \
-                                                  counters, t.group_window, t.cta_window)
+#define APRIL_LAUNCH_PERSISTENT(G)                                                                            \
+    k_persistent<G, RawSets><<<grid_main, kBlock, 0, st>>>(R, S, d_r, d_s, n, out, ctx->d_status, t.cta_threshold, \
+                                                           big_list, counters, t.group_window, t.cta_window)
     switch (t.group_lanes) {
         case 4: APRIL_LAUNCH_PERSISTENT(4); break;
         case 8: APRIL_LAUNCH_PERSISTENT(8); break;
@@ -564,15 +703,14 @@ static cudaError_t enqueue_batched(april_ctx *ctx, const DevSet &R, const DevSet
 // caller's stream.
 static april_status launch_batched(april_ctx *ctx, const april_dev_sets *R, const april_dev_sets *S,
                                    const uint32_t *d_r, const uint32_t *d_s, uint64_t n, uint8_t *out,
-                                   void *scratch, cudaStream_t st) {
-    const DevSet dR = dev_set(R), dS = dev_set(S);
+                                   void *scratch, bool packed, cudaStream_t st) {
     const unsigned grid_bin = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx->num_sms * 8);
     const uint32_t gl = ctx->tune.group_lanes;
-    const int occ = ctx->persistent_blocks_per_sm[gl == 4 ? 0 : gl == 8 ? 1 : gl == 16 ? 2 : 3];
+    const int occ = ctx->persistent_blocks_per_sm[packed ? 4 : gl == 4 ? 0 : gl == 8 ? 1 : gl == 16 ? 2 : 3];
     const int bps = ctx->tune.blocks_per_sm ? (int)std::min<uint32_t>(ctx->tune.blocks_per_sm, (uint32_t)occ) : occ;
     const unsigned grid_main = (unsigned)std::max(1, ctx->num_sms * bps);
     GraphKey key{R->desc, R->iv, S->desc, S->iv, R->n_objects, S->n_objects, d_r, d_s, out, scratch, n,
-                 ctx->tune, grid_bin, grid_main};
+                 ctx->tune, grid_bin, grid_main, packed, R->parts, R->pdesc, S->pdesc};
     cudaError_t e;
     if (!ctx->graph || !(key == ctx->key)) {
         if (ctx->graph) {
@@ -582,7 +720,8 @@ static april_status launch_batched(april_ctx *ctx, const april_dev_sets *R, cons
         cudaGraph_t g = nullptr;
         e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-        cudaError_t e1 = enqueue_batched(ctx, dR, dS, d_r, d_s, n, out, scratch, grid_bin, grid_main, ctx->cap_stream);
+        cudaError_t e1 = enqueue_batched(ctx, R, S, d_r, d_s, n, out, scratch, packed, grid_bin, grid_main,
+                                         ctx->cap_stream);
         e = cudaStreamEndCapture(ctx->cap_stream, &g);
         if (e1 != cudaSuccess) e = e1;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph, g, 0);
@@ -607,8 +746,13 @@ extern "C" april_status april_filter_pairs(april_ctx *ctx, const april_dev_sets 
     if (!ctx || !R || !S) return fail(APRIL_ERR_INVALID_ARG, "NULL argument");
     if (n == 0) return APRIL_OK;
     if (!d_r || !d_s || !d_verdict) return fail(APRIL_ERR_INVALID_ARG, "NULL pair or verdict array");
-    if (R->order != S->order) return fail(APRIL_ERR_INVALID_ARG, "R and S are on different grids");
+    if (R->order != S->order || R->parts != S->parts)
+        return fail(APRIL_ERR_INVALID_ARG, "R and S are on different grids");
     if (n > 0xFFFFFFFFull) return fail(APRIL_ERR_INVALID_ARG, "at most 2^32-1 pairs per call");
+    if (R->parts && mode != APRIL_MODE_BATCHED && mode != APRIL_MODE_BATCHED_PACKED)
+        return fail(APRIL_ERR_INVALID_ARG, "partitioned sets need APRIL_MODE_BATCHED or APRIL_MODE_BATCHED_PACKED");
+    if (mode == APRIL_MODE_BATCHED_PACKED && (!R->pdesc || !S->pdesc))
+        return fail(APRIL_ERR_INVALID_ARG, "APRIL_MODE_BATCHED_PACKED needs sets compressed by april_sets_compress");
     cudaStream_t st = (cudaStream_t)stream;
     const DevSet dR = dev_set(R), dS = dev_set(S);
     const int sms = ctx->num_sms;
@@ -625,12 +769,13 @@ extern "C" april_status april_filter_pairs(april_ctx *ctx, const april_dev_sets 
             k_warp<<<grid, kBlock, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, ctx->d_status, kWarpFirstWindow);
             break;
         }
-        case APRIL_MODE_BATCHED: {
+        case APRIL_MODE_BATCHED:
+        case APRIL_MODE_BATCHED_PACKED: {
             size_t need = 0;
             april_filter_scratch_bytes(mode, n, &need);
             if (!d_scratch || scratch_bytes < need) return fail(APRIL_ERR_INVALID_ARG, "scratch missing or too small");
             if (((uintptr_t)d_scratch) & 255u) return fail(APRIL_ERR_INVALID_ARG, "scratch must be 256-byte aligned");
-            return launch_batched(ctx, R, S, d_r, d_s, n, d_verdict, d_scratch, st);
+            return launch_batched(ctx, R, S, d_r, d_s, n, d_verdict, d_scratch, mode == APRIL_MODE_BATCHED_PACKED, st);
         }
         default: return fail(APRIL_ERR_INVALID_ARG, "unknown mode");
     }
@@ -791,6 +936,7 @@ extern "C" april_status april_filter_pairs_noalloc(const april_dev_sets *R, cons
     if (n == 0) return APRIL_OK;
     if (!d_r || !d_s || !d_verdict) return fail(APRIL_ERR_INVALID_ARG, "NULL pair or verdict array");
     if (R->order != S->order) return fail(APRIL_ERR_INVALID_ARG, "R and S are on different grids");
+    if (R->parts || S->parts) return fail(APRIL_ERR_INVALID_ARG, "april_filter_pairs_noalloc takes unpartitioned sets");
     if (n > kNoAllocMaxPairs)
         return fail(APRIL_ERR_INVALID_ARG, "april_filter_pairs_noalloc: n exceeds APRIL_NOALLOC_MAX_PAIRS (4194304); "
                                            "split the pairs or use april_filter_pairs with caller scratch");
@@ -811,7 +957,8 @@ extern "C" april_status april_filter_pairs_noalloc(const april_dev_sets *R, cons
             if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
             int sms = 0, bps = 0;
             e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_persistent<8>, kBlock, 0);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_persistent<8, RawSets>, kBlock, 0);
             if (e != cudaSuccess) return cuda_fail(e, "april_filter_pairs_noalloc set-up");
             slot.scratch = ptr;
             slot.num_sms = sms;
@@ -827,12 +974,12 @@ extern "C" april_status april_filter_pairs_noalloc(const april_dev_sets *R, cons
     // the array keeps the previous call's contents: reset counters and status
     e = cudaMemsetAsync(counters, 0, kCounterBytes, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(no-alloc counters)");
-    const DevSet dR = dev_set(R), dS = dev_set(S);
+    const RawSets dR{dev_set(R)}, dS{dev_set(S)};
     const unsigned grid_bin = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)nd.num_sms * 8);
     const unsigned grid_main = (unsigned)std::max(1, nd.num_sms * nd.blocks_per_sm);
     k_bin<<<grid_bin, 256, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, status, t.cta_threshold, big_list, counters);
-    k_persistent<8><<<grid_main, kBlock, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, status, t.cta_threshold, big_list,
-                                                  counters, t.group_window, t.cta_window);
+    k_persistent<8, RawSets><<<grid_main, kBlock, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, status, t.cta_threshold,
+                                                           big_list, counters, t.group_window, t.cta_window);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "april_filter_pairs_noalloc launch");
     return APRIL_OK;

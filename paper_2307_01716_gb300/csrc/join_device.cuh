@@ -192,20 +192,85 @@ __device__ __forceinline__ uint2 *stage_window(uint2 *buf, const uint2 *src, uin
     return buf + odd;
 }
 
-// Any overlap between X[0..n) and Y[0..m), by a group of NT threads (thread
+// A list as the joins read it.  RawList: intervals in global memory, staged
+// into shared memory with 16-byte cp.async.  PackedList: the compressed form
+// of Sec. 5.1 (blocks of 32 endpoints: a uint32 anchor and 31 uint16 or uint32
+// gaps), decoded in registers by the staging threads (one block per thread,
+// a running sum over the block) and stored to shared memory as intervals.
+// Either way the window's intervals end up at the returned shared address.
+struct RawList {
+    const uint2 *p;
+    uint32_t n;
+    template <uint32_t NT>
+    __device__ __forceinline__ uint32_t stage(uint2 *buf, uint32_t i0, uint32_t cnt, uint32_t tid) const {
+        return smem_addr(stage_window<NT>(buf, p + i0, cnt, tid));
+    }
+};
+
+struct PackedList {
+    const uint2 *blocks;  // per block {anchor, gap_off64 | wide << 31}
+    const uint8_t *gaps;  // the set's gap stream
+    uint32_t n;
+    template <uint32_t NT>
+    __device__ __forceinline__ uint32_t stage(uint2 *buf, uint32_t i0, uint32_t cnt, uint32_t tid) const {
+        const uint32_t base = smem_addr(buf);
+        const uint32_t e0 = 2 * i0, e1 = 2 * (i0 + cnt);  // endpoint range of the window
+        const uint32_t b0 = e0 >> 5, b1 = (e1 - 1) >> 5;
+        for (uint32_t b = b0 + tid; b <= b1; b += NT) {
+            const uint2 meta = __ldg(blocks + b);
+            uint32_t v = meta.x;
+            const uint8_t *gb = gaps + 64ull * (meta.y & 0x7FFFFFFFu);
+            uint32_t g[32];
+            if (meta.y >> 31) {
+                const uint4 *q = (const uint4 *)gb;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const uint4 u = __ldg(q + c);
+                    g[4 * c] = u.x;
+                    g[4 * c + 1] = u.y;
+                    g[4 * c + 2] = u.z;
+                    g[4 * c + 3] = u.w;
+                }
+            } else {
+                const uint4 *q = (const uint4 *)gb;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const uint4 u = __ldg(q + c);
+                    g[8 * c] = u.x & 0xFFFFu;
+                    g[8 * c + 1] = u.x >> 16;
+                    g[8 * c + 2] = u.y & 0xFFFFu;
+                    g[8 * c + 3] = u.y >> 16;
+                    g[8 * c + 4] = u.z & 0xFFFFu;
+                    g[8 * c + 5] = u.z >> 16;
+                    g[8 * c + 6] = u.w & 0xFFFFu;
+                    g[8 * c + 7] = u.w >> 16;
+                }
+            }
+#pragma unroll
+            for (uint32_t k = 0; k < 32; ++k) {
+                if (k) v += g[k];
+                const uint32_t e = 32 * b + k;
+                if (e >= e0 && e < e1) asm volatile("st.shared.u32 [%0], %1;\n" ::"r"(base + 4 * (e - e0)), "r"(v));
+            }
+        }
+        return base;
+    }
+};
+
+// Any overlap between lists X and Y, by a group of NT threads (thread
 // index tid) with shared buffers xb, yb of WMAX + 2 intervals each (16-byte
 // aligned) and, for a CTA group, one shared word `slot`.  The first window
 // holds w0 intervals per list (a multiple of NT); later windows double up to
 // WMAX.  Every thread of the group must call it with the same arguments.
-template <class Scope, uint32_t NT, uint32_t WMAX>
-__device__ __noinline__ bool tile_join(const uint2 *__restrict__ X, uint32_t n, const uint2 *__restrict__ Y,
-                                       uint32_t m, uint2 *xb, uint2 *yb, uint32_t *slot, uint32_t tid,
-                                       uint32_t w0) {
+template <class Scope, uint32_t NT, uint32_t WMAX, class ListT>
+__device__ __noinline__ bool tile_join(const ListT X, const ListT Y, uint2 *xb, uint2 *yb, uint32_t *slot,
+                                       uint32_t tid, uint32_t w0) {
+    const uint32_t n = X.n, m = Y.n;
     uint32_t i0 = 0, j0 = 0, w = w0;
     while (i0 < n && j0 < m) {
         const uint32_t nx = min(w, n - i0), ny = min(w, m - j0);
-        const uint32_t xa = smem_addr(stage_window<NT>(xb, X + i0, nx, tid));
-        const uint32_t ya = smem_addr(stage_window<NT>(yb, Y + j0, ny, tid));
+        const uint32_t xa = X.template stage<NT>(xb, i0, nx, tid);
+        const uint32_t ya = Y.template stage<NT>(yb, j0, ny, tid);
         cp_async_wait_all();
         Scope::sync();
         // D diagonals of the merge path lie in this window; thread tid walks

@@ -12,8 +12,10 @@ draw from stream 1000+seed.
                    sigma 1.0, clipped to [8, 20000]), radius log-normal (median
                    2e-4, sigma 1.2), 5% of centres in 32 Gaussian hotspots.
   3  skewed:       as 2 but radius Pareto(alpha=1.3, x_m=1.17e-4) capped at
-                   RADIUS_CAP_SKEWED; candidate pairs sampled (seeded) to
-                   10M when the join yields more.
+                   RADIUS_CAP_SKEWED (A-lists up to ~10^5 intervals); the
+                   polygon count is grown from 200k to 340k per side so that
+                   the join yields >= 10M candidates, which are then sampled
+                   (seeded) to exactly 10M.
   4  partitioned:  the config-2 polygons on a 16x16 partition grid, each
                    partition rasterised at its own 2^14 grid.
   5  serving:      300k + 300k polygons from the config-3 generator, N=16.
@@ -35,7 +37,7 @@ from .mbrjoin import mbr_join
 HOTSPOT_FRAC = 0.05
 HOTSPOTS = 32
 HOTSPOT_SIGMA = 2.5e-4  # tuned so that the full config-2 join yields 2-5M candidates
-RADIUS_CAP_SKEWED = 0.02
+RADIUS_CAP_SKEWED = 0.04
 PARETO_ALPHA = 1.3
 PARETO_XM = 2e-4 / 2 ** (1 / 1.3)
 
@@ -112,7 +114,7 @@ def _hot(seed):
     return 0.1 + 0.8 * _rng(seed, 1000).random((HOTSPOTS, 2))
 
 
-RECIPE_VERSION = 2
+RECIPE_VERSION = 5
 
 
 def _cache_path(cfg, scale, max_pairs):
@@ -122,6 +124,10 @@ def _cache_path(cfg, scale, max_pairs):
 
 def make(cfg: int, scale: float = 1.0, max_pairs: int | None = None, cache: bool = True) -> Workload:
     """Build (or load from the on-disk cache) workload `cfg` at `scale`."""
+    if cfg == 4:  # the config-2 polygons and candidates, on 16x16 partitions of order 14
+        w = make(2, scale, max_pairs, cache)
+        return Workload(name="partitioned-16x16-n14", order=14, R=w.R, S=w.S, pr=w.pr, ps=w.ps, partitions=16,
+                        meta=dict(w.meta))
     use_cache = cache and scale >= 0.05
     if use_cache:
         path = _cache_path(cfg, scale, max_pairs)
@@ -164,7 +170,7 @@ def _make(cfg: int, scale: float, max_pairs: int | None) -> Workload:
         S = paper_side(sd, 2 * sd + 1, n, hot, skewed=False)
         order = 16 if cfg == 2 else 14
     elif cfg in (3, 5):
-        base = 200_000 if cfg == 3 else 300_000
+        base = 340_000 if cfg == 3 else 300_000  # config 3 grown from 200k until the join yields >= 10M
         n = max(int(round(base * scale)), 2)
         hot = _hot(2)
         sd = 2 if cfg == 3 else 4
@@ -181,7 +187,7 @@ def _make(cfg: int, scale: float, max_pairs: int | None) -> Workload:
         keep = np.sort(_rng(seed, 2000).choice(len(pr), max_pairs, replace=False))
         pr, ps = pr[keep], ps[keep]
         meta["sampled_to"] = int(max_pairs)
-    names = {1: "tiny-plain-1k", 2: "paper-scale-200k", 3: "skewed-pareto-200k",
+    names = {1: "tiny-plain-1k", 2: "paper-scale-200k", 3: "skewed-pareto-340k-10M",
              4: "partitioned-16x16-n14", 5: "serving-300k"}
     return Workload(name=names[cfg], order=order, R=R, S=S, pr=pr, ps=ps,
                     partitions=16 if cfg == 4 else 0, meta=meta)

@@ -190,3 +190,68 @@ def test_batched_scratch_checks(torch_cuda, ctx):
     with pytest.raises(A.AprilError) as e:
         ctx.april_filter_pairs(dR, dS, d_r, d_s, n, out, A.MODE_BATCHED, small)
     assert e.value.status == -1
+
+
+# ---------------------------------------------------------------- config 4
+def _run(torch, ctx, dR, dS, pr, ps, mode_id):
+    n = len(pr)
+    d_r = torch.from_numpy(np.ascontiguousarray(pr, dtype=np.uint32).view(np.int32)).cuda()
+    d_s = torch.from_numpy(np.ascontiguousarray(ps, dtype=np.uint32).view(np.int32)).cuda()
+    out = torch.full((max(n, 1),), 0xEE, dtype=torch.uint8, device="cuda")
+    scratch = torch.empty(max(ctx.scratch_bytes(mode_id, n), 256), dtype=torch.uint8, device="cuda")
+    ctx.april_filter_pairs(dR, dS, d_r, d_s, n, out, mode_id, scratch)
+    ctx.april_sync_status()
+    return out[:n].cpu().numpy()
+
+
+def _partitioned(w):
+    R, S = A.april_build_partitioned_sets(w.R.xy, w.R.off, w.S.xy, w.S.off, 16, 14)
+    R.compress()
+    S.compress()
+    return R, S, A.april_upload(R), A.april_upload(S)
+
+
+def test_partitioned_raw_and_packed_equal_oracle(torch_cuda, ctx):
+    w = _data.workload(4, 0.02)
+    R, S, dR, dS = _partitioned(w)
+    want = oracle.partitioned_verdicts(w.R.xy, w.R.off, w.R.mbr, w.S.xy, w.S.off, w.S.mbr, w.pr, w.ps, 16, 14)
+    assert len(want) > 500
+    for mode in (A.MODE_BATCHED, A.MODE_BATCHED_PACKED):
+        got = _run(torch_cuda, ctx, dR, dS, w.pr, w.ps, mode)
+        assert np.array_equal(got, want), (mode, np.nonzero(got != want)[0][:10])
+    # partitioned sets are only accepted by the batched modes
+    with pytest.raises(A.AprilError):
+        _run(torch_cuda, ctx, dR, dS, w.pr[:4], w.ps[:4], A.MODE_WARP)
+
+
+@pytest.mark.parametrize("cfg,scale", [(1, 1.0), (2, 0.01), (3, 0.01)])
+def test_packed_global_grid_equals_oracle(torch_cuda, ctx, cfg, scale):
+    w = _data.workload(cfg, scale)
+    g = A.global_grid(w.order)
+    R = A.april_build_sets(w.R.xy, w.R.off, g)
+    S = A.april_build_sets(w.S.xy, w.S.off, g)
+    R.compress()
+    S.compress()
+    dR, dS = A.april_upload(R), A.april_upload(S)
+    got = _run(torch_cuda, ctx, dR, dS, w.pr, w.ps, A.MODE_BATCHED_PACKED)
+    assert np.array_equal(got, _data.oracle_verdicts(cfg, scale))
+    # uncompressed sets are refused by the packed mode
+    R2 = A.april_build_sets(w.R.xy, w.R.off, g)
+    dR2 = A.april_upload(R2)
+    with pytest.raises(A.AprilError):
+        _run(torch_cuda, ctx, dR2, dR2, w.pr[:4], w.pr[:4], A.MODE_BATCHED_PACKED)
+
+
+def test_partitioned_full_size_sampled(torch_cuda, ctx):
+    """Config 4 at full size: packed == raw on every pair; a seeded sample of
+    pairs against the partitioned oracle."""
+    w = _data.workload(4, 1.0)
+    R, S, dR, dS = _partitioned(w)
+    raw = _run(torch_cuda, ctx, dR, dS, w.pr, w.ps, A.MODE_BATCHED)
+    packed = _run(torch_cuda, ctx, dR, dS, w.pr, w.ps, A.MODE_BATCHED_PACKED)
+    assert np.array_equal(raw, packed)
+    rng = np.random.default_rng(44)
+    idx = np.sort(rng.choice(len(w.pr), 800, replace=False))
+    want = oracle.partitioned_verdicts(w.R.xy, w.R.off, w.R.mbr, w.S.xy, w.S.off, w.S.mbr, w.pr[idx], w.ps[idx],
+                                       16, 14)
+    assert np.array_equal(raw[idx], want)
