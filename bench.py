@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tuning (profiling runs)")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--serving-requests", type=int, default=120)
     return ap.parse_args()
 
 
@@ -142,6 +144,65 @@ def cpu_baseline(w, seconds: float, seed: int = 1234):
     return {"value": done / dt, "unit": "pairs/s", "cores": 1, "kind": "oracle",
             "sample": f"{done} random pairs of the {len(w.pr)} (seeded), cell-set oracle, single thread, "
                       f"{dt:.1f} s"}
+
+
+def serving_bench(ctx_cls, A, torch, dev, n_requests: int, budget_gb: float = 40.0):
+    """Config 5: 300k + 300k polygons (config-3 generator, 2^16 grid) resident
+    in HBM; requests are query windows of 1k-2M candidate pairs (log-uniform)
+    arriving as a Poisson stream.  Continuous batching (8 stream slots, a 40 GB
+    arena) against one request per launch, at 50% and 80% of the measured
+    one-request-per-launch capacity."""
+    from synth import configs, serving
+    w = configs.make(5)
+    g = A.global_grid(w.order)
+    R = A.april_build_sets(w.R.xy, w.R.off, g)
+    S = A.april_build_sets(w.S.xy, w.S.off, g)
+    dR, dS = A.april_upload(R, dev), A.april_upload(S, dev)
+    ctx = ctx_cls(dev.index or 0)
+    maker = serving.RequestMaker(w.R.mbr, w.S.mbr, w.pr, w.ps)
+    reqs = maker.requests(seed=11, count=n_requests, rate=0.0)
+    bufs = [(torch.from_numpy(q.pr.view(np.int32).copy()).pin_memory(),
+             torch.from_numpy(q.ps.view(np.int32).copy()).pin_memory(),
+             torch.empty(len(q.pr), dtype=torch.uint8).pin_memory()) for q in reqs]
+    sizes = np.array([len(q.pr) for q in reqs])
+    arena = torch.empty(int(budget_gb * (1 << 30)), dtype=torch.uint8, device=dev)
+
+    def run(max_inflight, arrivals):
+        srv = A.Server(ctx, dR, dS, arena, max_inflight)
+        try:
+            for b in bufs[:4]:  # warm-up
+                srv.april_wait(srv.april_submit(*b))
+            t0 = time.perf_counter()
+            tickets = []
+            for b, at in zip(bufs, arrivals):
+                while time.perf_counter() - t0 < at:
+                    pass
+                tickets.append(srv.april_submit(*b))
+            stats = [srv.april_wait(t, 600000) for t in tickets]
+            info = srv.info()
+        finally:
+            srv.close()
+        lat = np.array([(st.done_ns - st.submit_ns) / 1e6 for st in stats])
+        span = (max(st.done_ns for st in stats) - min(st.submit_ns for st in stats)) / 1e9
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "pairs_per_s": float(sizes.sum() / span),
+                "requests_per_s": float(len(reqs) / span), "max_concurrent": int(info.max_concurrent),
+                "arena_peak_gb": info.arena_peak_bytes / (1 << 30)}
+
+    # capacity: all requests offered at once, one per launch
+    cap = run(1, np.zeros(len(reqs)))
+    capacity = cap["requests_per_s"]
+    out = {"workload": w.name, "candidates": int(len(w.pr)), "requests": len(reqs),
+           "request_pairs_mean": float(sizes.mean()), "request_pairs_p50": float(np.median(sizes)),
+           "budget_gb": budget_gb, "capacity_one_per_launch_req_s": capacity, "rates": {}}
+    rng = np.random.default_rng(77)
+    gaps = rng.exponential(1.0, len(reqs))
+    for frac in (0.5, 0.8):
+        lam = frac * capacity
+        arrivals = np.cumsum(gaps) / lam
+        out["rates"][f"{frac:.0%}"] = {"rate_req_s": lam, "continuous": run(8, arrivals),
+                                       "one_per_launch": run(1, arrivals)}
+    return out
 
 
 def dist_env():
@@ -315,6 +376,8 @@ def main():
         "tune": tune,
         "verdict_mix": (np.bincount(host_v, minlength=3)[:3] / n).round(4).tolist(),
     }
+    if rank == 0 and not args.no_serving:
+        line["serving"] = serving_bench(A.Context, A, torch, dev, args.serving_requests)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
         line["cpu_baseline"]["cpu"] = os.uname().machine

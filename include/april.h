@@ -295,6 +295,75 @@ april_status april_filter_pairs_host(april_ctx *ctx, const april_dev_sets *R, co
  * APRIL_ERR_CUDA if the stream itself failed). */
 april_status april_sync_status(april_ctx *ctx, void *stream);
 
+/* ----------------------------------------------------------------- serving */
+
+/* A serving loop over resident sets (a build-side addition; the paper runs
+ * one join at a time).  Requests (lists of candidate pairs in host memory)
+ * are queued by april_submit and admitted in arrival order by a runtime
+ * thread whenever one of max_inflight stream slots is free and the request's
+ * device buffers fit in the caller's arena (the memory budget).  Each
+ * admitted request is copied in, filtered by the batched kernels (at most one
+ * CTA per 256 pairs, so small requests share the GPU with the others) and
+ * copied out on its own stream; requests on different slots run
+ * concurrently.  max_inflight = 1 serves one request per launch.  Nothing on
+ * the device waits on the host: completion is detected with CUDA events. */
+typedef struct april_server april_server;
+
+typedef struct april_req_stats {
+    uint64_t n_pairs;
+    int64_t submit_ns;  /* host steady clock, nanoseconds */
+    int64_t admit_ns;   /* when its copy-in and kernels were enqueued */
+    int64_t done_ns;    /* when the runtime saw its verdicts land in host memory */
+    uint32_t slot;
+    int32_t status;
+} april_req_stats;
+
+typedef struct april_server_info {
+    uint64_t admitted;
+    uint64_t completed;
+    uint64_t pending;
+    uint64_t in_flight;
+    uint64_t max_concurrent;    /* most requests on the device at once so far */
+    uint64_t arena_bytes;
+    uint64_t arena_peak_bytes;  /* most arena bytes in use at once so far */
+} april_server_info;
+
+/* Creates a server for sets R and S (already uploaded; they stay resident).
+ * d_arena/arena_bytes: caller-allocated device memory (256-byte aligned) that
+ * bounds all request buffers: a request of n pairs needs about 21 n bytes.
+ * max_inflight: 1..64 stream slots.  The context must outlive the server. */
+april_status april_server_create(april_ctx *ctx, const april_dev_sets *R, const april_dev_sets *S, void *d_arena,
+                                 size_t arena_bytes, uint32_t max_inflight, april_server **out);
+
+/* Queues a request of n pairs (h_r[k], h_s[k]); its verdicts will be written
+ * to h_verdict (n bytes).  The three host buffers must stay valid until the
+ * request is done (pinned memory makes the copies asynchronous).  Never
+ * blocks on the GPU.  Returns APRIL_ERR_OVER_BUDGET if the request alone
+ * needs more than the whole arena. */
+april_status april_submit(april_server *server, const uint32_t *h_r, const uint32_t *h_s, uint64_t n,
+                          uint8_t *h_verdict, uint64_t *ticket);
+
+/* APRIL_PENDING while the request is queued or running; otherwise fills
+ * *stats (optional), forgets the ticket and returns APRIL_OK or the
+ * request's error (APRIL_ERR_OUT_OF_RANGE_ID, APRIL_ERR_CANCELLED,
+ * APRIL_ERR_CUDA). */
+april_status april_poll(april_server *server, uint64_t ticket, april_req_stats *stats);
+
+/* As april_poll, but first waits up to timeout_ms for the request to finish
+ * (returns APRIL_PENDING if it has not). */
+april_status april_wait(april_server *server, uint64_t ticket, uint32_t timeout_ms, april_req_stats *stats);
+
+/* Cancels a request that is still queued (APRIL_OK; its poll then returns
+ * APRIL_ERR_CANCELLED).  A request already on the device runs to completion
+ * (returns APRIL_PENDING). */
+april_status april_cancel(april_server *server, uint64_t ticket);
+
+april_status april_server_get_info(april_server *server, april_server_info *info);
+
+/* Cancels queued requests, waits for the ones on the device, and frees the
+ * server (not the arena, which belongs to the caller). */
+void april_server_destroy(april_server *server);
+
 /* ------------------------------------------------- allocation-free filter */
 
 /* The paper has no counterpart to this entry point; it serves callers that

@@ -56,6 +56,17 @@ class april_tune(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class april_req_stats(ctypes.Structure):
+    _fields_ = [("n_pairs", ctypes.c_uint64), ("submit_ns", ctypes.c_int64), ("admit_ns", ctypes.c_int64),
+                ("done_ns", ctypes.c_int64), ("slot", ctypes.c_uint32), ("status", ctypes.c_int32)]
+
+
+class april_server_info(ctypes.Structure):
+    _fields_ = [("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("pending", ctypes.c_uint64),
+                ("in_flight", ctypes.c_uint64), ("max_concurrent", ctypes.c_uint64),
+                ("arena_bytes", ctypes.c_uint64), ("arena_peak_bytes", ctypes.c_uint64)]
+
+
 class april_dev_sets(ctypes.Structure):
     _fields_ = [("desc", ctypes.c_void_p), ("iv", ctypes.c_void_p), ("n_objects", ctypes.c_uint32),
                 ("order", ctypes.c_uint32), ("iv_slots", ctypes.c_uint64), ("n_entries", ctypes.c_uint32),
@@ -93,6 +104,14 @@ SIGNATURES = {
     "april_build_partitioned_sets": (_st, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _u32, ctypes.POINTER(_vp),
                                            ctypes.POINTER(_vp)]),
     "april_sets_compress": (_st, [_vp]),
+    "april_server_create": (_st, [_vp, ctypes.POINTER(april_dev_sets), ctypes.POINTER(april_dev_sets), _vp,
+                                  ctypes.c_size_t, _u32, ctypes.POINTER(_vp)]),
+    "april_submit": (_st, [_vp, _vp, _vp, _u64, _vp, ctypes.POINTER(_u64)]),
+    "april_poll": (_st, [_vp, _u64, ctypes.POINTER(april_req_stats)]),
+    "april_wait": (_st, [_vp, _u64, _u32, ctypes.POINTER(april_req_stats)]),
+    "april_cancel": (_st, [_vp, _u64]),
+    "april_server_get_info": (_st, [_vp, ctypes.POINTER(april_server_info)]),
+    "april_server_destroy": (None, [_vp]),
     "april_sets_packed_list": (_st, [_vp, _u32, ctypes.c_int, ctypes.POINTER(ctypes.POINTER(_u32)),
                                      ctypes.POINTER(ctypes.POINTER(ctypes.c_uint8)), ctypes.POINTER(_u32)]),
     "april_filter_pairs_noalloc": (_st, [ctypes.POINTER(april_dev_sets), ctypes.POINTER(april_dev_sets), _vp, _vp,
@@ -319,6 +338,62 @@ class Context:
         import torch
         st = stream if stream is not None else torch.cuda.current_stream()
         return check(load().april_sync_status(self.handle, st.cuda_stream))
+
+
+class Server:
+    """Serving loop over resident sets (april_server_*).  Keeps the arena,
+    the sets and every submitted request's host buffers alive."""
+
+    def __init__(self, ctx: "Context", R: DevSets, S: DevSets, arena, max_inflight: int = 4):
+        self._ctx, self._R, self._S, self._arena = ctx, R, S, arena
+        h = _vp()
+        check(load().april_server_create(ctx.handle, ctypes.byref(R.c), ctypes.byref(S.c), _ptr(arena),
+                                         int(arena.numel()), max_inflight, ctypes.byref(h)))
+        self.handle = h.value
+        self._live = {}
+
+    def april_submit(self, h_r, h_s, h_verdict) -> int:
+        t = _u64()
+        n = len(h_r)
+        check(load().april_submit(self.handle, _ptr(h_r), _ptr(h_s), n, _ptr(h_verdict), ctypes.byref(t)))
+        self._live[t.value] = (h_r, h_s, h_verdict)
+        return t.value
+
+    def april_poll(self, ticket: int):
+        """None while pending, else april_req_stats (raises on a failed request)."""
+        st = april_req_stats()
+        rc = load().april_poll(self.handle, ticket, ctypes.byref(st))
+        if rc == APRIL_PENDING:
+            return None
+        self._live.pop(ticket, None)
+        check(rc)
+        return st
+
+    def april_wait(self, ticket: int, timeout_ms: int = 60000):
+        st = april_req_stats()
+        rc = load().april_wait(self.handle, ticket, timeout_ms, ctypes.byref(st))
+        if rc == APRIL_PENDING:
+            return None
+        self._live.pop(ticket, None)
+        check(rc)
+        return st
+
+    def april_cancel(self, ticket: int) -> int:
+        return check(load().april_cancel(self.handle, ticket))
+
+    def info(self) -> april_server_info:
+        i = april_server_info()
+        check(load().april_server_get_info(self.handle, ctypes.byref(i)))
+        return i
+
+    def close(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.april_server_destroy(self.handle)
+            self.handle = None
+            self._live.clear()
+
+    def __del__(self):
+        self.close()
 
 
 NOALLOC_MAX_PAIRS = 4194304

@@ -15,6 +15,13 @@ april_status fail(april_status code, const std::string &msg);
 
 }  // namespace april
 
+// Shared between filter.cu and server.cu (not exported).
+april_status april_enqueue_request(april_ctx *ctx, const april_dev_sets *R, const april_dev_sets *S,
+                                   const uint32_t *d_r, const uint32_t *d_s, uint64_t n, uint8_t *d_verdict,
+                                   void *d_scratch, uint32_t *d_status, unsigned max_ctas, void *stream);
+int april_ctx_num_sms(const april_ctx *ctx);
+int april_ctx_device(const april_ctx *ctx);
+
 // Host-side sets: per-entry descriptors and the interval slots exactly as
 // they are laid out in device memory by april_upload.  An entry is one
 // object's approximation on one grid: for sets built on one global grid the

@@ -660,7 +660,9 @@ static inline PartView part_view(const april_dev_sets *d) {
 // (partitioned sets only), K4 binning, K3 persistent filter.
 static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, const april_dev_sets *Sd,
                                    const uint32_t *d_r, const uint32_t *d_s, uint64_t n, uint8_t *out, void *scratch,
-                                   bool packed, unsigned grid_bin, unsigned grid_main, cudaStream_t st) {
+                                   bool packed, unsigned grid_bin, unsigned grid_main, cudaStream_t st,
+                                   uint32_t *status = nullptr) {
+    if (!status) status = ctx->d_status;
     uint32_t *counters = (uint32_t *)scratch;
     uint32_t *big_list = (uint32_t *)((char *)scratch + kCounterBytes);
     const april_tune &t = ctx->tune;
@@ -677,16 +679,16 @@ static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, con
     }
     if (packed) {
         const PackedSets R = packed_set(Rd), S = packed_set(Sd);
-        k_bin<<<grid_bin, 256, 0, st>>>(R, S, d_r, d_s, n, out, ctx->d_status, t.cta_threshold, big_list, counters);
-        k_persistent<32, PackedSets><<<grid_main, kBlock, 0, st>>>(R, S, d_r, d_s, n, out, ctx->d_status,
+        k_bin<<<grid_bin, 256, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold, big_list, counters);
+        k_persistent<32, PackedSets><<<grid_main, kBlock, 0, st>>>(R, S, d_r, d_s, n, out, status,
                                                                    t.cta_threshold, big_list, counters, 64u,
                                                                    t.cta_window);
         return cudaGetLastError();
     }
     const RawSets R{dev_set(Rd)}, S{dev_set(Sd)};
-    k_bin<<<grid_bin, 256, 0, st>>>(R, S, d_r, d_s, n, out, ctx->d_status, t.cta_threshold, big_list, counters);
+    k_bin<<<grid_bin, 256, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold, big_list, counters);
 #define APRIL_LAUNCH_PERSISTENT(G)                                                                            \
-    k_persistent<G, RawSets><<<grid_main, kBlock, 0, st>>>(R, S, d_r, d_s, n, out, ctx->d_status, t.cta_threshold, \
+    k_persistent<G, RawSets><<<grid_main, kBlock, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold,       \
                                                            big_list, counters, t.group_window, t.cta_window)
     switch (t.group_lanes) {
         case 4: APRIL_LAUNCH_PERSISTENT(4); break;
@@ -738,6 +740,29 @@ static april_status launch_batched(april_ctx *ctx, const april_dev_sets *R, cons
     ctx->graph_launches++;
     return APRIL_OK;
 }
+
+// Batched filter of one serving request (see server.cu): plain launches on
+// `st` (no graph: every request has its own buffers), at most `max_ctas`
+// persistent CTAs so that small requests leave SMs to the requests they
+// overlap with, and a per-request status word.
+april_status april_enqueue_request(april_ctx *ctx, const april_dev_sets *R, const april_dev_sets *S,
+                                   const uint32_t *d_r, const uint32_t *d_s, uint64_t n, uint8_t *d_verdict,
+                                   void *d_scratch, uint32_t *d_status, unsigned max_ctas, void *stream) {
+    if (n == 0) return APRIL_OK;
+    const bool packed = false;  // serving reads the raw lists
+    const unsigned grid_bin = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx->num_sms * 8));
+    const uint32_t gl = ctx->tune.group_lanes;
+    const int occ = ctx->persistent_blocks_per_sm[packed ? 4 : gl == 4 ? 0 : gl == 8 ? 1 : gl == 16 ? 2 : 3];
+    unsigned grid_main = (unsigned)std::max(1, ctx->num_sms * occ);
+    grid_main = std::min<unsigned>(grid_main, std::max<unsigned>(1, max_ctas));
+    cudaError_t e = enqueue_batched(ctx, R, S, d_r, d_s, n, d_verdict, d_scratch, packed, grid_bin, grid_main,
+                                    (cudaStream_t)stream, d_status);
+    if (e != cudaSuccess) return cuda_fail(e, "enqueueing a serving request");
+    return APRIL_OK;
+}
+
+int april_ctx_num_sms(const april_ctx *ctx) { return ctx->num_sms; }
+int april_ctx_device(const april_ctx *ctx) { return ctx->device; }
 
 extern "C" april_status april_filter_pairs(april_ctx *ctx, const april_dev_sets *R, const april_dev_sets *S,
                                            const uint32_t *d_r, const uint32_t *d_s, uint64_t n,

@@ -24,3 +24,7 @@ def oracle_verdicts(cfg: int, scale: float):
 def oracle_sample(w, idx):
     idx = np.asarray(idx)
     return oracle.verdicts(w.R.xy, w.R.off, w.S.xy, w.S.off, w.pr[idx], w.ps[idx], oracle.Grid(w.order))
+
+
+def oracle_sample_pairs(w, pr, ps):
+    return oracle.verdicts(w.R.xy, w.R.off, w.S.xy, w.S.off, np.asarray(pr), np.asarray(ps), oracle.Grid(w.order))
