@@ -48,11 +48,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3])
-    ap.add_argument("--mode", default="batched", choices=["batched", "warp", "plain"])
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4])
+    ap.add_argument("--mode", default="batched", choices=["batched", "warp", "plain", "packed"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tuning (profiling runs)")
+    ap.add_argument("--tune", default=None, help="T,G,W,CW: fixed batched tuning instead of the autotuner")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
     ap.add_argument("--serving-requests", type=int, default=120)
     return ap.parse_args()
@@ -66,16 +67,26 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def kernel_traffic(kernel: str, workload: str):
+def kernel_source_sha() -> str:
+    """Hash of the kernel sources a profile was taken on."""
+    h = hashlib.sha256()
+    for f in ("filter.cu", "join_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2307_01716_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def kernel_traffic(kernel: str, workload: str, tune):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel source."""
+    the current kernel sources with the same tuning."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
-    src = open(os.path.join(ROOT, "paper_2307_01716_gb300", "csrc", "filter.cu"), "rb").read()
-    sha = hashlib.sha256(src).hexdigest()[:16]
+    sha = kernel_source_sha()
+    key = None if tune is None else [tune["cta_threshold"], tune["group_lanes"], tune["group_window"],
+                                     tune["cta_window"]]
     for e in json.load(open(p)):
-        if e.get("kernel") == kernel and e.get("workload") == workload and e.get("src_sha") == sha:
+        if (e.get("kernel") == kernel and e.get("workload") == workload and e.get("src_sha") == sha
+                and e.get("tune") == key):
             return e.get("dram_bytes_per_launch")
     return None
 
@@ -128,17 +139,36 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def oracle_fn(w):
+    """f(pr, ps) -> the oracle's verdicts for workload w (partitioned
+    workloads: each pair on its routed partition's grid, the grids computed
+    once)."""
+    import oracle
+    if not w.partitions:
+        g = oracle.Grid(w.order)
+        return lambda pr, ps: oracle.verdicts(w.R.xy, w.R.off, w.S.xy, w.S.off, pr, ps, g)
+    grids = oracle.partition_areas(w.R.mbr, w.S.mbr, w.partitions, w.order)
+
+    def f(pr, ps):
+        part = oracle.route_pairs(w.R.mbr, w.S.mbr, pr, ps, w.partitions)
+        out = np.zeros(len(pr), dtype=np.uint8)
+        for p in np.unique(part):
+            sel = np.nonzero(part == p)[0]
+            out[sel] = oracle.verdicts(w.R.xy, w.R.off, w.S.xy, w.S.off, pr[sel], ps[sel], grids[int(p)])
+        return out
+    return f
+
+
 def cpu_baseline(w, seconds: float, seed: int = 1234):
     """The oracle, as it stands, on a bounded random sample of the pairs."""
-    import oracle
-    g = oracle.Grid(w.order)
+    f = oracle_fn(w)
     rng = np.random.default_rng(seed)
     done = 0
     t0 = time.perf_counter()
     batch = 200
     while time.perf_counter() - t0 < seconds:
         idx = np.sort(rng.choice(len(w.pr), batch, replace=False))
-        oracle.verdicts(w.R.xy, w.R.off, w.S.xy, w.S.off, w.pr[idx], w.ps[idx], g)
+        f(w.pr[idx], w.ps[idx])
         done += batch
     dt = time.perf_counter() - t0
     return {"value": done / dt, "unit": "pairs/s", "cores": 1, "kind": "oracle",
@@ -217,16 +247,15 @@ def run_reference(args):
     if rank != 0:
         return
     from synth import configs
-    import oracle
     w = configs.make(args.config)
-    g = oracle.Grid(w.order)
+    f = oracle_fn(w)
     rng = np.random.default_rng(99)
     per_step = 300
     times = []
     for step in range(args.warmup + args.steps):
         idx = np.sort(rng.choice(len(w.pr), per_step, replace=False))
         t0 = time.perf_counter()
-        oracle.verdicts(w.R.xy, w.R.off, w.S.xy, w.S.off, w.pr[idx], w.ps[idx], g)
+        f(w.pr[idx], w.ps[idx])
         if step >= args.warmup:
             times.append(time.perf_counter() - t0)
     value = per_step * len(times) / sum(times)
@@ -258,9 +287,15 @@ def main():
     dev = torch.device("cuda", local)
 
     w = configs.make(args.config)
-    grid = A.global_grid(w.order)
-    R = A.april_build_sets(w.R.xy, w.R.off, grid)
-    S = A.april_build_sets(w.S.xy, w.S.off, grid)
+    if w.partitions:
+        R, S = A.april_build_partitioned_sets(w.R.xy, w.R.off, w.S.xy, w.S.off, w.partitions, w.order)
+    else:
+        grid = A.global_grid(w.order)
+        R = A.april_build_sets(w.R.xy, w.R.off, grid)
+        S = A.april_build_sets(w.S.xy, w.S.off, grid)
+    if args.mode == "packed" or w.partitions:
+        R.compress()
+        S.compress()
     dR, dS = A.april_upload(R, dev), A.april_upload(S, dev)
     ctx = A.Context(local)
     n = len(w.pr)
@@ -274,8 +309,10 @@ def main():
     host_v, consumed = A.april_host_filter(R, S, w.pr, w.ps)
     b_alg = float(IV_BYTES * consumed.sum() + n * (PAIR_ID_BYTES + DESC_BYTES + VERDICT_BYTES))
 
+    mode_ids = dict(A.MODES, packed=A.MODE_BATCHED_PACKED)
+
     def make_runner(mode_name):
-        m = A.MODES[mode_name]
+        m = mode_ids[mode_name]
         sb = ctx.scratch_bytes(m, n)
         scratch = torch.empty(max(sb, 256), dtype=torch.uint8, device=dev) if sb else None
 
@@ -307,7 +344,11 @@ def main():
 
     mode = args.mode
     tune = None
-    if mode == "batched" and not args.no_autotune:
+    if mode in ("batched", "packed") and args.tune:
+        T, G, W, CW = (int(x) for x in args.tune.split(","))
+        ctx.set_tune(A.april_tune(T, G, W, CW, 0, 0.0))
+        tune = ctx.get_tune().as_dict()
+    elif mode in ("batched", "packed") and not args.no_autotune:
         # the project's autotuner picks the CTA threshold and first warp window
         m = A.MODE_BATCHED
         scratch = torch.empty(ctx.scratch_bytes(m, n), dtype=torch.uint8, device=dev)
@@ -316,20 +357,24 @@ def main():
     clocks = Clocks()
     clocks.start()
     t_main = time_mode(mode, args.steps, args.warmup)
-    t_plain = time_mode("plain", max(3, args.steps // 2), args.warmup) if mode != "plain" else t_main
-    t_warp = time_mode("warp", args.steps, args.warmup) if mode == "batched" else None
+    if w.partitions:  # partitioned sets run only in the batched modes
+        t_plain = None
+        t_warp = None
+        t_other = time_mode("packed" if mode == "batched" else "batched", args.steps, args.warmup)
+    else:
+        t_plain = time_mode("plain", max(3, args.steps // 2), args.warmup) if mode != "plain" else t_main
+        t_warp = time_mode("warp", args.steps, args.warmup) if mode == "batched" else None
+        t_other = None
 
+    from paper_2307_01716_gb300 import dist as D
     ms = statistics.mean(t_main)
-    ms_t = torch.tensor([ms], device=dev)
-    if ws > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = D.max_over_ranks(ms, ws, device=dev)
     value = ws * n / (ms_max * 1e-3)
-    plain_ms = statistics.mean(t_plain)
+    plain_ms = statistics.mean(t_plain) if t_plain else None
 
     # end to end through the host-buffer entry point (pinned host pairs in,
     # host verdicts out, copies inside the timed region)
-    m = A.MODES[mode]
+    m = mode_ids[mode]
     work = torch.empty(ctx.host_work_bytes(m, n), dtype=torch.uint8, device=dev)
     h_r = torch.from_numpy(w.pr.view(np.int32)).pin_memory()
     h_s = torch.from_numpy(w.ps.view(np.int32)).pin_memory()
@@ -350,9 +395,10 @@ def main():
 
     peak, peak_kind = peaks()
     achieved = b_alg / (ms * 1e-3) / 1e9
-    kernel_name = {"plain": "k_plain", "warp": "k_warp", "batched": "k_persistent"}[mode]
-    traffic = kernel_traffic(kernel_name, w.name)
-    launches = {"plain": 1, "warp": 1, "batched": 2}[mode]  # batched: binning + persistent kernel
+    kernel_name = {"plain": "k_plain", "warp": "k_warp", "batched": "k_persistent", "packed": "k_persistent"}[mode]
+    traffic = kernel_traffic(kernel_name, w.name, tune)
+    # batched: binning + persistent kernel (+ routing for partitioned sets)
+    launches = {"plain": 1, "warp": 1, "batched": 2, "packed": 2}[mode] + (1 if w.partitions else 0)
 
     line = {
         "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
@@ -360,9 +406,16 @@ def main():
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": w.name, "polygons_per_side": int(w.R.n), "grid_order": w.order,
                    "pairs": n, "mode": mode, "l2": "flushed between timed steps (256 MB write)",
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-        "plain": {"pairs_per_s": n / (plain_ms * 1e-3), "ms_per_step": plain_ms,
-                  "speedup_of_mode": plain_ms / ms},
+                   "parallelism": (f"dp{ws}: every rank filters its own full batch of pairs against its own "
+                                  "resident sets; no collective on the data path") if ws > 1 else "single GPU"},
+        "plain": None if plain_ms is None else {"pairs_per_s": n / (plain_ms * 1e-3), "ms_per_step": plain_ms,
+                                                "speedup_of_mode": plain_ms / ms},
+        "other_batched_mode": None if t_other is None else {
+            "mode": "packed" if mode == "batched" else "batched",
+            "pairs_per_s": n / (statistics.mean(t_other) * 1e-3), "ms_per_step": statistics.mean(t_other)},
+        "sets": {"raw_list_bytes_per_side": [int(R.info().raw_list_bytes), int(S.info().raw_list_bytes)],
+                 "packed_list_bytes_per_side": [int(R.info().packed_list_bytes), int(S.info().packed_list_bytes)],
+                 "entries_per_side": [int(R.info().n_entries), int(S.info().n_entries)]},
         "warp": None if t_warp is None else {"pairs_per_s": n / (statistics.mean(t_warp) * 1e-3),
                                              "ms_per_step": statistics.mean(t_warp)},
         "useful_GBps": achieved,
@@ -384,6 +437,7 @@ def main():
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
+        dist.barrier()  # the other ranks wait for rank 0's serving and CPU legs
         dist.destroy_process_group()
 
 
