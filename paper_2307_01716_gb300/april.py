@@ -14,7 +14,7 @@ from dataclasses import dataclass
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libapril.so")
+LIB_PATH = os.environ.get("APRIL_LIB", os.path.join(HERE, "libapril.so"))
 
 APRIL_OK = 0
 APRIL_PENDING = 1
@@ -130,7 +130,7 @@ def load():
     global _lib
     if _lib is None:
         from . import build as _build
-        if not _build.up_to_date():
+        if LIB_PATH == _build.OUT and not _build.up_to_date():
             _build.build()
         if not os.path.exists(LIB_PATH):
             raise ImportError(f"libapril.so missing at {LIB_PATH}")

@@ -37,22 +37,26 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(s) <= t for s in _sources() if os.path.exists(s))
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, out: str | None = None, defines=()) -> str:
+    """Compile libapril.so (or `out`), with optional -D definitions."""
+    target = out or OUT
+    if not force and out is None and up_to_date():
         return OUT
-    os.makedirs(BUILD, exist_ok=True)
+    build_dir = BUILD if out is None else out + "_build"
+    os.makedirs(build_dir, exist_ok=True)
+    dflags = [f"-D{d}" for d in defines]
     nvcc = _nvcc()
     jobs = []
     objs = []
     for s in CXX_SOURCES:
-        o = os.path.join(BUILD, s + ".o")
+        o = os.path.join(build_dir, s + ".o")
         objs.append(o)
-        jobs.append(["g++", "-O3", "-std=c++17", "-fPIC", "-pthread", "-Wall", "-c",
+        jobs.append(["g++", "-O3", "-std=c++17", "-fPIC", "-pthread", "-Wall", *dflags, "-c",
                      os.path.join(CSRC, s), "-o", o])
     for s in CU_SOURCES:
-        o = os.path.join(BUILD, s + ".o")
+        o = os.path.join(build_dir, s + ".o")
         objs.append(o)
-        jobs.append([nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+        jobs.append([nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", *dflags,
                      "--expt-relaxed-constexpr", "-Xptxas", "-v" if verbose else "-O3",
                      "-c", os.path.join(CSRC, s), "-o", o])
     procs = [subprocess.Popen(j, stdout=subprocess.PIPE, stderr=subprocess.STDOUT) for j in jobs]
@@ -65,10 +69,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
             failed.append(" ".join(j))
     if failed:
         raise RuntimeError("compilation failed: " + "; ".join(failed))
-    tmp = OUT + f".tmp{os.getpid()}"
+    tmp = target + f".tmp{os.getpid()}"
     subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"])
-    os.replace(tmp, OUT)
-    return OUT
+    os.replace(tmp, target)
+    return target
 
 
 if __name__ == "__main__":

@@ -50,7 +50,7 @@ struct april_sets {
 inline uint64_t april_round256(uint64_t b) { return (b + 255) / 256 * 256; }
 
 // Device image layout (each section starts 256-byte aligned):
-//   desc (16 B/entry) | iv (8 B/slot) | obj_ll (8 B/object) | obj_entry (4 B x (n+1))
+//   desc (16 B/entry) | iv (8 B/slot, then a 16-byte pad) | obj_ll (8 B/object) | obj_entry (4 B x (n+1))
 //   | entry_pid (4 B/entry) | pdesc (16 B/entry) | block table (8 B/block) | gaps
 struct april_image_layout {
     uint64_t desc, iv, obj_ll, obj_entry, entry_pid, pdesc, anchors, gaps, total;
@@ -62,7 +62,7 @@ inline april_image_layout april_layout(const april_sets &S) {
     L.desc = o;
     o += april_round256((uint64_t)S.n_entries * 16);
     L.iv = o;
-    o += april_round256((uint64_t)S.iv.size() * 4);
+    o += april_round256((uint64_t)S.iv.size() * 4 + 16);  // 16-byte pad: bulk copies round spans up to 16 bytes
     L.obj_ll = o;
     o += april_round256((uint64_t)S.obj_ll.size() * 4);
     L.obj_entry = o;

@@ -50,7 +50,21 @@ constexpr uint32_t kCtaWMax = 2048;              // largest CTA window per list
 constexpr uint32_t kWarpFirstWindow = 64;        // first window of a join in APRIL_MODE_WARP
 constexpr uint32_t kWarpBuf = kWarpWMax + 2;     // staging buffer per list (odd start + rounding)
 constexpr uint32_t kCtaBuf = kCtaWMax + 2;
-constexpr uint32_t kWarpShare = 544;             // intervals of shared staging per warp (all group sizes fit)
+// Compile-time knobs (defaults are the shipped configuration):
+//   APRIL_MIN_BLOCKS  minimum resident CTAs per SM requested for k_persistent
+//   APRIL_GROUP_PER   diagonals each lane walks per window in the group engine
+#ifdef APRIL_MIN_BLOCKS
+#define APRIL_PERSISTENT_BOUNDS __launch_bounds__(256, APRIL_MIN_BLOCKS)
+#else
+#define APRIL_PERSISTENT_BOUNDS __launch_bounds__(256)
+#endif
+#ifndef APRIL_GROUP_PER
+#define APRIL_GROUP_PER 8
+#endif
+constexpr uint32_t kGroupPer = APRIL_GROUP_PER;
+// intervals of shared staging per warp: the largest of 2 lists x (32/G groups)
+// x (kGroupPer*G + 2) over the group sizes, and 2 x kWarpBuf for whole warps
+constexpr uint32_t kWarpShare = 64 * kGroupPer + 32 > 2 * (kWarpWMax + 2) ? 64 * kGroupPer + 32 : 2 * (kWarpWMax + 2);
 constexpr uint32_t kSharedIv = kWarpsPerBlock * kWarpShare;  // one buffer serves both phases
 static_assert(2 * kCtaBuf <= kSharedIv, "CTA windows must fit in the warps' buffers");
 static_assert(kWarpBuf % 2 == 0 && kCtaBuf % 2 == 0, "buffers must stay 16-byte aligned");
@@ -119,31 +133,49 @@ __global__ void __launch_bounds__(256) k_plain(DevSet R, DevSet S, const uint32_
 
 // Algorithm 2 for one pair by one warp: AA; if no overlap, a true negative;
 // else AF, then FA.
+// Shared-memory synchronisation state of a warp or CTA join: the mbarrier the
+// window copies complete on, its phase bit, and a timeout flag.
+struct JoinSync {
+    uint32_t bar;
+    uint32_t phase;
+    bool timeout;
+};
+
 template <class SetsT>
 __device__ __forceinline__ uint8_t warp_verdict(const SetsT &R, const SetsT &S, const typename SetsT::Desc &dr,
                                                 const typename SetsT::Desc &ds, uint2 *xs, uint2 *ys, uint32_t lane,
-                                                uint32_t w0) {
-    if (!tile_join<WarpScope, 32, kWarpWMax>(R.list(dr, false), S.list(ds, false), xs, ys, nullptr, lane, w0))
-        return APRIL_TRUE_NEGATIVE;
-    if (tile_join<WarpScope, 32, kWarpWMax>(R.list(dr, false), S.list(ds, true), xs, ys, nullptr, lane, w0))
+                                                uint32_t w0, JoinSync &js) {
+    const uint32_t b = js.bar;
+    if (!tile_join<WarpScope, 32, kWarpWMax>(R.list(dr, false), S.list(ds, false), xs, ys, nullptr, lane, w0, b,
+                                              &js.phase, &js.timeout))
+        return js.timeout ? APRIL_VERDICT_ERROR : APRIL_TRUE_NEGATIVE;
+    if (tile_join<WarpScope, 32, kWarpWMax>(R.list(dr, false), S.list(ds, true), xs, ys, nullptr, lane, w0, b,
+                                             &js.phase, &js.timeout))
         return APRIL_TRUE_HIT;
-    if (tile_join<WarpScope, 32, kWarpWMax>(R.list(dr, true), S.list(ds, false), xs, ys, nullptr, lane, w0))
+    if (js.timeout) return APRIL_VERDICT_ERROR;
+    if (tile_join<WarpScope, 32, kWarpWMax>(R.list(dr, true), S.list(ds, false), xs, ys, nullptr, lane, w0, b,
+                                             &js.phase, &js.timeout))
         return APRIL_TRUE_HIT;
-    return APRIL_INCONCLUSIVE;
+    return js.timeout ? APRIL_VERDICT_ERROR : APRIL_INCONCLUSIVE;
 }
 
 // Algorithm 2 for one pair by the whole CTA.
 template <class SetsT>
 __device__ __forceinline__ uint8_t cta_verdict(const SetsT &R, const SetsT &S, const typename SetsT::Desc &dr,
                                                const typename SetsT::Desc &ds, uint2 *xs, uint2 *ys, uint32_t *slot,
-                                               uint32_t tid, uint32_t w0) {
-    if (!tile_join<CtaScope, kBlock, kCtaWMax>(R.list(dr, false), S.list(ds, false), xs, ys, slot, tid, w0))
-        return APRIL_TRUE_NEGATIVE;
-    if (tile_join<CtaScope, kBlock, kCtaWMax>(R.list(dr, false), S.list(ds, true), xs, ys, slot, tid, w0))
+                                               uint32_t tid, uint32_t w0, JoinSync &js) {
+    const uint32_t b = js.bar;
+    if (!tile_join<CtaScope, kBlock, kCtaWMax>(R.list(dr, false), S.list(ds, false), xs, ys, slot, tid, w0, b,
+                                               &js.phase, &js.timeout))
+        return js.timeout ? APRIL_VERDICT_ERROR : APRIL_TRUE_NEGATIVE;
+    if (tile_join<CtaScope, kBlock, kCtaWMax>(R.list(dr, false), S.list(ds, true), xs, ys, slot, tid, w0, b,
+                                              &js.phase, &js.timeout))
         return APRIL_TRUE_HIT;
-    if (tile_join<CtaScope, kBlock, kCtaWMax>(R.list(dr, true), S.list(ds, false), xs, ys, slot, tid, w0))
+    if (js.timeout) return APRIL_VERDICT_ERROR;
+    if (tile_join<CtaScope, kBlock, kCtaWMax>(R.list(dr, true), S.list(ds, false), xs, ys, slot, tid, w0, b,
+                                              &js.phase, &js.timeout))
         return APRIL_TRUE_HIT;
-    return APRIL_INCONCLUSIVE;
+    return js.timeout ? APRIL_VERDICT_ERROR : APRIL_INCONCLUSIVE;
 }
 
 // One warp filters the 32 pairs starting at `base`: every lane fetches the
@@ -152,10 +184,11 @@ __device__ __forceinline__ uint8_t cta_verdict(const SetsT &R, const SetsT &S, c
 // whose cost |A(r)| + |A(s)| exceeds cta_threshold are left to the CTA phase
 // (pass UINT32_MAX to take every pair).
 template <class SetsT>
-__device__ __forceinline__ void warp_chunk(const SetsT &R, const SetsT &S, const uint32_t *__restrict__ pr,
+__device__ __forceinline__ bool warp_chunk(const SetsT &R, const SetsT &S, const uint32_t *__restrict__ pr,
                                            const uint32_t *__restrict__ ps, uint64_t n, uint64_t base,
                                            uint8_t *__restrict__ out, uint32_t *status, uint2 *xs, uint2 *ys,
-                                           uint32_t lane, uint32_t w0, uint32_t cta_threshold, bool flag_bad) {
+                                           uint32_t lane, uint32_t w0, uint32_t cta_threshold, bool flag_bad,
+                                           JoinSync &js) {
     const uint64_t k = base + lane;
     typename SetsT::Desc dr{}, ds{};
     bool take = false;
@@ -176,10 +209,23 @@ __device__ __forceinline__ void warp_chunk(const SetsT &R, const SetsT &S, const
         const uint32_t t = __ffs(todo) - 1;
         todo &= todo - 1;
         const typename SetsT::Desc a = SetsT::shfl(dr, t), b = SetsT::shfl(ds, t);
-        const uint8_t v = warp_verdict(R, S, a, b, xs, ys, lane, w0);
+        const uint8_t v = warp_verdict(R, S, a, b, xs, ys, lane, w0, js);
         if (lane == t) mine = v;
+        if (js.timeout) {
+            if (lane == 0) atomicOr(status, ST_TIMEOUT);
+            return false;
+        }
     }
     if (take) out[k] = mine;
+    return true;
+}
+
+// Initialises `count` mbarriers (8 bytes each, 8-byte aligned) at bars;
+// every thread of the block must call it.
+__device__ __forceinline__ void init_barriers(uint64_t *bars, uint32_t count) {
+    for (uint32_t i = threadIdx.x; i < count; i += blockDim.x) mbar_init(smem_addr(bars + i), 1);
+    if (threadIdx.x == 0) mbar_init_fence();
+    __syncthreads();
 }
 
 // ------------------------------------------------------- K1: warp/pair
@@ -187,11 +233,15 @@ __global__ void __launch_bounds__(kBlock) k_warp(DevSet R, DevSet S, const uint3
                                                  const uint32_t *__restrict__ ps, uint64_t n,
                                                  uint8_t *__restrict__ out, uint32_t *status, uint32_t w0) {
     __shared__ __align__(16) uint2 sm[kWarpsPerBlock][2][kWarpBuf];
+    __shared__ uint64_t bars[kWarpsPerBlock];
+    init_barriers(bars, kWarpsPerBlock);
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    JoinSync js{smem_addr(&bars[warp]), 0u, false};
     const uint64_t stride = (uint64_t)gridDim.x * kWarpsPerBlock * 32;
     for (uint64_t base = ((uint64_t)blockIdx.x * kWarpsPerBlock + warp) * 32; base < n; base += stride)
-        warp_chunk(RawSets{R}, RawSets{S}, pr, ps, n, base, out, status, sm[warp][0], sm[warp][1], lane, w0,
-                   0xffffffffu, true);
+        if (!warp_chunk(RawSets{R}, RawSets{S}, pr, ps, n, base, out, status, sm[warp][0], sm[warp][1], lane, w0,
+                        0xffffffffu, true, js))
+            return;
 }
 
 // --------------------------------------------- K4: length binning (batched)
@@ -241,7 +291,7 @@ __global__ void __launch_bounds__(256) k_bin(SetsT R, SetsT S, const uint32_t *_
 template <uint32_t G>
 struct GroupCfg {
     static constexpr uint32_t NG = 32 / G;
-    static constexpr uint32_t WMAX = 8 * G;
+    static constexpr uint32_t WMAX = kGroupPer * G;
     static constexpr uint32_t BUF = WMAX + 2;
     static constexpr uint32_t LEADS = G == 32 ? 1u : G == 16 ? 0x00010001u : G == 8 ? 0x01010101u : 0x11111111u;
 };
@@ -264,12 +314,14 @@ __device__ __forceinline__ bool join_lists(const DevSet &R, const DevSet &S, con
 template <uint32_t G>
 __device__ __forceinline__ void group_engine(const DevSet &R, const DevSet &S, const uint32_t *__restrict__ pr,
                                              const uint32_t *__restrict__ ps, uint64_t n, uint8_t *__restrict__ out,
-                                             uint32_t *counters, uint32_t cta_threshold, uint2 *wbuf, uint32_t lane,
-                                             uint32_t w0) {
+                                             uint32_t *status, uint32_t *counters, uint32_t cta_threshold, uint2 *wbuf,
+                                             uint32_t bars, uint32_t lane, uint32_t w0) {
     using C = GroupCfg<G>;
     const uint32_t g = lane / G, t = lane % G, glead = g * G;
     const uint32_t gbits = (G == 32 ? kFull : ((1u << G) - 1u)) << glead;
     uint2 *xb = wbuf + g * 2 * C::BUF, *yb = xb + C::BUF;
+    const uint32_t bar = bars + 8u * g;  // this group's mbarrier
+    uint32_t phase = 0;
     const uint64_t nchunks = (n + 31) / 32;
     // the warp's chunk: lane l holds pair base + l
     uint64_t qk = 0;
@@ -332,22 +384,38 @@ __device__ __forceinline__ void group_engine(const DevSet &R, const DevSet &S, c
         if (!__any_sync(kFull, active)) break;  // only reachable once the pairs are exhausted
 
         // -------- one window of every active group's join
+        // each active group's window arrives by two bulk copies on its mbarrier
         uint32_t nx = 0, ny = 0, xa = 0, ya = 0;
+        bool ok = true;
         if (active) {
             nx = min(w, nX - i0);
             ny = min(w, nY - j0);
-            xa = smem_addr(stage_window<G>(xb, X + i0, nx, t));
-            ya = smem_addr(stage_window<G>(yb, Y + j0, ny, t));
+            if (t == 0) {
+                fence_proxy_async();
+                const uint2 *a;
+                uint32_t bx, by, ox, oy;
+                bulk_span(X + i0, nx, a, bx, ox);
+                bulk_span(Y + j0, ny, a, by, oy);
+                mbar_arrive_expect_tx(bar, bx + by);
+                bulk_load(smem_addr(xb), X + i0 - ox, bx, bar);
+                bulk_load(smem_addr(yb), Y + j0 - oy, by, bar);
+            }
+            ok = mbar_wait(bar, phase);
+            phase ^= 1u;
+            xa = smem_addr(xb) + 8u * (uint32_t)(((uintptr_t)(X + i0) >> 3) & 1u);
+            ya = smem_addr(yb) + 8u * (uint32_t)(((uintptr_t)(Y + j0) >> 3) & 1u);
         }
-        cp_async_wait_all();
-        __syncwarp();
+        if (!__all_sync(kFull, ok)) {  // a bounded wait ran out: report and stop this warp
+            if (lane == 0) atomicOr(status, ST_TIMEOUT);
+            return;
+        }
         bool found = false;
         uint32_t state = 0xffffffffu, D = 0, owner = 0;
         if (active) {
             D = min(w, nx + ny);
             const uint32_t per = w / G;
             owner = (D - 1) / per;
-            found = window_walk(xa, nx, ya, ny, w, D, per, t * per, state);
+            found = window_walk<C::WMAX / G>(xa, nx, ya, ny, w, D, per, t * per, state);
         }
         const uint32_t fmask = __ballot_sync(kFull, found);  // every read of the windows is done here
         const uint32_t split = __shfl_sync(kFull, state, glead + owner);
@@ -387,15 +455,20 @@ __device__ __forceinline__ void group_engine(const DevSet &R, const DevSet &S, c
 // on the short pairs.  Work is handed out by atomic counters; nothing waits
 // on another CTA.
 template <uint32_t G, class SetsT>
-__global__ void __launch_bounds__(kBlock) k_persistent(SetsT R, SetsT S, const uint32_t *__restrict__ pr,
+__global__ void APRIL_PERSISTENT_BOUNDS k_persistent(SetsT R, SetsT S,
+                                                                         const uint32_t *__restrict__ pr,
                                                        const uint32_t *__restrict__ ps, uint64_t n,
                                                        uint8_t *__restrict__ out, uint32_t *status,
                                                        uint32_t cta_threshold, const uint32_t *__restrict__ big_list,
                                                        uint32_t *counters, uint32_t w0_group, uint32_t w0_cta) {
     __shared__ __align__(16) uint2 sm[kSharedIv];
     __shared__ uint32_t s_item, s_slot;
+    // mbarriers: [0] the CTA phase, [1 + warp * 8 + group] the group engine
+    __shared__ uint64_t bars[1 + kWarpsPerBlock * 8];
+    init_barriers(bars, 1 + kWarpsPerBlock * 8);
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const uint32_t nbig = *((volatile uint32_t *)&counters[C_BIG_COUNT]);
+    JoinSync cs{smem_addr(&bars[0]), 0u, false};
     for (;;) {
         if (tid == 0) s_item = atomicAdd(&counters[C_BIG_HEAD], 1u);
         __syncthreads();
@@ -404,23 +477,30 @@ __global__ void __launch_bounds__(kBlock) k_persistent(SetsT R, SetsT S, const u
         if (it >= nbig) break;
         const uint64_t k = big_list[it];
         const typename SetsT::Desc dr = R.load(__ldg(pr + k)), ds = S.load(__ldg(ps + k));
-        const uint8_t v = cta_verdict(R, S, dr, ds, sm, sm + kCtaBuf, &s_slot, tid, w0_cta);
+        const uint8_t v = cta_verdict(R, S, dr, ds, sm, sm + kCtaBuf, &s_slot, tid, w0_cta, cs);
         if (tid == 0) out[k] = v;
+        if (cs.timeout) {  // a bounded wait ran out: report and stop this CTA
+            if (tid == 0) atomicOr(status, ST_TIMEOUT);
+            return;
+        }
     }
     __syncthreads();
     uint2 *wbuf = sm + warp * kWarpShare;
     if constexpr (G == 32 || SetsT::kPacked) {
+        JoinSync js{smem_addr(&bars[1 + warp * 8]), 0u, false};
         const uint64_t nchunks = (n + 31) / 32;
         for (;;) {
             uint32_t c = 0;
             if (lane == 0) c = atomicAdd(&counters[C_CHUNK_HEAD], 1u);
             c = __shfl_sync(kFull, c, 0);
             if (c >= nchunks) break;
-            warp_chunk(R, S, pr, ps, n, (uint64_t)c * 32, out, status, wbuf, wbuf + kWarpBuf, lane, w0_group,
-                       cta_threshold, false);
+            if (!warp_chunk(R, S, pr, ps, n, (uint64_t)c * 32, out, status, wbuf, wbuf + kWarpBuf, lane, w0_group,
+                            cta_threshold, false, js))
+                return;
         }
     } else {
-        group_engine<G>(R.s, S.s, pr, ps, n, out, counters, cta_threshold, wbuf, lane, w0_group);
+        group_engine<G>(R.s, S.s, pr, ps, n, out, status, counters, cta_threshold, wbuf, smem_addr(&bars[1 + warp * 8]),
+                        lane, w0_group);
     }
 }
 
@@ -520,7 +600,8 @@ static april_tune default_tune() {
 static april_status check_tune(const april_tune &t) {
     const uint32_t G = t.group_lanes;
     if (G != 4 && G != 8 && G != 16 && G != 32) return fail(APRIL_ERR_INVALID_ARG, "group_lanes must be 4, 8, 16 or 32");
-    if (t.group_window < G || t.group_window > 8 * G || (t.group_window & (t.group_window - 1)))
+    const uint32_t gmax = G == 32 ? kWarpWMax : kGroupPer * G;
+    if (t.group_window < G || t.group_window > gmax || (t.group_window & (t.group_window - 1)))
         return fail(APRIL_ERR_INVALID_ARG, "group_window must be a power of two in [group_lanes, 8*group_lanes]");
     if (t.cta_window < kBlock || t.cta_window > kCtaWMax || (t.cta_window & (t.cta_window - 1)))
         return fail(APRIL_ERR_INVALID_ARG, "cta_window must be a power of two in [256, 2048]");

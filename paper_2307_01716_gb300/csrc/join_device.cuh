@@ -78,11 +78,27 @@ __device__ __forceinline__ uint32_t lds1(uint32_t a) {
 // Merge-path split of the windows at shared addresses xa (nx intervals) and
 // ya (ny intervals) at diagonal d: the number of X elements among the first
 // d merged elements (X first on equal `last`).
+#ifndef APRIL_SEARCH_FIXED
+#define APRIL_SEARCH_FIXED 0
+#endif
 __device__ __forceinline__ uint32_t merge_split(uint32_t xa, uint32_t nx, uint32_t ya, uint32_t ny, uint32_t d) {
     uint32_t lo = d > ny ? d - ny : 0u, hi = min(d, nx);
     // compares X[mid].last <= Y[d-mid-1].last; the byte offsets of the two
     // `end` words move in opposite directions as mid changes
     const uint32_t yb = ya + 8u * (d - 1u) + 4u;
+#if APRIL_SEARCH_FIXED
+    // a fixed trip count (windows hold at most 2048 intervals): no divergence
+#pragma unroll
+    for (int it = 0; it < 12; ++it) {
+        if (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            const uint32_t xl = lds1(xa + 8u * mid + 4u) - 1u;
+            const uint32_t yl = lds1(yb - 8u * mid) - 1u;
+            if (xl <= yl) lo = mid + 1;
+            else hi = mid;
+        }
+    }
+#else
     while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
         const uint32_t xl = lds1(xa + 8u * mid + 4u) - 1u;
@@ -90,6 +106,7 @@ __device__ __forceinline__ uint32_t merge_split(uint32_t xa, uint32_t nx, uint32
         if (xl <= yl) lo = mid + 1;
         else hi = mid;
     }
+#endif
     return lo;
 }
 
@@ -135,7 +152,8 @@ __device__ __forceinline__ bool walk_checked(uint32_t xa, uint32_t nx, uint32_t 
 }
 
 // The merge-path work of one thread in a window of D diagonals (w per list,
-// nx/ny staged): diagonals [d0, d0 + per).
+// nx/ny staged): diagonals [d0, d0 + per), per a power of two <= MAXPER.
+template <uint32_t MAXPER>
 __device__ __forceinline__ bool window_walk(uint32_t xa, uint32_t nx, uint32_t ya, uint32_t ny, uint32_t w,
                                             uint32_t D, uint32_t per, uint32_t d0, uint32_t &state) {
     state = 0xffffffffu;
@@ -143,11 +161,21 @@ __device__ __forceinline__ bool window_walk(uint32_t xa, uint32_t nx, uint32_t y
     const uint32_t i = merge_split(xa, nx, ya, ny, d0);
     const uint32_t j = d0 - i;
     if (nx == w && ny == w) {
-        switch (per) {
-            case 1: return walk_fixed<1>(xa, ya, i, j, state);
-            case 2: return walk_fixed<2>(xa, ya, i, j, state);
-            case 4: return walk_fixed<4>(xa, ya, i, j, state);
-            default: return walk_fixed<8>(xa, ya, i, j, state);
+        if constexpr (MAXPER >= 16) {
+            switch (per) {
+                case 1: return walk_fixed<1>(xa, ya, i, j, state);
+                case 2: return walk_fixed<2>(xa, ya, i, j, state);
+                case 4: return walk_fixed<4>(xa, ya, i, j, state);
+                case 8: return walk_fixed<8>(xa, ya, i, j, state);
+                default: return walk_fixed<16>(xa, ya, i, j, state);
+            }
+        } else {
+            switch (per) {
+                case 1: return walk_fixed<1>(xa, ya, i, j, state);
+                case 2: return walk_fixed<2>(xa, ya, i, j, state);
+                case 4: return walk_fixed<4>(xa, ya, i, j, state);
+                default: return walk_fixed<8>(xa, ya, i, j, state);
+            }
         }
     }
     return walk_checked(xa, nx, ya, ny, i, j, min(per, D - d0), state);
@@ -155,6 +183,7 @@ __device__ __forceinline__ bool window_walk(uint32_t xa, uint32_t nx, uint32_t y
 
 struct WarpScope {
     static __device__ __forceinline__ void sync() { __syncwarp(); }
+    static __device__ __forceinline__ bool all(bool b) { return __all_sync(kFull, b) != 0; }
     // OR of `b` over the group; `v` from thread `src` is returned to all.
     // Doubles as the point after which the window may be overwritten.
     static __device__ __forceinline__ bool vote(bool b, uint32_t &v, uint32_t src, uint32_t *) {
@@ -165,6 +194,7 @@ struct WarpScope {
 
 struct CtaScope {
     static __device__ __forceinline__ void sync() { __syncthreads(); }
+    static __device__ __forceinline__ bool all(bool b) { return __syncthreads_and(b) != 0; }
     static __device__ __forceinline__ bool vote(bool b, uint32_t &v, uint32_t src, uint32_t *slot) {
         if (threadIdx.x == src) *slot = v;
         const bool any = __syncthreads_or(b) != 0;
@@ -172,6 +202,61 @@ struct CtaScope {
         return any;
     }
 };
+
+// ----- TMA bulk copies and mbarriers (sm_90+ PTX; used on sm_103a) -----
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// Orders this thread's earlier generic-proxy accesses of shared memory before
+// later async-proxy (bulk copy) writes to it.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// One-dimensional bulk copy global -> shared; completes `bytes` on the mbarrier.
+// dst, src and bytes must be multiples of 16.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// Spins on the mbarrier phase with an iteration limit; false if it ran out.
+constexpr uint32_t kMbarSpinLimit = 1u << 24;
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
+    for (uint32_t k = 0; k < kMbarSpinLimit; ++k)
+        if (mbar_try_wait(bar, phase)) return true;
+    return false;
+}
+
+// Window staging by bulk copy: the 16-byte aligned span around src[0..cnt)
+// (src - 1 when src is odd, rounded up to an even count) is copied to buf;
+// returns the shared address of src[0] inside buf and the byte count.  The
+// device image ends with a 16-byte pad, so the rounding never leaves it.
+__device__ __forceinline__ uint32_t bulk_span(const uint2 *src, uint32_t cnt, const uint2 *&a, uint32_t &bytes,
+                                              uint32_t &odd) {
+    odd = (uint32_t)(((uintptr_t)src >> 3) & 1u);
+    a = src - odd;
+    bytes = ((cnt + odd + 1) & ~1u) * 8u;
+    return odd * 8u;
+}
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -199,15 +284,28 @@ __device__ __forceinline__ uint2 *stage_window(uint2 *buf, const uint2 *src, uin
 // a running sum over the block) and stored to shared memory as intervals.
 // Either way the window's intervals end up at the returned shared address.
 struct RawList {
+    static constexpr bool kBulk = true;
     const uint2 *p;
     uint32_t n;
     template <uint32_t NT>
     __device__ __forceinline__ uint32_t stage(uint2 *buf, uint32_t i0, uint32_t cnt, uint32_t tid) const {
         return smem_addr(stage_window<NT>(buf, p + i0, cnt, tid));
     }
+    // Bulk-copy form: called by the one issuing thread; returns bytes in flight.
+    __device__ __forceinline__ uint32_t issue(uint2 *buf, uint32_t i0, uint32_t cnt, uint32_t bar) const {
+        const uint2 *a;
+        uint32_t bytes, odd;
+        bulk_span(p + i0, cnt, a, bytes, odd);
+        bulk_load(smem_addr(buf), a, bytes, bar);
+        return bytes;
+    }
+    __device__ __forceinline__ uint32_t window(const uint2 *buf, uint32_t i0) const {
+        return smem_addr(buf) + 8u * (uint32_t)(((uintptr_t)(p + i0) >> 3) & 1u);
+    }
 };
 
 struct PackedList {
+    static constexpr bool kBulk = false;
     const uint2 *blocks;  // per block {anchor, gap_off64 | wide << 31}
     const uint8_t *gaps;  // the set's gap stream
     uint32_t n;
@@ -255,6 +353,8 @@ struct PackedList {
         }
         return base;
     }
+    __device__ __forceinline__ uint32_t issue(uint2 *, uint32_t, uint32_t, uint32_t) const { return 0; }
+    __device__ __forceinline__ uint32_t window(const uint2 *buf, uint32_t) const { return smem_addr(buf); }
 };
 
 // Any overlap between lists X and Y, by a group of NT threads (thread
@@ -262,24 +362,49 @@ struct PackedList {
 // aligned) and, for a CTA group, one shared word `slot`.  The first window
 // holds w0 intervals per list (a multiple of NT); later windows double up to
 // WMAX.  Every thread of the group must call it with the same arguments.
+// For raw lists the window is staged by two bulk copies issued by thread 0
+// and completed on the mbarrier `bar` (phase bit in *phase, flipped per
+// window); a wait that runs out sets *timeout and ends the join.
 template <class Scope, uint32_t NT, uint32_t WMAX, class ListT>
 __device__ __noinline__ bool tile_join(const ListT X, const ListT Y, uint2 *xb, uint2 *yb, uint32_t *slot,
-                                       uint32_t tid, uint32_t w0) {
+                                       uint32_t tid, uint32_t w0, uint32_t bar, uint32_t *phase, bool *timeout) {
     const uint32_t n = X.n, m = Y.n;
     uint32_t i0 = 0, j0 = 0, w = w0;
     while (i0 < n && j0 < m) {
         const uint32_t nx = min(w, n - i0), ny = min(w, m - j0);
-        const uint32_t xa = X.template stage<NT>(xb, i0, nx, tid);
-        const uint32_t ya = Y.template stage<NT>(yb, j0, ny, tid);
-        cp_async_wait_all();
-        Scope::sync();
+        uint32_t xa, ya;
+        if constexpr (ListT::kBulk) {
+            if (tid == 0) {
+                fence_proxy_async();
+                const uint2 *a;
+                uint32_t bx, by, ox, oy;
+                bulk_span(X.p + i0, nx, a, bx, ox);
+                bulk_span(Y.p + j0, ny, a, by, oy);
+                mbar_arrive_expect_tx(bar, bx + by);
+                X.issue(xb, i0, nx, bar);
+                Y.issue(yb, j0, ny, bar);
+            }
+            const bool ok = Scope::all(mbar_wait(bar, *phase));
+            *phase ^= 1u;
+            if (!ok) {
+                *timeout = true;
+                return false;
+            }
+            xa = X.window(xb, i0);
+            ya = Y.window(yb, j0);
+        } else {
+            xa = X.template stage<NT>(xb, i0, nx, tid);
+            ya = Y.template stage<NT>(yb, j0, ny, tid);
+            cp_async_wait_all();
+            Scope::sync();
+        }
         // D diagonals of the merge path lie in this window; thread tid walks
         // [d0, d0 + per).  No list can run out inside a full window.
         const uint32_t D = min(w, nx + ny);
         const uint32_t per = w / NT;
         const uint32_t owner = (D - 1) / per;  // walks the window's last diagonal
         uint32_t state;
-        const bool found = window_walk(xa, nx, ya, ny, w, D, per, tid * per, state);
+        const bool found = window_walk<WMAX / NT>(xa, nx, ya, ny, w, D, per, tid * per, state);
         if (Scope::vote(found, state, owner, slot)) return true;
         if (D == nx + ny || state == 0xffffffffu) return false;  // a list is exhausted
         i0 += state;
