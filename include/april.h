@@ -290,6 +290,26 @@ april_status april_filter_pairs_host(april_ctx *ctx, const april_dev_sets *R, co
                                      const uint32_t *h_r, const uint32_t *h_s, uint64_t n, uint8_t *h_verdict,
                                      int mode, void *d_work, size_t work_bytes, void *stream);
 
+/* Filter variants (paper Sec. 4.3.2 and Sec. 5.3) on sets built on global
+ * grids, by the batched kernels (long pairs by CTAs, the rest by warps).
+ *   predicate APRIL_PREDICATE_INTERSECTS: Algorithm 2 when R and S use the
+ *     same order; when they differ (Sec. 5.3, "Different Granularity") the
+ *     finer side's intervals are coarsened while they are read,
+ *     [st, end) -> [st >> n, ((end - 1) >> n) + 1) with n = 2 |order_r - order_s|,
+ *     and the filter is AA then the one join with the coarse side's F-list
+ *     (A(r') x F(s) when r is finer, F(r) x A(s') when s is finer).
+ *   predicate APRIL_PREDICATE_WITHIN (Sec. 4.3.2, "Spatial Within Joins";
+ *     equal orders): AA (no overlap: APRIL_TRUE_NEGATIVE, r is not within s),
+ *     then whether every A(r) interval lies inside one F(s) interval
+ *     (APRIL_TRUE_HIT: r is within s) or not (APRIL_INCONCLUSIVE).
+ * Other arguments and the scratch size are those of april_filter_pairs with
+ * APRIL_MODE_BATCHED; the context's cta_threshold applies. */
+#define APRIL_PREDICATE_INTERSECTS 0
+#define APRIL_PREDICATE_WITHIN 1
+april_status april_filter_pairs_ex(april_ctx *ctx, const april_dev_sets *R, const april_dev_sets *S,
+                                   const uint32_t *d_r, const uint32_t *d_s, uint64_t n, uint8_t *d_verdict,
+                                   int predicate, void *d_scratch, size_t scratch_bytes, void *stream);
+
 /* Waits for `stream`, then returns and clears the context's device status:
  * APRIL_OK, APRIL_ERR_OUT_OF_RANGE_ID or APRIL_ERR_DEVICE_TIMEOUT (or
  * APRIL_ERR_CUDA if the stream itself failed). */
@@ -402,6 +422,17 @@ april_status april_filter_pairs_noalloc(const april_dev_sets *R, const april_dev
 april_status april_host_filter(const april_sets *R, const april_sets *S, const uint32_t *pr,
                                const uint32_t *ps, uint64_t n, uint32_t n_threads, uint8_t *verdict,
                                uint64_t *consumed);
+
+/* The filter variants of april_filter_pairs_ex, run sequentially on the host
+ * over built sets on global grids (a CPU reference execution used for
+ * measurement, never by april_filter_pairs_ex).  Same verdicts and
+ * consumed-interval counts as april_host_filter for
+ * APRIL_PREDICATE_INTERSECTS on equal orders.  Out-of-range ids give
+ * APRIL_VERDICT_ERROR and consumed 0; partitioned sets, an unknown predicate
+ * or APRIL_PREDICATE_WITHIN on different orders return
+ * APRIL_ERR_INVALID_ARG.  consumed may be NULL. */
+april_status april_host_filter_ex(const april_sets *R, const april_sets *S, const uint32_t *pr, const uint32_t *ps,
+                                  uint64_t n, int predicate, uint32_t n_threads, uint8_t *verdict, uint64_t *consumed);
 
 #ifdef __cplusplus
 }

@@ -25,6 +25,7 @@ from __future__ import annotations
 import ctypes
 import os
 import subprocess
+import threading
 
 import numpy as np
 
@@ -32,6 +33,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "april_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
+_lib_lock = threading.Lock()
 
 LATTICE_BITS = 24
 
@@ -54,6 +56,14 @@ def build(force: bool = False) -> str:
 
 def lib():
     global _lib
+    if _lib is not None:
+        return _lib
+    with _lib_lock:
+        return _load()
+
+
+def _load():
+    global _lib
     if _lib is None:
         build()
         L = ctypes.CDLL(_LIB)
@@ -68,6 +78,10 @@ def lib():
         L.oracle_verdicts.argtypes = [p64, p64, p64, p64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                       ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                       ctypes.c_void_p]
+        L.oracle_verdicts_ex.restype = ctypes.c_int
+        L.oracle_verdicts_ex.argtypes = [p64, p64, p64, p64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                         ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                         ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
         L.oracle_hilbert_d.restype = ctypes.c_uint64
         L.oracle_hilbert_d.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64]
         L.oracle_hilbert_many.restype = None
@@ -140,6 +154,29 @@ def verdicts(R_xy, R_off, S_xy, S_off, pr, ps, grid: Grid) -> np.ndarray:
                                len(pr), *grid.args(), out.ctypes.data)
     if rc != 0:
         raise RuntimeError(f"oracle_verdicts failed ({rc})")
+    return out
+
+
+INTERSECTS = 0
+WITHIN = 1
+
+
+def verdicts_ex(R_xy, R_off, S_xy, S_off, pr, ps, order_r: int, order_s: int, pred: int = INTERSECTS) -> np.ndarray:
+    """Verdicts of the filter variants on global grids of orders order_r and
+    order_s (Sec. 5.3 when they differ) for the intersects predicate, or of
+    the within-join filter (Sec. 4.3.2; equal orders)."""
+    rxy = np.ascontiguousarray(R_xy, dtype=np.int64).reshape(-1)
+    sxy = np.ascontiguousarray(S_xy, dtype=np.int64).reshape(-1)
+    roff = np.ascontiguousarray(R_off, dtype=np.int64)
+    soff = np.ascontiguousarray(S_off, dtype=np.int64)
+    pr = np.ascontiguousarray(pr, dtype=np.uint32)
+    ps = np.ascontiguousarray(ps, dtype=np.uint32)
+    out = np.zeros(len(pr), dtype=np.uint8)
+    gr, gs = Grid(order_r), Grid(order_s)
+    rc = lib().oracle_verdicts_ex(_p64(rxy), _p64(roff), _p64(sxy), _p64(soff), pr.ctypes.data, ps.ctypes.data,
+                                  len(pr), 0, 0, gr.h, gr.G, gs.h, gs.G, pred, out.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(f"oracle_verdicts_ex failed ({rc})")
     return out
 
 

@@ -306,3 +306,106 @@ uint64_t oracle_hilbert_d(int order, uint64_t x, uint64_t y) {
 void oracle_hilbert_many(int order, const int64_t *x, const int64_t *y, int64_t n, uint64_t *d) {
     for (int64_t k = 0; k < n; k++) d[k] = oracle_hilbert_d(order, (uint64_t)x[k], (uint64_t)y[k]);
 }
+
+/* ------------------------------------------------------------------------
+ * Variants of the filter (paper Sec. 4.3.2 within joins, Sec. 5.3 different
+ * granularity), as set operations on rasters.
+ *
+ * within (pred = 1, one grid):
+ *   verdict = 0 if A(r) n A(s) is empty (disjoint: not within),
+ *             1 if every cell of A(r) is in F(s) (r lies inside s),
+ *             2 otherwise.
+ * intersects on two grids of the same data space (pred = 0), the finer one
+ * 2^k times finer per axis: let A'(p) be the coarse cells that contain a
+ * fine A-cell of the finer polygon p.  With r the finer polygon:
+ *   verdict = 0 if A'(r) n A(s) is empty, 1 if A'(r) n F(s) is not empty,
+ *             2 otherwise
+ * (only the coarse polygon's F-list is used); symmetrically when s is finer.
+ * ------------------------------------------------------------------------ */
+
+/* Coarse cell window and bitmap (1 = A') of a polygon rasterised on the fine
+ * grid (ox, oy, hf, Gf) and mapped k levels up. */
+static int coarse_a(const raster_t *fine, int k, int64_t *cwin, uint8_t **bits) {
+    cwin[0] = fine->win[0] >> k;
+    cwin[1] = fine->win[1] >> k;
+    cwin[2] = fine->win[2] >> k;
+    cwin[3] = fine->win[3] >> k;
+    int64_t W = cwin[2] - cwin[0] + 1, H = cwin[3] - cwin[1] + 1;
+    *bits = (uint8_t *)calloc((size_t)(W * H), 1);
+    if (!*bits) return -2;
+    int64_t fw = fine->win[2] - fine->win[0] + 1;
+    for (int64_t j = fine->win[1]; j <= fine->win[3]; j++)
+        for (int64_t i = fine->win[0]; i <= fine->win[2]; i++)
+            if (fine->cls[(j - fine->win[1]) * fw + (i - fine->win[0])] & CLS_A)
+                (*bits)[((j >> k) - cwin[1]) * W + ((i >> k) - cwin[0])] = 1;
+    return 0;
+}
+
+static uint8_t cls_at(const raster_t *r, int64_t i, int64_t j) {
+    if (i < r->win[0] || i > r->win[2] || j < r->win[1] || j > r->win[3]) return 0;
+    return r->cls[(j - r->win[1]) * (r->win[2] - r->win[0] + 1) + (i - r->win[0])];
+}
+
+int oracle_verdicts_ex(const int64_t *rxy, const int64_t *roff, const int64_t *sxy, const int64_t *soff,
+                       const uint32_t *pr, const uint32_t *ps, int64_t npairs, int64_t ox, int64_t oy,
+                       int64_t hr, int64_t Gr, int64_t hs, int64_t Gs, int pred, uint8_t *out) {
+    if (hr * Gr != hs * Gs) return -4;
+    if (pred == 1 && hr != hs) return -4;
+    raster_t rr = {{0, 0, 0, 0}, NULL, -1}, sr = {{0, 0, 0, 0}, NULL, -1};
+    int rc = 0;
+    for (int64_t k = 0; k < npairs && rc == 0; k++) {
+        int64_t r = pr[k], s = ps[k];
+        if (rr.id != r) {
+            free(rr.cls);
+            rr.id = r;
+            rc = make_raster(rxy + 2 * roff[r], roff[r + 1] - roff[r], ox, oy, hr, Gr, &rr);
+            if (rc) break;
+        }
+        if (sr.id != s) {
+            free(sr.cls);
+            sr.id = s;
+            rc = make_raster(sxy + 2 * soff[s], soff[s + 1] - soff[s], ox, oy, hs, Gs, &sr);
+            if (rc) break;
+        }
+        uint8_t v = 2;
+        if (pred == 1) {
+            int aa = 0, all_in = 1;
+            int64_t rw = rr.win[2] - rr.win[0] + 1;
+            for (int64_t j = rr.win[1]; j <= rr.win[3]; j++)
+                for (int64_t i = rr.win[0]; i <= rr.win[2]; i++) {
+                    if (!(rr.cls[(j - rr.win[1]) * rw + (i - rr.win[0])] & CLS_A)) continue;
+                    uint8_t c = cls_at(&sr, i, j);
+                    if (c & CLS_A) aa = 1;
+                    if (!(c & CLS_F)) all_in = 0;
+                }
+            v = !aa ? 0 : (all_in ? 1 : 2);
+        } else if (hr == hs) {
+            v = pair_verdict(&rr, &sr);
+        } else {
+            /* the finer polygon's A-cells lifted to the coarse grid */
+            const raster_t *fine = hr < hs ? &rr : &sr, *coarse = hr < hs ? &sr : &rr;
+            int lv = 0;
+            while ((hr < hs ? hr : hs) << lv < (hr < hs ? hs : hr)) lv++;
+            int64_t cw[4];
+            uint8_t *bits = NULL;
+            rc = coarse_a(fine, lv, cw, &bits);
+            if (rc == 0) {
+                int aa = 0, th = 0;
+                int64_t W = cw[2] - cw[0] + 1;
+                for (int64_t j = cw[1]; j <= cw[3]; j++)
+                    for (int64_t i = cw[0]; i <= cw[2]; i++) {
+                        if (!bits[(j - cw[1]) * W + (i - cw[0])]) continue;
+                        uint8_t c = cls_at(coarse, i, j);
+                        if (c & CLS_A) aa = 1;
+                        if (c & CLS_F) th = 1;
+                    }
+                v = !aa ? 0 : (th ? 1 : 2);
+            }
+            free(bits);
+        }
+        out[k] = v;
+    }
+    free(rr.cls);
+    free(sr.cls);
+    return rc;
+}

@@ -24,6 +24,7 @@ ERRORS = {
 }
 TRUE_NEGATIVE, TRUE_HIT, INCONCLUSIVE, VERDICT_ERROR = 0, 1, 2, 0xFF
 MODE_PLAIN, MODE_WARP, MODE_BATCHED, MODE_BATCHED_PACKED = 0, 1, 2, 3
+PREDICATE_INTERSECTS, PREDICATE_WITHIN = 0, 1
 MODES = {"plain": MODE_PLAIN, "warp": MODE_WARP, "batched": MODE_BATCHED}
 
 
@@ -99,6 +100,9 @@ SIGNATURES = {
     "april_filter_pairs_host": (_st, [_vp, ctypes.POINTER(april_dev_sets), ctypes.POINTER(april_dev_sets), _vp, _vp,
                                       _u64, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
     "april_host_filter": (_st, [_vp, _vp, _vp, _vp, _u64, _u32, _vp, _vp]),
+    "april_filter_pairs_ex": (_st, [_vp, ctypes.POINTER(april_dev_sets), ctypes.POINTER(april_dev_sets), _vp, _vp,
+                                    _u64, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
+    "april_host_filter_ex": (_st, [_vp, _vp, _vp, _vp, _u64, ctypes.c_int, _u32, _vp, _vp]),
     "april_sets_object_entries": (_st, [_vp, _u32, ctypes.POINTER(_u32), ctypes.POINTER(_u32)]),
     "april_sets_entry_grid": (_st, [_vp, _u32, ctypes.POINTER(_u32), ctypes.POINTER(april_grid)]),
     "april_build_partitioned_sets": (_st, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _u32, ctypes.POINTER(_vp),
@@ -303,6 +307,14 @@ class Context:
         check(load().april_filter_pairs(self.handle, ctypes.byref(R.c), ctypes.byref(S.c), _ptr(d_r), _ptr(d_s),
                                         n, _ptr(d_verdict), mode, _ptr(scratch), sb, st.cuda_stream))
 
+    def april_filter_pairs_ex(self, R: DevSets, S: DevSets, d_r, d_s, n: int, d_verdict, predicate: int, scratch,
+                              stream=None) -> None:
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream()
+        check(load().april_filter_pairs_ex(self.handle, ctypes.byref(R.c), ctypes.byref(S.c), _ptr(d_r), _ptr(d_s), n,
+                                           _ptr(d_verdict), predicate, _ptr(scratch), int(scratch.numel()),
+                                           st.cuda_stream))
+
     def get_tune(self) -> april_tune:
         t = april_tune()
         check(load().april_get_tune(self.handle, ctypes.byref(t)))
@@ -406,6 +418,17 @@ def april_filter_pairs_noalloc(R: DevSets, S: DevSets, d_r, d_s, n: int, d_verdi
     st = stream if stream is not None else torch.cuda.current_stream()
     check(load().april_filter_pairs_noalloc(ctypes.byref(R.c), ctypes.byref(S.c), _ptr(d_r), _ptr(d_s), n,
                                             _ptr(d_verdict), st.cuda_stream))
+
+
+def april_host_filter_ex(R: Sets, S: Sets, pr: np.ndarray, ps: np.ndarray, predicate: int, n_threads: int = 0):
+    """Host execution of the filter variants: (verdicts, consumed intervals)."""
+    pr = np.ascontiguousarray(pr, dtype=np.uint32)
+    ps = np.ascontiguousarray(ps, dtype=np.uint32)
+    v = np.zeros(len(pr), dtype=np.uint8)
+    c = np.zeros(len(pr), dtype=np.uint64)
+    check(load().april_host_filter_ex(R.handle, S.handle, _ptr(pr), _ptr(ps), len(pr), predicate, n_threads,
+                                      _ptr(v), _ptr(c)))
+    return v, c
 
 
 def april_host_filter(R: Sets, S: Sets, pr: np.ndarray, ps: np.ndarray, n_threads: int = 0):

@@ -771,3 +771,82 @@ extern "C" april_status april_host_filter(const april_sets *R, const april_sets 
     });
     return APRIL_OK;
 }
+
+namespace {
+
+// One join of a filter variant, sequentially: the merge of Algorithm 2 over
+// X and Y, each interval of a side with shift > 0 coarsened as it is read
+// (Sec. 5.3); pred 0 looks for an overlap, pred 1 for an X interval that no Y
+// interval contains (Sec. 4.3.2).  *used counts the intervals read.
+bool host_join_ex(const uint32_t *X, uint32_t nx, uint32_t sx, const uint32_t *Y, uint32_t ny, uint32_t sy, int pred,
+                  uint64_t *used) {
+    uint32_t i = 0, j = 0;
+    auto get = [](const uint32_t *L, uint32_t k, uint32_t sh, uint32_t &st, uint32_t &last) {
+        st = L[2 * k] >> sh;
+        last = (L[2 * k + 1] - 1u) >> sh;
+    };
+    while (i < nx && j < ny) {
+        uint32_t xs, xl, ys, yl;
+        get(X, i, sx, xs, xl);
+        get(Y, j, sy, ys, yl);
+        if (pred == 0) {
+            if (xs <= yl && ys <= xl) {
+                *used += (uint64_t)i + 1 + j + 1;
+                return true;
+            }
+        } else if (xl <= yl && ys > xs) {
+            *used += (uint64_t)i + 1 + j + 1;
+            return true;
+        }
+        if (xl <= yl) ++i;
+        else ++j;
+    }
+    *used += (uint64_t)std::min(i + 1, nx) + std::min(j + 1, ny);
+    return pred == 1 && i < nx;  // containment: X left over once Y ran out
+}
+
+}  // namespace
+
+extern "C" april_status april_host_filter_ex(const april_sets *R, const april_sets *S, const uint32_t *pr,
+                                             const uint32_t *ps, uint64_t n, int predicate, uint32_t n_threads,
+                                             uint8_t *verdict, uint64_t *consumed) {
+    if (!R || !S || (n && (!pr || !ps || !verdict))) return fail(APRIL_ERR_INVALID_ARG, "NULL argument");
+    if (R->parts || S->parts) return fail(APRIL_ERR_INVALID_ARG, "april_host_filter_ex takes sets on one global grid");
+    if (predicate != APRIL_PREDICATE_INTERSECTS && predicate != APRIL_PREDICATE_WITHIN)
+        return fail(APRIL_ERR_INVALID_ARG, "unknown predicate");
+    if (predicate == APRIL_PREDICATE_WITHIN && R->order != S->order)
+        return fail(APRIL_ERR_INVALID_ARG, "the within filter needs both sets on the same grid");
+    const uint32_t sx = R->order > S->order ? 2 * (R->order - S->order) : 0;
+    const uint32_t sy = S->order > R->order ? 2 * (S->order - R->order) : 0;
+    parallel_for(n, resolve_threads(n_threads), 4096, [&](uint32_t, uint64_t b, uint64_t e) {
+        for (uint64_t k = b; k < e; ++k) {
+            const uint32_t r = pr[k], s = ps[k];
+            uint64_t used = 0;
+            uint8_t v;
+            if (r >= R->n_entries || s >= S->n_entries) {
+                v = APRIL_VERDICT_ERROR;
+            } else {
+                const uint32_t *dr = &R->desc[4 * (size_t)r], *ds = &S->desc[4 * (size_t)s];
+                const uint32_t *Ar = &R->iv[2 * (size_t)dr[0]], *Fr = &R->iv[2 * (size_t)dr[2]];
+                const uint32_t *As = &S->iv[2 * (size_t)ds[0]], *Fs = &S->iv[2 * (size_t)ds[2]];
+                if (!host_join_ex(Ar, dr[1], sx, As, ds[1], sy, 0, &used)) {
+                    v = APRIL_TRUE_NEGATIVE;
+                } else if (predicate == APRIL_PREDICATE_WITHIN) {
+                    v = host_join_ex(Ar, dr[1], 0, Fs, ds[3], 0, 1, &used) ? APRIL_INCONCLUSIVE : APRIL_TRUE_HIT;
+                } else if (sx == 0 && sy == 0) {
+                    v = (host_join_ex(Ar, dr[1], 0, Fs, ds[3], 0, 0, &used) ||
+                         host_join_ex(Fr, dr[3], 0, As, ds[1], 0, 0, &used))
+                            ? APRIL_TRUE_HIT
+                            : APRIL_INCONCLUSIVE;
+                } else if (sx) {
+                    v = host_join_ex(Ar, dr[1], sx, Fs, ds[3], 0, 0, &used) ? APRIL_TRUE_HIT : APRIL_INCONCLUSIVE;
+                } else {
+                    v = host_join_ex(Fr, dr[3], 0, As, ds[1], sy, 0, &used) ? APRIL_TRUE_HIT : APRIL_INCONCLUSIVE;
+                }
+            }
+            verdict[k] = v;
+            if (consumed) consumed[k] = used;
+        }
+    });
+    return APRIL_OK;
+}

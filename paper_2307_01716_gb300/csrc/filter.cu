@@ -504,6 +504,108 @@ __global__ void APRIL_PERSISTENT_BOUNDS k_persistent(SetsT R, SetsT S,
     }
 }
 
+// -------------------------------- K7: filter variants (Sec. 4.3.2, Sec. 5.3)
+// A plan is the decision sequence of one filter variant: each stage joins one
+// list of r with one list of s under a predicate and either decides the
+// verdict or moves to another stage.  The finer side's lists are coarsened
+// on load when the two sets use grids of different order (Sec. 5.3).
+struct Plan {
+    uint8_t nst;
+    uint8_t xf[3], yf[3];       // stage's list: 0 = A-list, 1 = F-list (r, s)
+    uint8_t pred[3];            // kOverlap or kContain
+    int8_t on_true[3], on_false[3];  // >= 0: next stage; < 0: verdict -(v + 1)
+    uint8_t sx, sy;             // coarsening shifts of r's / s's intervals (bits)
+};
+
+template <class Scope, uint32_t NT, uint32_t WMAX>
+__device__ __forceinline__ uint8_t plan_verdict(const Plan &P, const RawSets &R, const RawSets &S, const uint4 &dr,
+                                                const uint4 &ds, uint2 *xs, uint2 *ys, uint32_t *slot, uint32_t tid,
+                                                uint32_t w0, JoinSync &js) {
+    int st = 0;
+    for (int guard = 0; guard < 3; ++guard) {
+        const RawList X = R.list(dr, P.xf[st] != 0), Y = S.list(ds, P.yf[st] != 0);
+        const bool res =
+            P.pred[st] == kContain
+                ? tile_join<Scope, NT, WMAX, RawList, kContain>(X, Y, xs, ys, slot, tid, w0, js.bar, &js.phase,
+                                                                &js.timeout, P.sx, P.sy)
+                : tile_join<Scope, NT, WMAX, RawList, kOverlap>(X, Y, xs, ys, slot, tid, w0, js.bar, &js.phase,
+                                                                &js.timeout, P.sx, P.sy);
+        if (js.timeout) return APRIL_VERDICT_ERROR;
+        const int nx = res ? P.on_true[st] : P.on_false[st];
+        if (nx < 0) return (uint8_t)(-(nx + 1));
+        st = nx;
+    }
+    return APRIL_VERDICT_ERROR;
+}
+
+// Same shape as K3 with 32-lane groups: long pairs by whole CTAs, the rest by
+// warps taking 32-pair chunks.
+__global__ void __launch_bounds__(kBlock) k_general(Plan P, DevSet Rd, DevSet Sd, const uint32_t *__restrict__ pr,
+                                                    const uint32_t *__restrict__ ps, uint64_t n,
+                                                    uint8_t *__restrict__ out, uint32_t *status,
+                                                    uint32_t cta_threshold, const uint32_t *__restrict__ big_list,
+                                                    uint32_t *counters) {
+    __shared__ __align__(16) uint2 sm[kSharedIv];
+    __shared__ uint32_t s_item, s_slot;
+    __shared__ uint64_t bars[1 + kWarpsPerBlock];
+    init_barriers(bars, 1 + kWarpsPerBlock);
+    const RawSets R{Rd}, S{Sd};
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t nbig = *((volatile uint32_t *)&counters[C_BIG_COUNT]);
+    JoinSync cs{smem_addr(&bars[0]), 0u, false};
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(&counters[C_BIG_HEAD], 1u);
+        __syncthreads();
+        const uint32_t it = s_item;
+        __syncthreads();
+        if (it >= nbig) break;
+        const uint64_t k = big_list[it];
+        const uint4 dr = R.load(__ldg(pr + k)), ds = S.load(__ldg(ps + k));
+        const uint8_t v = plan_verdict<CtaScope, kBlock, kCtaWMax>(P, R, S, dr, ds, sm, sm + kCtaBuf, &s_slot, tid,
+                                                                    256u, cs);
+        if (tid == 0) out[k] = v;
+        if (cs.timeout) {
+            if (tid == 0) atomicOr(status, ST_TIMEOUT);
+            return;
+        }
+    }
+    __syncthreads();
+    uint2 *xs = sm + warp * kWarpShare, *ys = xs + kWarpBuf;
+    JoinSync js{smem_addr(&bars[1 + warp]), 0u, false};
+    const uint64_t nchunks = (n + 31) / 32;
+    for (;;) {
+        uint32_t c = 0;
+        if (lane == 0) c = atomicAdd(&counters[C_CHUNK_HEAD], 1u);
+        c = __shfl_sync(kFull, c, 0);
+        if (c >= nchunks) break;
+        const uint64_t k = (uint64_t)c * 32 + lane;
+        uint4 dr = make_uint4(0, 0, 0, 0), ds = make_uint4(0, 0, 0, 0);
+        bool take = false;
+        if (k < n) {
+            const uint32_t r = __ldg(pr + k), s2 = __ldg(ps + k);
+            if (r < R.n() && s2 < S.n()) {
+                dr = R.load(r);
+                ds = S.load(s2);
+                take = (uint64_t)dr.y + ds.y <= (uint64_t)cta_threshold;
+            }
+        }
+        uint32_t todo = __ballot_sync(kFull, take);
+        uint8_t mine = 0;
+        while (todo) {
+            const uint32_t t = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const uint8_t v = plan_verdict<WarpScope, 32, kWarpWMax>(P, R, S, shfl4(dr, t), shfl4(ds, t), xs, ys,
+                                                                      nullptr, lane, 64u, js);
+            if (lane == t) mine = v;
+            if (js.timeout) {
+                if (lane == 0) atomicOr(status, ST_TIMEOUT);
+                return;
+            }
+        }
+        if (take) out[k] = mine;
+    }
+}
+
 // ------------------------------------------- K6: partition routing (a-8)
 // Sec. 5.2: a candidate pair is evaluated in the one partition that holds the
 // lower-left corner of MBR(r) n MBR(s).  Writes the two entries (object
@@ -886,6 +988,72 @@ extern "C" april_status april_filter_pairs(april_ctx *ctx, const april_dev_sets 
         default: return fail(APRIL_ERR_INVALID_ARG, "unknown mode");
     }
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return APRIL_OK;
+}
+
+// Decision plans (see K7).  Verdict v is encoded as -(v + 1).
+static Plan make_plan(int predicate, uint32_t order_r, uint32_t order_s) {
+    Plan P{};
+    const int8_t TN = -1, TH = -2, INC = -3;
+    if (predicate == APRIL_PREDICATE_WITHIN) {
+        // Sec. 4.3.2: AA (no overlap: not within), then "every A(r) interval
+        // lies in one F(s) interval" (yes: within; a violation: refine)
+        P.nst = 2;
+        P.xf[0] = 0; P.yf[0] = 0; P.pred[0] = kOverlap; P.on_true[0] = 1; P.on_false[0] = TN;
+        P.xf[1] = 0; P.yf[1] = 1; P.pred[1] = kContain; P.on_true[1] = INC; P.on_false[1] = TH;
+        return P;
+    }
+    P.xf[0] = 0; P.yf[0] = 0; P.pred[0] = kOverlap; P.on_true[0] = 1; P.on_false[0] = TN;
+    if (order_r == order_s) {  // Algorithm 2
+        P.nst = 3;
+        P.xf[1] = 0; P.yf[1] = 1; P.pred[1] = kOverlap; P.on_true[1] = TH; P.on_false[1] = 2;
+        P.xf[2] = 1; P.yf[2] = 0; P.pred[2] = kOverlap; P.on_true[2] = TH; P.on_false[2] = INC;
+    } else if (order_r > order_s) {  // Sec. 5.3: coarsen r, use only the coarse side's F-list
+        P.nst = 2;
+        P.sx = (uint8_t)(2 * (order_r - order_s));
+        P.xf[1] = 0; P.yf[1] = 1; P.pred[1] = kOverlap; P.on_true[1] = TH; P.on_false[1] = INC;
+    } else {
+        P.nst = 2;
+        P.sy = (uint8_t)(2 * (order_s - order_r));
+        P.xf[1] = 1; P.yf[1] = 0; P.pred[1] = kOverlap; P.on_true[1] = TH; P.on_false[1] = INC;
+    }
+    return P;
+}
+
+extern "C" april_status april_filter_pairs_ex(april_ctx *ctx, const april_dev_sets *R, const april_dev_sets *S,
+                                              const uint32_t *d_r, const uint32_t *d_s, uint64_t n,
+                                              uint8_t *d_verdict, int predicate, void *d_scratch,
+                                              size_t scratch_bytes, void *stream) {
+    if (!ctx || !R || !S) return fail(APRIL_ERR_INVALID_ARG, "NULL argument");
+    if (n == 0) return APRIL_OK;
+    if (!d_r || !d_s || !d_verdict) return fail(APRIL_ERR_INVALID_ARG, "NULL pair or verdict array");
+    if (predicate != APRIL_PREDICATE_INTERSECTS && predicate != APRIL_PREDICATE_WITHIN)
+        return fail(APRIL_ERR_INVALID_ARG, "unknown predicate");
+    if (R->parts || S->parts) return fail(APRIL_ERR_INVALID_ARG, "april_filter_pairs_ex takes sets on one global grid");
+    if (predicate == APRIL_PREDICATE_WITHIN && R->order != S->order)
+        return fail(APRIL_ERR_INVALID_ARG, "the within filter needs both sets on the same grid");
+    if (n > 0xFFFFFFFFull) return fail(APRIL_ERR_INVALID_ARG, "at most 2^32-1 pairs per call");
+    size_t need = 0;
+    april_filter_scratch_bytes(APRIL_MODE_BATCHED, n, &need);
+    if (!d_scratch || scratch_bytes < need) return fail(APRIL_ERR_INVALID_ARG, "scratch missing or too small");
+    if (((uintptr_t)d_scratch) & 255u) return fail(APRIL_ERR_INVALID_ARG, "scratch must be 256-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t *counters = (uint32_t *)d_scratch;
+    uint32_t *big_list = (uint32_t *)((char *)d_scratch + kCounterBytes);
+    const RawSets dR{dev_set(R)}, dS{dev_set(S)};
+    const Plan P = make_plan(predicate, R->order, S->order);
+    const unsigned grid_bin = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx->num_sms * 8);
+    int bps = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_general, kBlock, 0);
+    const unsigned grid_main = (unsigned)std::max(1, ctx->num_sms * std::max(bps, 1));
+    cudaError_t e = cudaMemsetAsync(counters, 0, kCounterBytes, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    k_bin<<<grid_bin, 256, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, ctx->d_status, ctx->tune.cta_threshold, big_list,
+                                    counters);
+    k_general<<<grid_main, kBlock, 0, st>>>(P, dR.s, dS.s, d_r, d_s, n, d_verdict, ctx->d_status,
+                                            ctx->tune.cta_threshold, big_list, counters);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return APRIL_OK;
 }

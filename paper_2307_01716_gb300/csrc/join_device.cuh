@@ -114,15 +114,24 @@ __device__ __forceinline__ uint32_t merge_split(uint32_t xa, uint32_t nx, uint32
 // sequential merge at those states.  `full` windows (neither list ends in
 // them) need no bound checks.  Returns the OR of the tests; *state receives
 // i after the last step, or 0xffffffff if a list ran out first.
-template <uint32_t PER>
+// Predicates a join can test at each merge state (i, j):
+//   kOverlap   X_i overlaps Y_j (Algorithm 2's IntervalJoin)
+//   kContain   X_i is emitted here but Y_j does not start at or before it, so
+//              Y_j (the first Y ending at or after X_i) cannot contain X_i --
+//              a violation of "every X interval lies in one Y interval"
+//              (the within-join variant of Sec. 4.3.2)
+enum JoinPred : int { kOverlap = 0, kContain = 1 };
+
+template <uint32_t PER, int PRED = kOverlap>
 __device__ __forceinline__ bool walk_fixed(uint32_t xa, uint32_t ya, uint32_t i, uint32_t j, uint32_t &state) {
     uint2 x = lds2(xa + 8u * i), y = lds2(ya + 8u * j);
     bool found = false;
 #pragma unroll
     for (uint32_t q = 0; q < PER; ++q) {
         const uint32_t xl = x.y - 1u, yl = y.y - 1u;
-        found |= (x.x <= yl) & (y.x <= xl);
         const bool ax = xl <= yl;
+        if (PRED == kOverlap) found |= (x.x <= yl) & (y.x <= xl);
+        else found |= ax & (y.x > x.x);
         i += ax;
         j += !ax;
         if (q + 1 < PER) {
@@ -135,6 +144,7 @@ __device__ __forceinline__ bool walk_fixed(uint32_t xa, uint32_t ya, uint32_t i,
     return found;
 }
 
+template <int PRED = kOverlap>
 __device__ __forceinline__ bool walk_checked(uint32_t xa, uint32_t nx, uint32_t ya, uint32_t ny, uint32_t i,
                                              uint32_t j, uint32_t steps, uint32_t &state) {
     bool found = false;
@@ -142,18 +152,21 @@ __device__ __forceinline__ bool walk_checked(uint32_t xa, uint32_t nx, uint32_t 
     for (; q < steps && i < nx && j < ny; ++q) {
         const uint2 x = lds2(xa + 8u * i), y = lds2(ya + 8u * j);
         const uint32_t xl = x.y - 1u, yl = y.y - 1u;
-        found |= (x.x <= yl) & (y.x <= xl);
         const bool ax = xl <= yl;
+        if (PRED == kOverlap) found |= (x.x <= yl) & (y.x <= xl);
+        else found |= ax & (y.x > x.x);
         i += ax;
         j += !ax;
     }
+    // containment: Y ran out (this is its last window) while X elements remain
+    if (PRED == kContain && q < steps && j >= ny && i < nx) found = true;
     state = (q == steps) ? i : 0xffffffffu;
     return found;
 }
 
 // The merge-path work of one thread in a window of D diagonals (w per list,
 // nx/ny staged): diagonals [d0, d0 + per), per a power of two <= MAXPER.
-template <uint32_t MAXPER>
+template <uint32_t MAXPER, int PRED = kOverlap>
 __device__ __forceinline__ bool window_walk(uint32_t xa, uint32_t nx, uint32_t ya, uint32_t ny, uint32_t w,
                                             uint32_t D, uint32_t per, uint32_t d0, uint32_t &state) {
     state = 0xffffffffu;
@@ -163,22 +176,36 @@ __device__ __forceinline__ bool window_walk(uint32_t xa, uint32_t nx, uint32_t y
     if (nx == w && ny == w) {
         if constexpr (MAXPER >= 16) {
             switch (per) {
-                case 1: return walk_fixed<1>(xa, ya, i, j, state);
-                case 2: return walk_fixed<2>(xa, ya, i, j, state);
-                case 4: return walk_fixed<4>(xa, ya, i, j, state);
-                case 8: return walk_fixed<8>(xa, ya, i, j, state);
-                default: return walk_fixed<16>(xa, ya, i, j, state);
+                case 1: return walk_fixed<1, PRED>(xa, ya, i, j, state);
+                case 2: return walk_fixed<2, PRED>(xa, ya, i, j, state);
+                case 4: return walk_fixed<4, PRED>(xa, ya, i, j, state);
+                case 8: return walk_fixed<8, PRED>(xa, ya, i, j, state);
+                default: return walk_fixed<16, PRED>(xa, ya, i, j, state);
             }
         } else {
             switch (per) {
-                case 1: return walk_fixed<1>(xa, ya, i, j, state);
-                case 2: return walk_fixed<2>(xa, ya, i, j, state);
-                case 4: return walk_fixed<4>(xa, ya, i, j, state);
-                default: return walk_fixed<8>(xa, ya, i, j, state);
+                case 1: return walk_fixed<1, PRED>(xa, ya, i, j, state);
+                case 2: return walk_fixed<2, PRED>(xa, ya, i, j, state);
+                case 4: return walk_fixed<4, PRED>(xa, ya, i, j, state);
+                default: return walk_fixed<8, PRED>(xa, ya, i, j, state);
             }
         }
     }
-    return walk_checked(xa, nx, ya, ny, i, j, min(per, D - d0), state);
+    return walk_checked<PRED>(xa, nx, ya, ny, i, j, min(per, D - d0), state);
+}
+
+// Coarsens a staged window in place (Sec. 5.3, joining approximations of
+// different granularity): interval [st, end) of the finer grid becomes the
+// interval of the coarser grid's cells that contain its cells,
+// [st >> sh, ((end - 1) >> sh) + 1).  The result is sorted by start and by
+// end but may overlap its neighbours, which the merge tolerates on this side.
+template <uint32_t NT>
+__device__ __forceinline__ void coarsen_window(uint32_t a, uint32_t cnt, uint32_t sh, uint32_t tid) {
+    for (uint32_t k = tid; k < cnt; k += NT) {
+        const uint2 v = lds2(a + 8u * k);
+        const uint32_t st = v.x >> sh, en = ((v.y - 1u) >> sh) + 1u;
+        asm volatile("st.shared.v2.u32 [%0], {%1, %2};\n" ::"r"(a + 8u * k), "r"(st), "r"(en));
+    }
 }
 
 struct WarpScope {
@@ -365,10 +392,12 @@ struct PackedList {
 // For raw lists the window is staged by two bulk copies issued by thread 0
 // and completed on the mbarrier `bar` (phase bit in *phase, flipped per
 // window); a wait that runs out sets *timeout and ends the join.
-template <class Scope, uint32_t NT, uint32_t WMAX, class ListT>
+template <class Scope, uint32_t NT, uint32_t WMAX, class ListT, int PRED = kOverlap>
 __device__ __noinline__ bool tile_join(const ListT X, const ListT Y, uint2 *xb, uint2 *yb, uint32_t *slot,
-                                       uint32_t tid, uint32_t w0, uint32_t bar, uint32_t *phase, bool *timeout) {
+                                       uint32_t tid, uint32_t w0, uint32_t bar, uint32_t *phase, bool *timeout,
+                                       uint32_t sx = 0, uint32_t sy = 0) {
     const uint32_t n = X.n, m = Y.n;
+    if (PRED == kContain && n > 0 && m == 0) return true;  // nothing can contain X
     uint32_t i0 = 0, j0 = 0, w = w0;
     while (i0 < n && j0 < m) {
         const uint32_t nx = min(w, n - i0), ny = min(w, m - j0);
@@ -398,20 +427,25 @@ __device__ __noinline__ bool tile_join(const ListT X, const ListT Y, uint2 *xb, 
             cp_async_wait_all();
             Scope::sync();
         }
+        if (sx | sy) {
+            if (sx) coarsen_window<NT>(xa, nx, sx, tid);
+            if (sy) coarsen_window<NT>(ya, ny, sy, tid);
+            Scope::sync();
+        }
         // D diagonals of the merge path lie in this window; thread tid walks
         // [d0, d0 + per).  No list can run out inside a full window.
         const uint32_t D = min(w, nx + ny);
         const uint32_t per = w / NT;
         const uint32_t owner = (D - 1) / per;  // walks the window's last diagonal
         uint32_t state;
-        const bool found = window_walk<WMAX / NT>(xa, nx, ya, ny, w, D, per, tid * per, state);
+        const bool found = window_walk<WMAX / NT, PRED>(xa, nx, ya, ny, w, D, per, tid * per, state);
         if (Scope::vote(found, state, owner, slot)) return true;
-        if (D == nx + ny || state == 0xffffffffu) return false;  // a list is exhausted
+        if (D == nx + ny || state == 0xffffffffu) return false;  // a list ran out (violations were seen in the walk)
         i0 += state;
         j0 += D - state;
         w = min(w * 2u, WMAX);
     }
-    return false;
+    return PRED == kContain && i0 < n;  // Y ended before X: the rest of X has no container
 }
 
 }  // namespace april_dev
