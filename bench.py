@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--tune", default=None, help="T,G,W,CW: fixed batched tuning instead of the autotuner")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
     ap.add_argument("--serving-requests", type=int, default=120)
+    ap.add_argument("--no-selection", action="store_true", help="skip the selection-query measurement")
+    ap.add_argument("--no-variants", action="store_true", help="skip the within / mixed-granularity measurement")
     return ap.parse_args()
 
 
@@ -174,6 +176,114 @@ def cpu_baseline(w, seconds: float, seed: int = 1234):
     return {"value": done / dt, "unit": "pairs/s", "cores": 1, "kind": "oracle",
             "sample": f"{done} random pairs of the {len(w.pr)} (seeded), cell-set oracle, single thread, "
                       f"{dt:.1f} s"}
+
+
+def _event_times(torch, stream, flush, run, steps, warmup):
+    """CUDA-event times (ms) of `run` on `stream`, L2 flushed before each step."""
+    for _ in range(warmup):
+        run()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        evs[k][0].record(stream)
+        run()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def selection_bench(ctx, A, torch, dev, stream, flush, R, dR, steps, warmup):
+    """Selection queries (Sec. 4.3.1): 1000 county-like query polygons over the
+    200k data polygons of config 2 (R side), the data lists and the MBR index
+    resident.  Timed: april_select (MBR candidates on the GPU, the count read
+    back, the batched filter) with the query lists already on the device; and
+    end to end from host query polygons (host construction of the query
+    lists, upload, april_select, verdicts back to the host)."""
+    from synth import selection
+    s = selection.make(1.0, 1000)
+    g = A.global_grid(s.order)
+    if R is None:
+        R = A.april_build_sets(s.R.xy, s.R.off, g)
+        dR = A.april_upload(R, dev)
+    dI = A.april_index_upload(A.april_index_build(R), dev)
+    t0 = time.perf_counter()
+    Q = A.april_build_sets(s.Q.xy, s.Q.off, g)
+    build_s = time.perf_counter() - t0
+    dQ = A.april_upload(Q, dev)
+    off = torch.empty(s.Q.n + 1, dtype=torch.int32, device=dev)
+    sc0 = torch.empty(ctx.select_scratch_bytes(0), dtype=torch.uint8, device=dev)
+    n = ctx.april_select(dI, dR, dQ, 0, None, None, None, off, sc0, stream)
+    d_r = torch.empty(n, dtype=torch.int32, device=dev)
+    d_q = torch.empty(n, dtype=torch.int32, device=dev)
+    d_v = torch.empty(n, dtype=torch.uint8, device=dev)
+    scratch = torch.empty(ctx.select_scratch_bytes(n), dtype=torch.uint8, device=dev)
+
+    def run():
+        ctx.april_select(dI, dR, dQ, n, d_r, d_q, d_v, off, scratch, stream)
+    t = _event_times(torch, stream, flush, run, steps, warmup)
+    ctx.april_sync_status(stream)
+    r = d_r.cpu().numpy().view(np.uint32)
+    q = d_q.cpu().numpy().view(np.uint32)
+    v = d_v.cpu().numpy()
+    t0 = time.perf_counter()
+    hv, _ = A.april_host_filter(R, Q, r, q)
+    host_all = time.perf_counter() - t0
+    k1 = min(n, 20_000)
+    t0 = time.perf_counter()
+    A.april_host_filter(R, Q, r[:k1], q[:k1], n_threads=1)
+    host_one = time.perf_counter() - t0
+    if not np.array_equal(v, hv):
+        raise SystemExit("selection verdicts differ from Algorithm 2 on the host")
+    # end to end: host polygons in, host verdicts out
+    e2e = []
+    h_v = torch.empty(n, dtype=torch.uint8).pin_memory()
+    for k in range(max(2, steps // 3)):
+        flush.fill_(k & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Qk = A.april_build_sets(s.Q.xy, s.Q.off, g)
+        dQk = A.april_upload(Qk, dev, stream)
+        ctx.april_select(dI, dR, dQk, n, d_r, d_q, d_v, off, scratch, stream)
+        h_v.copy_(d_v, non_blocking=True)
+        stream.synchronize()
+        e2e.append(time.perf_counter() - t0)
+    ms = statistics.mean(t)
+    return {"workload": s.name, "queries": int(s.Q.n), "candidate_pairs": int(n), "ms_per_batch": ms,
+            "queries_per_s": s.Q.n / (ms * 1e-3), "pairs_per_s": n / (ms * 1e-3),
+            "query_list_build_ms_host": build_s * 1e3,
+            "e2e": {"ms_per_batch": statistics.mean(e2e) * 1e3,
+                    "queries_per_s": s.Q.n / statistics.mean(e2e),
+                    "path": "host query construction + upload + april_select + verdicts to host"},
+            "cpu_alg2": {"threads_1_pairs_per_s": k1 / host_one, "threads_all_pairs_per_s": n / host_all,
+                         "threads": os.cpu_count()},
+            "verdict_mix": (np.bincount(v, minlength=3)[:3] / max(n, 1)).round(4).tolist()}
+
+
+def variants_bench(ctx, A, torch, dev, stream, flush, w, R, S, dR, dS, steps, warmup):
+    """The filter variants on the same candidate pairs: within (Sec. 4.3.2,
+    both sets at N) and different granularity (Sec. 5.3, S at N-2)."""
+    n = len(w.pr)
+    d_r = torch.from_numpy(w.pr.view(np.int32)).to(dev)
+    d_s = torch.from_numpy(w.ps.view(np.int32)).to(dev)
+    out = torch.empty(n, dtype=torch.uint8, device=dev)
+    scratch = torch.empty(ctx.scratch_bytes(A.MODE_BATCHED, n), dtype=torch.uint8, device=dev)
+    S2 = A.april_build_sets(w.S.xy, w.S.off, A.global_grid(w.order - 2))
+    dS2 = A.april_upload(S2, dev)
+    res = {}
+    for name, sets, dsets, pred in (("within", S, dS, A.PREDICATE_WITHIN),
+                                    (f"intersects_r{w.order}_s{w.order - 2}", S2, dS2, A.PREDICATE_INTERSECTS)):
+        def run():
+            ctx.april_filter_pairs_ex(dR, dsets, d_r, d_s, n, out, pred, scratch, stream)
+        t = _event_times(torch, stream, flush, run, steps, warmup)
+        ctx.april_sync_status(stream)
+        hv, _ = A.april_host_filter_ex(R, sets, w.pr, w.ps, pred)
+        if not np.array_equal(out.cpu().numpy(), hv):
+            raise SystemExit(f"variant {name}: verdicts differ from the host execution")
+        ms = statistics.mean(t)
+        res[name] = {"pairs_per_s": n / (ms * 1e-3), "ms_per_step": ms,
+                     "verdict_mix": (np.bincount(hv, minlength=3)[:3] / n).round(4).tolist()}
+    return res
 
 
 def serving_bench(ctx_cls, A, torch, dev, n_requests: int, budget_gb: float = 40.0):
@@ -305,9 +415,26 @@ def main():
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
-    # algorithmic bytes: the intervals sequential Algorithm 2 reads, per pair
+    # algorithmic bytes: the intervals sequential Algorithm 2 reads, per pair;
+    # the same host run (all cores) is the CPU Algorithm 2 leg
+    t0 = time.perf_counter()
     host_v, consumed = A.april_host_filter(R, S, w.pr, w.ps)
+    host_all_s = time.perf_counter() - t0
     b_alg = float(IV_BYTES * consumed.sum() + n * (PAIR_ID_BYTES + DESC_BYTES + VERDICT_BYTES))
+    b_full = None
+    if not w.partitions:  # no early exit: AA, AF and FA read every list in full
+        a_r, f_r = R.lengths()
+        a_s, f_s = S.lengths()
+        iv = (2 * a_r[w.pr].astype(np.uint64) + 2 * a_s[w.ps] + f_r[w.pr] + f_s[w.ps]).sum()
+        b_full = float(IV_BYTES * iv + n * (PAIR_ID_BYTES + DESC_BYTES + VERDICT_BYTES))
+    k1 = min(n, 100_000)
+    t0 = time.perf_counter()
+    A.april_host_filter(R, S, w.pr[:k1], w.ps[:k1], n_threads=1)
+    host_one_s = time.perf_counter() - t0
+    cpu_alg2 = {"kind": "Algorithm 2 merge joins (AA, AF, FA, early exit) over the same lists, host C++",
+                "threads_1": {"pairs_per_s": k1 / host_one_s, "sample": f"first {k1} pairs"},
+                "threads_all": {"pairs_per_s": n / host_all_s, "threads": os.cpu_count(), "sample": "all pairs"},
+                "cpu": os.uname().machine}
 
     mode_ids = dict(A.MODES, packed=A.MODE_BATCHED_PACKED)
 
@@ -420,6 +547,9 @@ def main():
                                              "ms_per_step": statistics.mean(t_warp)},
         "useful_GBps": achieved,
         "algorithmic_bytes_per_step": b_alg,
+        "full_scan_bytes_per_step": b_full,
+        "dram_over_algorithmic": None if traffic is None else traffic / b_alg,
+        "cpu_alg2": cpu_alg2,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": kernel_name,
                      "peak_kind": f"{peak_kind} copy bandwidth (burst)"},
@@ -429,6 +559,13 @@ def main():
         "tune": tune,
         "verdict_mix": (np.bincount(host_v, minlength=3)[:3] / n).round(4).tolist(),
     }
+    if rank == 0 and not args.no_variants and not w.partitions:
+        line["variants"] = variants_bench(ctx, A, torch, dev, stream, flush, w, R, S, dR, dS, args.steps,
+                                          args.warmup)
+    if rank == 0 and not args.no_selection:
+        same = args.config == 2 and not w.partitions
+        line["selection"] = selection_bench(ctx, A, torch, dev, stream, flush, R if same else None,
+                                            dR if same else None, args.steps, args.warmup)
     if rank == 0 and not args.no_serving:
         line["serving"] = serving_bench(A.Context, A, torch, dev, args.serving_requests)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -134,6 +134,14 @@ april_status april_sets_get_info(const april_sets *sets, april_sets_info *info);
 april_status april_sets_list(const april_sets *sets, uint32_t entry, int which, const uint32_t **iv,
                              uint32_t *n);
 
+/* Closed MBR of every object in lattice units: mbr[4o .. 4o+3] = x0, y0, x1,
+ * y1 (caller-owned host array of 4 * n_objects int32). */
+april_status april_sets_mbrs(const april_sets *sets, int32_t *mbr);
+
+/* Lengths of every entry's lists: a_len[e] and f_len[e] receive |A| and |F|
+ * of entry e, for e < info.n_entries (caller-owned host arrays). */
+april_status april_sets_lengths(const april_sets *sets, uint32_t *a_len, uint32_t *f_len);
+
 /* Entries of object `obj`: *first .. *first + *count - 1 (one entry, the
  * object itself, for sets on one grid). */
 april_status april_sets_object_entries(const april_sets *sets, uint32_t obj, uint32_t *first, uint32_t *count);
@@ -194,6 +202,7 @@ typedef struct april_dev_sets {
     const uint32_t *pdesc;      /* compressed: per entry {a_block, a_len, f_block, f_len} */
     const uint32_t *anchors;    /* compressed: block table, per block {anchor, gap_off64 | wide << 31} */
     const uint8_t *gaps;        /* compressed: gap blocks (64 or 128 bytes each) */
+    const int32_t *mbr;         /* per object {x0, y0, x1, y1}: closed MBR in lattice units */
 } april_dev_sets;
 
 /* Copies the sets into a caller-allocated device buffer of at least
@@ -409,6 +418,78 @@ void april_server_destroy(april_server *server);
 #define APRIL_NOALLOC_MAX_PAIRS 4194304u
 april_status april_filter_pairs_noalloc(const april_dev_sets *R, const april_dev_sets *S, const uint32_t *d_r,
                                         const uint32_t *d_s, uint64_t n, uint8_t *d_verdict, void *stream);
+
+/* ------------------------------------------------------ selection queries */
+
+/* Selection queries (Sec. 4.3.1): the data polygons R are pre-processed
+ * (APRIL lists on the device plus a bucket index over their MBRs); a batch of
+ * query polygons Q, with its own APRIL lists on the same grid, is answered by
+ * one april_select call: every pair (r, q) whose closed MBRs meet is found on
+ * the GPU and filtered (true negative / true hit / inconclusive), the pairs
+ * grouped by query.
+ *
+ * The index is a uniform grid of 2^bucket_bits x 2^bucket_bits buckets over
+ * the lattice square; an object is listed in every bucket its MBR meets.
+ * bucket_bits 0 picks about one object per bucket; at most 12.  R must be
+ * built on one global grid (not partitioned).  Errors: APRIL_ERR_INVALID_ARG,
+ * APRIL_ERR_NO_MEMORY. */
+typedef struct april_index april_index;
+
+typedef struct april_index_info {
+    uint32_t bucket_bits;
+    uint32_t n_objects;
+    uint64_t n_entries;     /* object copies over all buckets */
+    uint64_t device_bytes;  /* bytes april_index_upload needs */
+} april_index_info;
+
+april_status april_index_build(const april_sets *R, uint32_t bucket_bits, april_index **out);
+void april_index_destroy(april_index *index);
+april_status april_index_get_info(const april_index *index, april_index_info *info);
+
+/* Device image of an index, as written by april_index_upload (pointers into
+ * the caller's buffer):
+ *   off: (2^b)^2 + 1 bucket offsets into ent (buckets in row-major order);
+ *   ent: object ids, bucket by bucket, ascending within a bucket;
+ *   ebx: the bucket column of every entry. */
+typedef struct april_dev_index {
+    const uint32_t *off;
+    const uint32_t *ent;
+    const uint16_t *ebx;
+    uint32_t bucket_bits;
+    uint32_t n_objects;
+    uint64_t n_entries;
+} april_dev_index;
+
+/* Copies the index into a caller-allocated device buffer of at least
+ * info.device_bytes bytes (256-byte aligned), asynchronously on stream; the
+ * host index must stay alive until the copy completed. */
+april_status april_index_upload(const april_index *index, void *dev_buf, size_t dev_bytes, void *stream,
+                                april_dev_index *out);
+
+/* Device scratch april_select needs for up to `capacity` candidate pairs. */
+april_status april_select_scratch_bytes(uint64_t capacity, size_t *bytes);
+
+/* Answers the selection queries Q over R.
+ *   I            index built over R (april_index_build) and uploaded.
+ *   R, Q         device sets on the same global grid, with MBRs (april_upload).
+ *   capacity     room in d_r, d_q and d_verdict, in pairs.
+ *   d_r, d_q     receive the candidate pairs (data object, query), grouped by
+ *                query; within a query in a fixed order (bucket row, bucket,
+ *                object id), the same on every call.
+ *   d_verdict    receives each pair's verdict (as april_filter_pairs).
+ *   d_query_off  n_queries + 1 uint32: query q's pairs are
+ *                [d_query_off[q], d_query_off[q + 1]).
+ *   n_pairs      receives the number of candidate pairs.
+ * The call counts the candidates first and synchronizes the stream once to
+ * read the count; the pairs and the filter are then enqueued asynchronously
+ * (device errors as for april_filter_pairs, via april_sync_status).  With
+ * d_r, d_q and d_verdict all NULL it only counts (and fills d_query_off).
+ * More pairs than capacity: APRIL_ERR_OVER_BUDGET with *n_pairs set and
+ * d_query_off filled, nothing else written. */
+april_status april_select(april_ctx *ctx, const april_dev_index *I, const april_dev_sets *R,
+                          const april_dev_sets *Q, uint64_t capacity, uint32_t *d_r, uint32_t *d_q,
+                          uint8_t *d_verdict, uint32_t *d_query_off, uint64_t *n_pairs, void *d_scratch,
+                          size_t scratch_bytes, void *stream);
 
 /* ----------------------------------------------------- host Algorithm 2 */
 

@@ -180,6 +180,21 @@ def verdicts_ex(R_xy, R_off, S_xy, S_off, pr, ps, order_r: int, order_s: int, pr
     return out
 
 
+def select_candidates(mbr_r, mbr_q):
+    """The MBR step of a selection query (Sec. 4.3.1): every pair (r, q) whose
+    closed MBRs meet, by a direct test of each query against every data MBR.
+    Returns (r, q) sorted by q, then r."""
+    mbr_r = np.asarray(mbr_r, dtype=np.int64)
+    out_r, out_q = [], []
+    for q, (x0, y0, x1, y1) in enumerate(np.asarray(mbr_q, dtype=np.int64)):
+        hit = np.flatnonzero((mbr_r[:, 0] <= x1) & (x0 <= mbr_r[:, 2]) & (mbr_r[:, 1] <= y1) & (y0 <= mbr_r[:, 3]))
+        out_r.append(hit)
+        out_q.append(np.full(len(hit), q))
+    if not out_r:
+        return np.zeros(0, np.uint32), np.zeros(0, np.uint32)
+    return np.concatenate(out_r).astype(np.uint32), np.concatenate(out_q).astype(np.uint32)
+
+
 def hilbert(order: int, x, y) -> np.ndarray:
     x = np.ascontiguousarray(np.atleast_1d(x), dtype=np.int64)
     y = np.ascontiguousarray(np.atleast_1d(y), dtype=np.int64)

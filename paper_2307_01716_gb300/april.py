@@ -68,12 +68,22 @@ class april_server_info(ctypes.Structure):
                 ("arena_bytes", ctypes.c_uint64), ("arena_peak_bytes", ctypes.c_uint64)]
 
 
+class april_index_info(ctypes.Structure):
+    _fields_ = [("bucket_bits", ctypes.c_uint32), ("n_objects", ctypes.c_uint32), ("n_entries", ctypes.c_uint64),
+                ("device_bytes", ctypes.c_uint64)]
+
+
+class april_dev_index(ctypes.Structure):
+    _fields_ = [("off", ctypes.c_void_p), ("ent", ctypes.c_void_p), ("ebx", ctypes.c_void_p),
+                ("bucket_bits", ctypes.c_uint32), ("n_objects", ctypes.c_uint32), ("n_entries", ctypes.c_uint64)]
+
+
 class april_dev_sets(ctypes.Structure):
     _fields_ = [("desc", ctypes.c_void_p), ("iv", ctypes.c_void_p), ("n_objects", ctypes.c_uint32),
                 ("order", ctypes.c_uint32), ("iv_slots", ctypes.c_uint64), ("n_entries", ctypes.c_uint32),
                 ("parts", ctypes.c_uint32), ("obj_ll", ctypes.c_void_p), ("obj_entry", ctypes.c_void_p),
                 ("entry_pid", ctypes.c_void_p), ("pdesc", ctypes.c_void_p), ("anchors", ctypes.c_void_p),
-                ("gaps", ctypes.c_void_p)]
+                ("gaps", ctypes.c_void_p), ("mbr", ctypes.c_void_p)]
 
 
 _vp = ctypes.c_void_p
@@ -103,6 +113,16 @@ SIGNATURES = {
     "april_filter_pairs_ex": (_st, [_vp, ctypes.POINTER(april_dev_sets), ctypes.POINTER(april_dev_sets), _vp, _vp,
                                     _u64, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
     "april_host_filter_ex": (_st, [_vp, _vp, _vp, _vp, _u64, ctypes.c_int, _u32, _vp, _vp]),
+    "april_sets_lengths": (_st, [_vp, _vp, _vp]),
+    "april_index_build": (_st, [_vp, _u32, ctypes.POINTER(_vp)]),
+    "april_index_destroy": (None, [_vp]),
+    "april_index_get_info": (_st, [_vp, ctypes.POINTER(april_index_info)]),
+    "april_index_upload": (_st, [_vp, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(april_dev_index)]),
+    "april_select_scratch_bytes": (_st, [_u64, ctypes.POINTER(ctypes.c_size_t)]),
+    "april_select": (_st, [_vp, ctypes.POINTER(april_dev_index), ctypes.POINTER(april_dev_sets),
+                           ctypes.POINTER(april_dev_sets), _u64, _vp, _vp, _vp, _vp, ctypes.POINTER(_u64), _vp,
+                           ctypes.c_size_t, _vp]),
+    "april_sets_mbrs": (_st, [_vp, _vp]),
     "april_sets_object_entries": (_st, [_vp, _u32, ctypes.POINTER(_u32), ctypes.POINTER(_u32)]),
     "april_sets_entry_grid": (_st, [_vp, _u32, ctypes.POINTER(_u32), ctypes.POINTER(april_grid)]),
     "april_build_partitioned_sets": (_st, [_vp, _vp, _u32, _vp, _vp, _u32, _u32, _u32, _u32, ctypes.POINTER(_vp),
@@ -226,6 +246,20 @@ class Sets:
             out.append((int(anchor), wide, slots))
         return n.value, out
 
+    def mbrs(self) -> np.ndarray:
+        """(n_objects, 4) int32 closed MBRs x0, y0, x1, y1 in lattice units."""
+        out = np.zeros((self.info().n_objects, 4), dtype=np.int32)
+        check(load().april_sets_mbrs(self.handle, _ptr(out)))
+        return out
+
+    def lengths(self):
+        """(|A|, |F|) of every entry, two uint32 arrays."""
+        n = self.info().n_entries
+        a = np.zeros(n, dtype=np.uint32)
+        f = np.zeros(n, dtype=np.uint32)
+        check(load().april_sets_lengths(self.handle, _ptr(a), _ptr(f)))
+        return a, f
+
     def list(self, obj: int, which: int) -> np.ndarray:
         """(n, 2) uint32 array [st, end) of the A (which=0) or F (1) list of an
         entry (the object itself for sets on one grid)."""
@@ -280,6 +314,46 @@ def april_upload(sets: Sets, device=None, stream=None) -> DevSets:
     return DevSets(out, buf)
 
 
+class Index:
+    """april_index: bucket index over a set's object MBRs (selection queries)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.april_index_destroy(self.handle)
+            self.handle = None
+
+    def info(self) -> april_index_info:
+        inf = april_index_info()
+        check(load().april_index_get_info(self.handle, ctypes.byref(inf)))
+        return inf
+
+
+def april_index_build(sets: Sets, bucket_bits: int = 0) -> Index:
+    h = _vp()
+    check(load().april_index_build(sets.handle, bucket_bits, ctypes.byref(h)))
+    return Index(h.value)
+
+
+@dataclass
+class DevIndex:
+    c: april_dev_index
+    buf: object
+
+
+def april_index_upload(index: Index, device=None, stream=None) -> DevIndex:
+    import torch
+    inf = index.info()
+    buf = torch.empty(max(int(inf.device_bytes), 256), dtype=torch.uint8, device=device or "cuda")
+    out = april_dev_index()
+    st = stream if stream is not None else torch.cuda.current_stream(buf.device)
+    check(load().april_index_upload(index.handle, buf.data_ptr(), buf.numel(), st.cuda_stream, ctypes.byref(out)))
+    st.synchronize()
+    return DevIndex(out, buf)
+
+
 class Context:
     """april_ctx: device status block and kernel dispatch."""
 
@@ -314,6 +388,24 @@ class Context:
         check(load().april_filter_pairs_ex(self.handle, ctypes.byref(R.c), ctypes.byref(S.c), _ptr(d_r), _ptr(d_s), n,
                                            _ptr(d_verdict), predicate, _ptr(scratch), int(scratch.numel()),
                                            st.cuda_stream))
+
+    @staticmethod
+    def select_scratch_bytes(capacity: int) -> int:
+        b = ctypes.c_size_t()
+        check(load().april_select_scratch_bytes(capacity, ctypes.byref(b)))
+        return b.value
+
+    def april_select(self, index: DevIndex, R: DevSets, Q: DevSets, capacity: int, d_r, d_q, d_verdict, d_query_off,
+                     scratch, stream=None) -> int:
+        """Candidate pairs of the queries Q over R and their verdicts; returns
+        the number of pairs (d_r, d_q, d_verdict None: count only)."""
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream()
+        n = _u64()
+        check(load().april_select(self.handle, ctypes.byref(index.c), ctypes.byref(R.c), ctypes.byref(Q.c), capacity,
+                                  _ptr(d_r), _ptr(d_q), _ptr(d_verdict), _ptr(d_query_off), ctypes.byref(n),
+                                  _ptr(scratch), int(scratch.numel()), st.cuda_stream))
+        return n.value
 
     def get_tune(self) -> april_tune:
         t = april_tune()

@@ -20,6 +20,7 @@ april_status april_enqueue_request(april_ctx *ctx, const april_dev_sets *R, cons
                                    const uint32_t *d_r, const uint32_t *d_s, uint64_t n, uint8_t *d_verdict,
                                    void *d_scratch, uint32_t *d_status, unsigned max_ctas, void *stream);
 int april_ctx_num_sms(const april_ctx *ctx);
+uint32_t *april_ctx_status_word(april_ctx *ctx);
 int april_ctx_device(const april_ctx *ctx);
 
 // Host-side sets: per-entry descriptors and the interval slots exactly as
@@ -36,6 +37,7 @@ struct april_sets {
     uint64_t f_total = 0;
     std::vector<uint32_t> desc;       // 4 per entry: a_off, a_len, f_off, f_len (in intervals)
     std::vector<uint32_t> iv;         // 2 per slot: st, end
+    std::vector<int32_t> mbr;         // 4 per object: x0, y0, x1, y1 (lattice units, closed)
     std::vector<int32_t> obj_ll;      // parts > 0: 2 per object, lower-left corner of its MBR
     std::vector<uint32_t> obj_entry;  // parts > 0: n + 1 entry offsets (entries of an object are contiguous)
     std::vector<uint32_t> entry_pid;  // parts > 0: partition id of each entry (ascending within an object)
@@ -51,9 +53,9 @@ inline uint64_t april_round256(uint64_t b) { return (b + 255) / 256 * 256; }
 
 // Device image layout (each section starts 256-byte aligned):
 //   desc (16 B/entry) | iv (8 B/slot, then a 16-byte pad) | obj_ll (8 B/object) | obj_entry (4 B x (n+1))
-//   | entry_pid (4 B/entry) | pdesc (16 B/entry) | block table (8 B/block) | gaps
+//   | entry_pid (4 B/entry) | pdesc (16 B/entry) | block table (8 B/block) | gaps | mbr (16 B/object)
 struct april_image_layout {
-    uint64_t desc, iv, obj_ll, obj_entry, entry_pid, pdesc, anchors, gaps, total;
+    uint64_t desc, iv, obj_ll, obj_entry, entry_pid, pdesc, anchors, gaps, mbr, total;
 };
 
 inline april_image_layout april_layout(const april_sets &S) {
@@ -75,6 +77,8 @@ inline april_image_layout april_layout(const april_sets &S) {
     o += april_round256((uint64_t)S.anchors.size() * 4);
     L.gaps = o;
     o += april_round256((uint64_t)S.gaps.size());
+    L.mbr = o;
+    o += april_round256((uint64_t)S.mbr.size() * 4);
     L.total = o;
     return L;
 }

@@ -447,6 +447,12 @@ extern "C" april_status april_build_sets(const int32_t *xy, const uint64_t *vert
         S->n = n_polys;
         S->n_entries = n_polys;
         S->order = g.order;
+        S->mbr.resize(4 * (size_t)n_polys);
+        for (uint32_t p = 0; p < n_polys; ++p) {
+            const Mbr m = poly_mbr(xy + 2 * vert_off[p], vert_off[p + 1] - vert_off[p]);
+            int32_t *o = &S->mbr[4 * (size_t)p];
+            o[0] = (int32_t)m.x0, o[1] = (int32_t)m.y0, o[2] = (int32_t)m.x1, o[3] = (int32_t)m.y1;
+        }
         st = assemble_lists(S, lists, nt);
         if (st) {
             delete S;
@@ -488,6 +494,21 @@ extern "C" april_status april_sets_list(const april_sets *S, uint32_t entry, int
     uint32_t off = S->desc[4 * (size_t)entry + 2 * which], len = S->desc[4 * (size_t)entry + 2 * which + 1];
     *iv = S->iv.data() + 2 * (size_t)off;
     *n = len;
+    return APRIL_OK;
+}
+
+extern "C" april_status april_sets_mbrs(const april_sets *S, int32_t *mbr) {
+    if (!S || (S->n && !mbr)) return fail(APRIL_ERR_INVALID_ARG, "NULL argument");
+    std::copy(S->mbr.begin(), S->mbr.end(), mbr);
+    return APRIL_OK;
+}
+
+extern "C" april_status april_sets_lengths(const april_sets *S, uint32_t *a_len, uint32_t *f_len) {
+    if (!S || (S->n_entries && (!a_len || !f_len))) return fail(APRIL_ERR_INVALID_ARG, "NULL argument");
+    for (uint32_t e = 0; e < S->n_entries; ++e) {
+        a_len[e] = S->desc[4 * (size_t)e + 1];
+        f_len[e] = S->desc[4 * (size_t)e + 3];
+    }
     return APRIL_OK;
 }
 
@@ -607,6 +628,12 @@ extern "C" april_status april_build_partitioned_sets(const int32_t *r_xy, const 
             S->parts = parts;
             S->part_grid = grid_desc;
             S->obj_ll.resize(2 * (size_t)S->n);
+            S->mbr.resize(4 * (size_t)S->n);
+            for (uint32_t p = 0; p < S->n; ++p) {
+                const Mbr &m = mbr[side_i][p];
+                int32_t *o = &S->mbr[4 * (size_t)p];
+                o[0] = (int32_t)m.x0, o[1] = (int32_t)m.y0, o[2] = (int32_t)m.x1, o[3] = (int32_t)m.y1;
+            }
             S->obj_entry.assign((size_t)S->n + 1, 0u);
             std::vector<uint32_t> ent_obj;
             for (uint32_t p = 0; p < S->n; ++p) {

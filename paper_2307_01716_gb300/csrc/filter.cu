@@ -791,6 +791,7 @@ extern "C" april_status april_upload(const april_sets *S, void *dev_buf, size_t 
     put(L.pdesc, S->pdesc.data(), S->pdesc.size() * 4);
     put(L.anchors, S->anchors.data(), S->anchors.size() * 4);
     put(L.gaps, S->gaps.data(), S->gaps.size());
+    put(L.mbr, S->mbr.data(), S->mbr.size() * 4);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(upload)");
     *out = april_dev_sets{};
     out->desc = (const uint32_t *)(base + L.desc);
@@ -800,6 +801,7 @@ extern "C" april_status april_upload(const april_sets *S, void *dev_buf, size_t 
     out->iv_slots = S->iv.size() / 2;
     out->n_entries = S->n_entries;
     out->parts = S->parts;
+    out->mbr = S->mbr.empty() ? nullptr : (const int32_t *)(base + L.mbr);
     if (S->parts) {
         out->obj_ll = (const int32_t *)(base + L.obj_ll);
         out->obj_entry = (const uint32_t *)(base + L.obj_entry);
@@ -946,6 +948,7 @@ april_status april_enqueue_request(april_ctx *ctx, const april_dev_sets *R, cons
 
 int april_ctx_num_sms(const april_ctx *ctx) { return ctx->num_sms; }
 int april_ctx_device(const april_ctx *ctx) { return ctx->device; }
+uint32_t *april_ctx_status_word(april_ctx *ctx) { return ctx->d_status; }
 
 extern "C" april_status april_filter_pairs(april_ctx *ctx, const april_dev_sets *R, const april_dev_sets *S,
                                            const uint32_t *d_r, const uint32_t *d_s, uint64_t n,

@@ -43,8 +43,9 @@ def _rank(rank, world, port, q):
         g = A.global_grid(w.order)
         R = A.april_build_sets(w.R.xy, w.R.off, g)
         S = A.april_build_sets(w.S.xy, w.S.off, g)
-        a_r = np.array([R.list(i, 0).shape[0] for i in range(w.R.n)])
-        a_s = np.array([S.list(i, 0).shape[0] for i in range(w.S.n)])
+        a_r, _ = R.lengths()
+        a_s, _ = S.lengths()
+        assert a_r.tolist() == [R.list(i, 0).shape[0] for i in range(w.R.n)]
         shards = D.balanced_shards(D.pair_cost(a_r, a_s, w.pr, w.ps), world)
         lo, hi = shards[rank]
         v, _ = A.april_host_filter(R, S, w.pr[lo:hi], w.ps[lo:hi], n_threads=1)
