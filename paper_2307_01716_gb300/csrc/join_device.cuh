@@ -211,6 +211,7 @@ __device__ __forceinline__ void coarsen_window(uint32_t a, uint32_t cnt, uint32_
 struct WarpScope {
     static __device__ __forceinline__ void sync() { __syncwarp(); }
     static __device__ __forceinline__ bool all(bool b) { return __all_sync(kFull, b) != 0; }
+    static __device__ __forceinline__ uint32_t count(bool b) { return __popc(__ballot_sync(kFull, b)); }
     // OR of `b` over the group; `v` from thread `src` is returned to all.
     // Doubles as the point after which the window may be overwritten.
     static __device__ __forceinline__ bool vote(bool b, uint32_t &v, uint32_t src, uint32_t *) {
@@ -222,6 +223,7 @@ struct WarpScope {
 struct CtaScope {
     static __device__ __forceinline__ void sync() { __syncthreads(); }
     static __device__ __forceinline__ bool all(bool b) { return __syncthreads_and(b) != 0; }
+    static __device__ __forceinline__ uint32_t count(bool b) { return (uint32_t)__syncthreads_count(b); }
     static __device__ __forceinline__ bool vote(bool b, uint32_t &v, uint32_t src, uint32_t *slot) {
         if (threadIdx.x == src) *slot = v;
         const bool any = __syncthreads_or(b) != 0;
@@ -312,6 +314,7 @@ __device__ __forceinline__ uint2 *stage_window(uint2 *buf, const uint2 *src, uin
 // Either way the window's intervals end up at the returned shared address.
 struct RawList {
     static constexpr bool kBulk = true;
+    static constexpr bool kRandomAccess = true;
     const uint2 *p;
     uint32_t n;
     template <uint32_t NT>
@@ -333,6 +336,7 @@ struct RawList {
 
 struct PackedList {
     static constexpr bool kBulk = false;
+    static constexpr bool kRandomAccess = false;
     const uint2 *blocks;  // per block {anchor, gap_off64 | wide << 31}
     const uint8_t *gaps;  // the set's gap stream
     uint32_t n;
@@ -384,6 +388,28 @@ struct PackedList {
     __device__ __forceinline__ uint32_t window(const uint2 *buf, uint32_t) const { return smem_addr(buf); }
 };
 
+// First k in [0, n) whose interval's last cell, shifted right by sh, is at
+// least t (n if none): an NT-ary search by the group over the list in global
+// memory.  Each round the NT threads probe evenly spaced positions and count
+// the probes below t (a prefix, the keys being sorted), which leaves one gap
+// of the spacing to search; with NT = 32 a list of 10^4 intervals takes three
+// rounds.  Every thread of the group gets the same answer.
+template <class Scope, uint32_t NT>
+__device__ __forceinline__ uint32_t group_lower_bound(const uint2 *p, uint32_t n, uint32_t sh, uint32_t t,
+                                                      uint32_t tid) {
+    uint32_t lo = 0, hi = n;  // the answer lies in [lo, hi]
+    while (lo < hi) {
+        const uint32_t step = (hi - lo + NT - 1) / NT;
+        const uint32_t q = lo + (tid + 1) * step - 1;
+        const bool below = q < hi && ((__ldg(&p[q].y) - 1u) >> sh) < t;
+        const uint32_t c = Scope::count(below);
+        const uint32_t probes = (hi - lo) / step;  // probes that fell inside [lo, hi)
+        if (c < probes) hi = lo + (c + 1) * step - 1;
+        lo += c * step;
+    }
+    return lo;
+}
+
 // Any overlap between lists X and Y, by a group of NT threads (thread
 // index tid) with shared buffers xb, yb of WMAX + 2 intervals each (16-byte
 // aligned) and, for a CTA group, one shared word `slot`.  The first window
@@ -399,6 +425,22 @@ __device__ __noinline__ bool tile_join(const ListT X, const ListT Y, uint2 *xb, 
     const uint32_t n = X.n, m = Y.n;
     if (PRED == kContain && n > 0 && m == 0) return true;  // nothing can contain X
     uint32_t i0 = 0, j0 = 0, w = w0;
+    if constexpr (ListT::kRandomAccess) {
+        // Start each list at its first interval that can meet the other one:
+        // an interval of Y ending before X's first start meets no interval of
+        // X (nor contains one), and likewise for X against Y's first start.
+        // The merge from (0, 0) would pass over exactly those intervals, so
+        // the verdict is unchanged; only lists longer than a window search.
+        if (n && m && (n > w0 || m > w0)) {
+            const uint2 x0 = __ldg(X.p), y0 = __ldg(Y.p);
+            if (PRED == kOverlap) {
+                if (n > w0) i0 = group_lower_bound<Scope, NT>(X.p, n, sx, y0.x >> sy, tid);
+            } else if (((x0.y - 1u) >> sx) < (y0.x >> sy)) {
+                return true;  // X's first interval ends before any Y interval starts
+            }
+            if (m > w0) j0 = group_lower_bound<Scope, NT>(Y.p, m, sy, x0.x >> sx, tid);
+        }
+    }
     while (i0 < n && j0 < m) {
         const uint32_t nx = min(w, n - i0), ny = min(w, m - j0);
         uint32_t xa, ya;
