@@ -311,6 +311,29 @@ __device__ __forceinline__ bool join_lists(const DevSet &R, const DevSet &S, con
     return nX != 0 && nY != 0;
 }
 
+// The search of group_lower_bound for the G lanes of every group of a warp at
+// once (warp-collective; a group with lo == hi takes no part): on return lo
+// is the first k in [lo, hi) whose interval's last cell is at least `key`.
+template <uint32_t G>
+__device__ __forceinline__ void group_search(const uint2 *p, uint32_t key, uint32_t &lo, uint32_t &hi, uint32_t t,
+                                             uint32_t gbits) {
+    while (__any_sync(kFull, lo < hi)) {
+        bool below = false;
+        uint32_t step = 1;
+        if (lo < hi) {
+            step = (hi - lo + G - 1) / G;
+            const uint32_t q = lo + (t + 1) * step - 1;
+            below = q < hi && (__ldg(&p[q].y) - 1u) < key;
+        }
+        const uint32_t c = __popc(__ballot_sync(kFull, below) & gbits);
+        if (lo < hi) {
+            const uint32_t probes = (hi - lo) / step;
+            if (c < probes) hi = lo + (c + 1) * step - 1;
+            lo += c * step;
+        }
+    }
+}
+
 template <uint32_t G>
 __device__ __forceinline__ void group_engine(const DevSet &R, const DevSet &S, const uint32_t *__restrict__ pr,
                                              const uint32_t *__restrict__ ps, uint64_t n, uint8_t *__restrict__ out,
@@ -333,6 +356,7 @@ __device__ __forceinline__ void group_engine(const DevSet &R, const DevSet &S, c
     uint64_t k = 0;
     uint4 dr = make_uint4(0, 0, 0, 0), ds = make_uint4(0, 0, 0, 0);
     uint32_t stage = 0, nX = 0, nY = 0, i0 = 0, j0 = 0, w = w0;
+    bool fresh = false;  // the join has just started: its start has not been searched yet
     const uint2 *X = nullptr, *Y = nullptr;
 
     for (;;) {
@@ -375,6 +399,7 @@ __device__ __forceinline__ void group_engine(const DevSet &R, const DevSet &S, c
                 i0 = j0 = 0;
                 w = w0;
                 active = join_lists(R, S, dr, ds, 0, X, nX, Y, nY);
+                fresh = true;
                 if (!active && t == 0) out[k] = APRIL_TRUE_NEGATIVE;  // an empty A-list meets nothing
             }
             const uint32_t lastbit = __fns(avail, 0, (int)cnt);
@@ -383,11 +408,32 @@ __device__ __forceinline__ void group_engine(const DevSet &R, const DevSet &S, c
         }
         if (!__any_sync(kFull, active)) break;  // only reachable once the pairs are exhausted
 
+        // -------- a join that has just started skips, in each list longer
+        // than a window, the intervals ending before the other list's first
+        // start (they meet nothing; the merge would pass over them)
+        if (__any_sync(kFull, active && fresh)) {
+            const bool need = active && fresh;
+            uint32_t kx = 0, ky = 0;
+            if (need) {
+                kx = __ldg(&Y->x);
+                ky = __ldg(&X->x);
+            }
+            uint32_t lo = 0, hi = (need && nX > w0) ? nX : 0;
+            group_search<G>(X, kx, lo, hi, t, gbits);
+            if (need && nX > w0) i0 = lo;
+            lo = 0;
+            hi = (need && nY > w0) ? nY : 0;
+            group_search<G>(Y, ky, lo, hi, t, gbits);
+            if (need && nY > w0) j0 = lo;
+        }
+        fresh = false;
+        const bool ran_out = active && (i0 >= nX || j0 >= nY);  // the search passed a whole list
+
         // -------- one window of every active group's join
         // each active group's window arrives by two bulk copies on its mbarrier
         uint32_t nx = 0, ny = 0, xa = 0, ya = 0;
         bool ok = true;
-        if (active) {
+        if (active && !ran_out) {
             nx = min(w, nX - i0);
             ny = min(w, nY - j0);
             if (t == 0) {
@@ -411,7 +457,7 @@ __device__ __forceinline__ void group_engine(const DevSet &R, const DevSet &S, c
         }
         bool found = false;
         uint32_t state = 0xffffffffu, D = 0, owner = 0;
-        if (active) {
+        if (active && !ran_out) {
             D = min(w, nx + ny);
             const uint32_t per = w / G;
             owner = (D - 1) / per;
@@ -421,7 +467,8 @@ __device__ __forceinline__ void group_engine(const DevSet &R, const DevSet &S, c
         const uint32_t split = __shfl_sync(kFull, state, glead + owner);
         if (active) {
             int res = -1;  // -1: join continues, 0: no overlap, 1: overlap
-            if (fmask & gbits) res = 1;
+            if (ran_out) res = 0;
+            else if (fmask & gbits) res = 1;
             else if (D == nx + ny || split == 0xffffffffu) res = 0;
             else {
                 i0 += split;
@@ -438,6 +485,7 @@ __device__ __forceinline__ void group_engine(const DevSet &R, const DevSet &S, c
                     ++stage;
                     i0 = j0 = 0;
                     w = w0;
+                    fresh = true;
                     if (join_lists(R, S, dr, ds, stage, X, nX, Y, nY)) break;
                     if (stage == 2) verdict = APRIL_INCONCLUSIVE;
                 }
