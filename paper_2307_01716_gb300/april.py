@@ -110,10 +110,12 @@ SIGNATURES = {
     "april_filter_pairs_host": (_st, [_vp, ctypes.POINTER(april_dev_sets), ctypes.POINTER(april_dev_sets), _vp, _vp,
                                       _u64, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
     "april_host_filter": (_st, [_vp, _vp, _vp, _vp, _u64, _u32, _vp, _vp]),
+    "april_host_filter_searched": (_st, [_vp, _vp, _vp, _vp, _u64, _u32, _vp, _vp]),
     "april_filter_pairs_ex": (_st, [_vp, ctypes.POINTER(april_dev_sets), ctypes.POINTER(april_dev_sets), _vp, _vp,
                                     _u64, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
     "april_host_filter_ex": (_st, [_vp, _vp, _vp, _vp, _u64, ctypes.c_int, _u32, _vp, _vp]),
     "april_sets_lengths": (_st, [_vp, _vp, _vp]),
+    "april_sets_from_lists": (_st, [_u32, _u32, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
     "april_index_build": (_st, [_vp, _u32, ctypes.POINTER(_vp)]),
     "april_index_destroy": (None, [_vp]),
     "april_index_get_info": (_st, [_vp, ctypes.POINTER(april_index_info)]),
@@ -269,6 +271,25 @@ class Sets:
         if n.value == 0:
             return np.zeros((0, 2), dtype=np.uint32)
         return np.ctypeslib.as_array(p, shape=(n.value * 2,)).reshape(-1, 2).copy()
+
+
+def april_sets_from_lists(order: int, a_lists, f_lists, mbr=None) -> Sets:
+    """Sets from per-object (k, 2) [st, end) arrays (sorted, disjoint)."""
+    def flat(lists):
+        off = np.zeros(len(lists) + 1, dtype=np.uint64)
+        off[1:] = np.cumsum([len(L) for L in lists])
+        iv = (np.concatenate([np.asarray(L, dtype=np.uint64).reshape(-1, 2) for L in lists]) if len(lists)
+              else np.zeros((0, 2), np.uint64))
+        return off, np.ascontiguousarray((iv & 0xFFFFFFFF).astype(np.uint32).reshape(-1))
+    if len(a_lists) != len(f_lists):
+        raise ValueError("a_lists and f_lists differ in length")
+    ao, ai = flat(a_lists)
+    fo, fi = flat(f_lists)
+    m = None if mbr is None else np.ascontiguousarray(mbr, dtype=np.int32)
+    h = _vp()
+    check(load().april_sets_from_lists(len(a_lists), order, _ptr(ao), _ptr(ai), _ptr(fo), _ptr(fi), _ptr(m),
+                                       ctypes.byref(h)))
+    return Sets(h.value)
 
 
 def april_build_sets(xy: np.ndarray, vert_off: np.ndarray, grd: april_grid, n_threads: int = 0) -> Sets:
@@ -523,11 +544,14 @@ def april_host_filter_ex(R: Sets, S: Sets, pr: np.ndarray, ps: np.ndarray, predi
     return v, c
 
 
-def april_host_filter(R: Sets, S: Sets, pr: np.ndarray, ps: np.ndarray, n_threads: int = 0):
-    """Host Algorithm 2 over built sets: (verdicts, consumed intervals)."""
+def april_host_filter(R: Sets, S: Sets, pr: np.ndarray, ps: np.ndarray, n_threads: int = 0, searched: bool = False):
+    """Host Algorithm 2 over built sets: (verdicts, consumed intervals).
+    searched=True starts every join where the GPU kernels start it
+    (april_host_filter_searched: same verdicts, the kernels' reading model)."""
     pr = np.ascontiguousarray(pr, dtype=np.uint32)
     ps = np.ascontiguousarray(ps, dtype=np.uint32)
     v = np.zeros(len(pr), dtype=np.uint8)
     c = np.zeros(len(pr), dtype=np.uint64)
-    check(load().april_host_filter(R.handle, S.handle, _ptr(pr), _ptr(ps), len(pr), n_threads, _ptr(v), _ptr(c)))
+    fn = load().april_host_filter_searched if searched else load().april_host_filter
+    check(fn(R.handle, S.handle, _ptr(pr), _ptr(ps), len(pr), n_threads, _ptr(v), _ptr(c)))
     return v, c

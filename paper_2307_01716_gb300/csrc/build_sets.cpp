@@ -465,6 +465,55 @@ extern "C" april_status april_build_sets(const int32_t *xy, const uint64_t *vert
     }
 }
 
+extern "C" april_status april_sets_from_lists(uint32_t n, uint32_t order, const uint64_t *a_off,
+                                             const uint32_t *a_iv, const uint64_t *f_off, const uint32_t *f_iv,
+                                             const int32_t *mbr, april_sets **out) {
+    if (!out) return fail(APRIL_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (order < 1 || order > 16) return fail(APRIL_ERR_INVALID_ARG, "grid order must be 1..16");
+    if (n && (!a_off || !f_off)) return fail(APRIL_ERR_INVALID_ARG, "NULL offsets");
+    const uint64_t ncells = (uint64_t)1 << (2 * order);
+    try {
+        std::vector<PolyLists> lists(n);
+        for (int side = 0; side < 2; ++side) {
+            const uint64_t *off = side ? f_off : a_off;
+            const uint32_t *iv = side ? f_iv : a_iv;
+            if (off[n] > off[0] && !iv) return fail(APRIL_ERR_INVALID_ARG, "NULL interval array");
+            for (uint32_t o = 0; o < n; ++o) {
+                if (off[o + 1] < off[o]) return fail(APRIL_ERR_INVALID_ARG, "offsets are not monotone");
+                uint64_t prev_end = 0;
+                auto &L = side ? lists[o].F : lists[o].A;
+                for (uint64_t k = off[o]; k < off[o + 1]; ++k) {
+                    const uint64_t st = iv[2 * k];
+                    const uint64_t en = iv[2 * k + 1] == 0 && ncells == (1ull << 32) ? ncells : iv[2 * k + 1];
+                    if (st >= en || en > ncells || (k > off[o] && st < prev_end)) {
+                        char m[128];
+                        std::snprintf(m, sizeof m, "object %u: intervals must be non-empty, sorted and disjoint", o);
+                        return fail(APRIL_ERR_INVALID_ARG, m);
+                    }
+                    prev_end = en;
+                    L.push_back((uint32_t)st);
+                    L.push_back((uint32_t)en);
+                }
+            }
+        }
+        auto *S = new april_sets();
+        S->n = n;
+        S->n_entries = n;
+        S->order = order;
+        if (mbr) S->mbr.assign(mbr, mbr + 4 * (size_t)n);
+        april_status st = assemble_lists(S, lists, 0);
+        if (st) {
+            delete S;
+            return st;
+        }
+        *out = S;
+        return APRIL_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(APRIL_ERR_NO_MEMORY, "host allocation failed while importing lists");
+    }
+}
+
 extern "C" void april_sets_destroy(april_sets *sets) { delete sets; }
 
 extern "C" april_status april_sets_get_info(const april_sets *S, april_sets_info *info) {
@@ -752,6 +801,41 @@ bool host_join(const uint32_t *X, uint32_t nx, const uint32_t *Y, uint32_t ny, u
     return false;
 }
 
+// The same join started where the GPU kernels start it: each list at its
+// first interval whose last cell reaches the other list's first start (the
+// merge from the front would pass over the intervals before it without a
+// verdict).  *used counts the intervals the merge reads from there plus a
+// binary search per list (bit width of its length, in probed intervals).
+uint32_t lower_bound_last(const uint32_t *L, uint32_t n, uint32_t t) {
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = lo + (hi - lo) / 2;
+        if (L[2 * mid + 1] - 1u < t) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+uint32_t bit_width(uint32_t v) { return v ? 32u - (uint32_t)__builtin_clz(v) : 0u; }
+
+bool host_join_searched(const uint32_t *X, uint32_t nx, const uint32_t *Y, uint32_t ny, uint64_t *used) {
+    if (!nx || !ny) return false;
+    const uint32_t i0 = lower_bound_last(X, nx, Y[0]), j0 = lower_bound_last(Y, ny, X[0]);
+    *used += bit_width(nx) + bit_width(ny);
+    uint32_t i = i0, j = j0;
+    while (i < nx && j < ny) {
+        uint32_t xs = X[2 * i], xl = X[2 * i + 1] - 1u, ys = Y[2 * j], yl = Y[2 * j + 1] - 1u;
+        if (xs <= yl && ys <= xl) {
+            *used += (uint64_t)(i - i0) + 1 + (j - j0) + 1;
+            return true;
+        }
+        if (xl <= yl) ++i;
+        else ++j;
+    }
+    *used += (uint64_t)std::min(i + 1, nx) - i0 + std::min(j + 1, ny) - j0;
+    return false;
+}
+
 }  // namespace
 
 // Entry of object `obj` for partition `pid` (Sec. 5.2 routing), or UINT32_MAX.
@@ -761,9 +845,9 @@ static uint32_t find_entry(const april_sets *S, uint32_t obj, uint32_t pid) {
     return 0xffffffffu;
 }
 
-extern "C" april_status april_host_filter(const april_sets *R, const april_sets *S, const uint32_t *pr,
-                                          const uint32_t *ps, uint64_t n, uint32_t n_threads, uint8_t *verdict,
-                                          uint64_t *consumed) {
+static april_status host_filter(const april_sets *R, const april_sets *S, const uint32_t *pr, const uint32_t *ps,
+                                uint64_t n, uint32_t n_threads, uint8_t *verdict, uint64_t *consumed, bool searched) {
+    auto join = searched ? host_join_searched : host_join;
     if (!R || !S || (n && (!pr || !ps || !verdict))) return fail(APRIL_ERR_INVALID_ARG, "NULL argument");
     if (R->parts != S->parts || R->order != S->order) return fail(APRIL_ERR_INVALID_ARG, "R and S use different grids");
     const int64_t side = R->parts ? ((int64_t)1 << 24) / R->parts : 0;
@@ -787,9 +871,9 @@ extern "C" april_status april_host_filter(const april_sets *R, const april_sets 
                 const uint32_t *dr = &R->desc[4 * (size_t)r], *ds = &S->desc[4 * (size_t)s];
                 const uint32_t *Ar = &R->iv[2 * (size_t)dr[0]], *Fr = &R->iv[2 * (size_t)dr[2]];
                 const uint32_t *As = &S->iv[2 * (size_t)ds[0]], *Fs = &S->iv[2 * (size_t)ds[2]];
-                if (!host_join(Ar, dr[1], As, ds[1], &used)) v = APRIL_TRUE_NEGATIVE;
-                else if (host_join(Ar, dr[1], Fs, ds[3], &used)) v = APRIL_TRUE_HIT;
-                else if (host_join(Fr, dr[3], As, ds[1], &used)) v = APRIL_TRUE_HIT;
+                if (!join(Ar, dr[1], As, ds[1], &used)) v = APRIL_TRUE_NEGATIVE;
+                else if (join(Ar, dr[1], Fs, ds[3], &used)) v = APRIL_TRUE_HIT;
+                else if (join(Fr, dr[3], As, ds[1], &used)) v = APRIL_TRUE_HIT;
                 else v = APRIL_INCONCLUSIVE;
             }
             verdict[k] = v;
@@ -797,6 +881,18 @@ extern "C" april_status april_host_filter(const april_sets *R, const april_sets 
         }
     });
     return APRIL_OK;
+}
+
+extern "C" april_status april_host_filter(const april_sets *R, const april_sets *S, const uint32_t *pr,
+                                          const uint32_t *ps, uint64_t n, uint32_t n_threads, uint8_t *verdict,
+                                          uint64_t *consumed) {
+    return host_filter(R, S, pr, ps, n, n_threads, verdict, consumed, false);
+}
+
+extern "C" april_status april_host_filter_searched(const april_sets *R, const april_sets *S, const uint32_t *pr,
+                                                   const uint32_t *ps, uint64_t n, uint32_t n_threads,
+                                                   uint8_t *verdict, uint64_t *consumed) {
+    return host_filter(R, S, pr, ps, n, n_threads, verdict, consumed, true);
 }
 
 namespace {

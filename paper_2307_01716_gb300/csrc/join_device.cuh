@@ -232,6 +232,28 @@ struct CtaScope {
     }
 };
 
+// First k in [0, n) whose interval's last cell, shifted right by sh, is at
+// least t (n if none): an NT-ary search by the group over the list in global
+// memory.  Each round the NT threads probe evenly spaced positions and count
+// the probes below t (a prefix, the keys being sorted), which leaves one gap
+// of the spacing to search; with NT = 32 a list of 10^4 intervals takes three
+// rounds.  Every thread of the group gets the same answer.
+template <class Scope, uint32_t NT>
+__device__ __forceinline__ uint32_t group_lower_bound(const uint2 *p, uint32_t n, uint32_t sh, uint32_t t,
+                                                      uint32_t tid) {
+    uint32_t lo = 0, hi = n;  // the answer lies in [lo, hi]
+    while (lo < hi) {
+        const uint32_t step = (hi - lo + NT - 1) / NT;
+        const uint32_t q = lo + (tid + 1) * step - 1;
+        const bool below = q < hi && ((__ldg(&p[q].y) - 1u) >> sh) < t;
+        const uint32_t c = Scope::count(below);
+        const uint32_t probes = (hi - lo) / step;  // probes that fell inside [lo, hi)
+        if (c < probes) hi = lo + (c + 1) * step - 1;
+        lo += c * step;
+    }
+    return lo;
+}
+
 // ----- TMA bulk copies and mbarriers (sm_90+ PTX; used on sm_103a) -----
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
@@ -332,6 +354,12 @@ struct RawList {
     __device__ __forceinline__ uint32_t window(const uint2 *buf, uint32_t i0) const {
         return smem_addr(buf) + 8u * (uint32_t)(((uintptr_t)(p + i0) >> 3) & 1u);
     }
+    __device__ __forceinline__ uint32_t first_start() const { return __ldg(&p->x); }
+    // First interval whose last cell (shifted right by sh) is at least t.
+    template <class Scope, uint32_t NT>
+    __device__ __forceinline__ uint32_t search(uint32_t sh, uint32_t t, uint32_t tid) const {
+        return group_lower_bound<Scope, NT>(p, n, sh, t, tid);
+    }
 };
 
 struct PackedList {
@@ -386,29 +414,27 @@ struct PackedList {
     }
     __device__ __forceinline__ uint32_t issue(uint2 *, uint32_t, uint32_t, uint32_t) const { return 0; }
     __device__ __forceinline__ uint32_t window(const uint2 *buf, uint32_t) const { return smem_addr(buf); }
-};
-
-// First k in [0, n) whose interval's last cell, shifted right by sh, is at
-// least t (n if none): an NT-ary search by the group over the list in global
-// memory.  Each round the NT threads probe evenly spaced positions and count
-// the probes below t (a prefix, the keys being sorted), which leaves one gap
-// of the spacing to search; with NT = 32 a list of 10^4 intervals takes three
-// rounds.  Every thread of the group gets the same answer.
-template <class Scope, uint32_t NT>
-__device__ __forceinline__ uint32_t group_lower_bound(const uint2 *p, uint32_t n, uint32_t sh, uint32_t t,
-                                                      uint32_t tid) {
-    uint32_t lo = 0, hi = n;  // the answer lies in [lo, hi]
-    while (lo < hi) {
-        const uint32_t step = (hi - lo + NT - 1) / NT;
-        const uint32_t q = lo + (tid + 1) * step - 1;
-        const bool below = q < hi && ((__ldg(&p[q].y) - 1u) >> sh) < t;
-        const uint32_t c = Scope::count(below);
-        const uint32_t probes = (hi - lo) / step;  // probes that fell inside [lo, hi)
-        if (c < probes) hi = lo + (c + 1) * step - 1;
-        lo += c * step;
+    __device__ __forceinline__ uint32_t first_start() const { return __ldg(&blocks->x); }
+    // A start at or before the first interval whose last cell (shifted by sh)
+    // reaches t, at a block boundary: block b's anchor is the start of its
+    // interval 16b, so with c blocks anchored below t every interval before
+    // 16 (c - 1) ends below t as well.
+    template <class Scope, uint32_t NT>
+    __device__ __forceinline__ uint32_t search(uint32_t sh, uint32_t t, uint32_t tid) const {
+        const uint32_t nb = (2 * n + 31) / 32;
+        uint32_t lo = 0, hi = nb;  // count of blocks whose anchor lies below t
+        while (lo < hi) {
+            const uint32_t step = (hi - lo + NT - 1) / NT;
+            const uint32_t q = lo + (tid + 1) * step - 1;
+            const bool below = q < hi && (__ldg(&blocks[q].x) >> sh) < t;
+            const uint32_t c = Scope::count(below);
+            const uint32_t probes = (hi - lo) / step;
+            if (c < probes) hi = lo + (c + 1) * step - 1;
+            lo += c * step;
+        }
+        return lo ? 16u * (lo - 1) : 0u;
     }
-    return lo;
-}
+};
 
 // Any overlap between lists X and Y, by a group of NT threads (thread
 // index tid) with shared buffers xb, yb of WMAX + 2 intervals each (16-byte
@@ -425,21 +451,23 @@ __device__ __noinline__ bool tile_join(const ListT X, const ListT Y, uint2 *xb, 
     const uint32_t n = X.n, m = Y.n;
     if (PRED == kContain && n > 0 && m == 0) return true;  // nothing can contain X
     uint32_t i0 = 0, j0 = 0, w = w0;
-    if constexpr (ListT::kRandomAccess) {
-        // Start each list at its first interval that can meet the other one:
-        // an interval of Y ending before X's first start meets no interval of
-        // X (nor contains one), and likewise for X against Y's first start.
-        // The merge from (0, 0) would pass over exactly those intervals, so
-        // the verdict is unchanged; only lists longer than a window search.
-        if (n && m && (n > w0 || m > w0)) {
-            const uint2 x0 = __ldg(X.p), y0 = __ldg(Y.p);
-            if (PRED == kOverlap) {
-                if (n > w0) i0 = group_lower_bound<Scope, NT>(X.p, n, sx, y0.x >> sy, tid);
-            } else if (((x0.y - 1u) >> sx) < (y0.x >> sy)) {
-                return true;  // X's first interval ends before any Y interval starts
-            }
-            if (m > w0) j0 = group_lower_bound<Scope, NT>(Y.p, m, sy, x0.x >> sx, tid);
+    // Start each list at (or, for compressed lists, at a block boundary
+    // before) its first interval that can meet the other one: an interval of
+    // Y ending before X's first start meets no interval of X (nor contains
+    // one), and likewise for X against Y's first start.  The merge from
+    // (0, 0) would pass over those intervals, and a merge started anywhere
+    // before the first interval that can meet finds the same overlaps, so the
+    // verdict is unchanged; only lists longer than a window search.
+    if (n && m && (n > w0 || m > w0)) {
+        const uint32_t xs = X.first_start() >> sx, ys = Y.first_start() >> sy;
+        if (PRED == kOverlap) {
+            if (n > w0) i0 = X.template search<Scope, NT>(sx, ys, tid);
+        } else {
+            static_assert(PRED == kOverlap || ListT::kRandomAccess, "containment joins read raw lists");
+            if constexpr (ListT::kRandomAccess)
+                if (((__ldg(&X.p->y) - 1u) >> sx) < ys) return true;  // X's first interval ends before Y starts
         }
+        if (m > w0) j0 = Y.template search<Scope, NT>(sy, xs, tid);
     }
     while (i0 < n && j0 < m) {
         const uint32_t nx = min(w, n - i0), ny = min(w, m - j0);

@@ -105,3 +105,23 @@ def test_build_errors():
 def test_empty_set():
     S = A.april_build_sets(np.zeros((0, 2), np.int64), np.array([0]), A.global_grid(12))
     assert S.info().n_objects == 0
+
+
+@pytest.mark.parametrize("cfg,scale", [(1, 1.0), (3, 0.01)])
+def test_searched_host_filter(cfg, scale):
+    """Starting every join at the searched start keeps Algorithm 2's verdicts;
+    the merge then reads no more than the sequential one (plus the probes)."""
+    from tests import _data
+    w = _data.workload(cfg, scale)
+    g = A.global_grid(w.order)
+    R = A.april_build_sets(w.R.xy, w.R.off, g)
+    S = A.april_build_sets(w.S.xy, w.S.off, g)
+    v0, c0 = A.april_host_filter(R, S, w.pr, w.ps)
+    v1, c1 = A.april_host_filter(R, S, w.pr, w.ps, searched=True)
+    assert np.array_equal(v0, v1)
+    a_r, f_r = R.lengths()
+    a_s, f_s = S.lengths()
+    bw = lambda v: np.floor(np.log2(np.maximum(v, 1))).astype(np.int64) + (v > 0)
+    probes = 3 * (bw(np.maximum(a_r, f_r)[w.pr]) + bw(np.maximum(a_s, f_s)[w.ps]))
+    assert np.all(c1.astype(np.int64) <= c0.astype(np.int64) + probes)
+    assert c1.sum() < c0.sum()
