@@ -432,6 +432,46 @@ void april_server_destroy(april_server *server);
 april_status april_filter_pairs_noalloc(const april_dev_sets *R, const april_dev_sets *S, const uint32_t *d_r,
                                         const uint32_t *d_s, uint64_t n, uint8_t *d_verdict, void *stream);
 
+/* ------------------------------------------------- construction on the GPU */
+
+/* Builds the APRIL approximation of polygons that are in device memory and
+ * writes the device image the filter reads, on the GPU (Sec. 4.1 lists,
+ * constructed as in Sec. 6: touched cells per edge, sorted by Hilbert id,
+ * one point-in-polygon test per gap).  The lists equal april_build_sets'
+ * list for list (same exact arithmetic; the lists are canonical).
+ *   d_xy, d_vert_off  device arrays as for april_build_sets: int32 lattice
+ *                     (x, y) pairs and n_polys + 1 uint64 vertex offsets
+ *                     (8-byte aligned).
+ *   grid              as for april_build_sets.
+ *   d_work            device work buffer (256-byte aligned) of at least
+ *                     info->work_bytes; a call with a smaller one (or NULL)
+ *                     returns APRIL_ERR_OVER_BUDGET with info->work_bytes set
+ *                     to what counting needs, and the next call with that
+ *                     much reports the full sizes.
+ *   d_image           device image buffer (256-byte aligned) of at least
+ *                     info->image_bytes: descriptors, MBRs and interval
+ *                     slots (each polygon's lists in a slot range sized from
+ *                     its cell count; unused slots are never read).
+ *   out               receives the device sets (no partitions, no packed
+ *                     lists); pointers into d_image.
+ * The call counts cells on the device and synchronizes the stream once to
+ * read the sizes (filled into *info even when a buffer is too small, in
+ * which case it returns APRIL_ERR_OVER_BUDGET and builds nothing); the
+ * construction itself is then enqueued asynchronously on `stream`.
+ * A polygon with fewer than 3 vertices, outside the grid or meeting no cell:
+ * APRIL_ERR_GEOMETRY naming the first such polygon. */
+typedef struct april_device_build_info {
+    uint64_t touched_cells;  /* cell incidences of all edges (before merging) */
+    uint64_t work_bytes;     /* work buffer bytes the build needs */
+    uint64_t image_bytes;    /* image buffer bytes the build needs */
+    uint64_t iv_slots;       /* interval slots reserved in the image */
+} april_device_build_info;
+
+april_status april_build_sets_device(april_ctx *ctx, const int32_t *d_xy, const uint64_t *d_vert_off,
+                                     uint32_t n_polys, const april_grid *grid, void *d_work, size_t work_bytes,
+                                     void *d_image, size_t image_bytes, april_dev_sets *out,
+                                     april_device_build_info *info, void *stream);
+
 /* ------------------------------------------------------ selection queries */
 
 /* Selection queries (Sec. 4.3.1): the data polygons R are pre-processed

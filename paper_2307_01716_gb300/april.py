@@ -68,6 +68,11 @@ class april_server_info(ctypes.Structure):
                 ("arena_bytes", ctypes.c_uint64), ("arena_peak_bytes", ctypes.c_uint64)]
 
 
+class april_device_build_info(ctypes.Structure):
+    _fields_ = [("touched_cells", ctypes.c_uint64), ("work_bytes", ctypes.c_uint64), ("image_bytes", ctypes.c_uint64),
+                ("iv_slots", ctypes.c_uint64)]
+
+
 class april_index_info(ctypes.Structure):
     _fields_ = [("bucket_bits", ctypes.c_uint32), ("n_objects", ctypes.c_uint32), ("n_entries", ctypes.c_uint64),
                 ("device_bytes", ctypes.c_uint64)]
@@ -115,6 +120,9 @@ SIGNATURES = {
                                     _u64, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
     "april_host_filter_ex": (_st, [_vp, _vp, _vp, _vp, _u64, ctypes.c_int, _u32, _vp, _vp]),
     "april_sets_lengths": (_st, [_vp, _vp, _vp]),
+    "april_build_sets_device": (_st, [_vp, _vp, _vp, _u32, ctypes.POINTER(april_grid), _vp, ctypes.c_size_t, _vp,
+                                      ctypes.c_size_t, ctypes.POINTER(april_dev_sets),
+                                      ctypes.POINTER(april_device_build_info), _vp]),
     "april_sets_from_lists": (_st, [_u32, _u32, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
     "april_index_build": (_st, [_vp, _u32, ctypes.POINTER(_vp)]),
     "april_index_destroy": (None, [_vp]),
@@ -375,6 +383,9 @@ def april_index_upload(index: Index, device=None, stream=None) -> DevIndex:
     return DevIndex(out, buf)
 
 
+STATUS_OVER_BUDGET = -3
+
+
 class Context:
     """april_ctx: device status block and kernel dispatch."""
 
@@ -427,6 +438,30 @@ class Context:
                                   _ptr(d_r), _ptr(d_q), _ptr(d_verdict), _ptr(d_query_off), ctypes.byref(n),
                                   _ptr(scratch), int(scratch.numel()), st.cuda_stream))
         return n.value
+
+    def april_build_sets_device(self, d_xy, d_off, grd: april_grid, work=None, image=None, stream=None):
+        """GPU construction of the sets of the polygons in device memory
+        (d_xy: int32 (V, 2), d_off: int64 (n + 1,) on the device).  Returns
+        (DevSets over the image tensor, april_device_build_info).  Buffers that
+        are missing or too small are (re)allocated as torch tensors."""
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream(d_xy.device)
+        n = int(d_off.numel()) - 1
+        info = april_device_build_info()
+        out = april_dev_sets()
+        fn = load().april_build_sets_device
+        for _ in range(3):
+            status = fn(self.handle, _ptr(d_xy), _ptr(d_off), n, ctypes.byref(grd), _ptr(work),
+                        0 if work is None else int(work.numel()), _ptr(image), 0 if image is None else int(image.numel()),
+                        ctypes.byref(out), ctypes.byref(info), st.cuda_stream)
+            if status != STATUS_OVER_BUDGET:
+                check(status)
+                return DevSets(out, image), info
+            if work is None or work.numel() < info.work_bytes:
+                work = torch.empty(int(info.work_bytes), dtype=torch.uint8, device=d_xy.device)
+            if info.image_bytes and (image is None or image.numel() < info.image_bytes):
+                image = torch.empty(int(info.image_bytes), dtype=torch.uint8, device=d_xy.device)
+        check(status)
 
     def get_tune(self) -> april_tune:
         t = april_tune()

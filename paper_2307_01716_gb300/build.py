@@ -14,7 +14,7 @@ BUILD = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CXX_SOURCES = ["build_sets.cpp"]
-CU_SOURCES = ["filter.cu", "server.cu", "select.cu"]
+CU_SOURCES = ["filter.cu", "server.cu", "select.cu", "build_device.cu"]
 
 
 def _nvcc() -> str:

@@ -12,6 +12,9 @@ namespace april {
 
 // Records msg as the calling thread's last error and returns code.
 april_status fail(april_status code, const std::string &msg);
+// Validates a grid (as april_build_sets does) and returns its parameters.
+april_status check_grid_params(const april_grid *grid, int64_t &ox, int64_t &oy, int64_t &h, uint32_t &order,
+                               int64_t &G);
 
 }  // namespace april
 

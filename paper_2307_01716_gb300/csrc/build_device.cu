@@ -1,0 +1,664 @@
+// GPU construction of APRIL approximations: polygons in device memory in,
+// a device image of their A- and F-lists (the layout the filter reads) out.
+//
+// The cells and lists are exactly the host builder's (build_sets.cpp): both
+// take their arithmetic from geom.h, and the lists are canonical (maximal
+// intervals of the A and F cell sets, Sec. 4.1), so the two agree list for
+// list.  The steps follow the host builder (and Sec. 6):
+//   count  (k_bcount, one warp per polygon): MBR, cell window, the number of
+//          touched-cell incidences T (cells an edge meets, per edge) and of
+//          centre-line incidences (rows an edge crosses at their centre);
+//   scan   (k_bscan): per-polygon offsets into the work and image regions;
+//          the host reads the totals once;
+//   build  (k_bconstruct, one CTA per polygon, persistent):
+//     1. every edge writes its touched cells as keys (Hilbert id << 1 |
+//        crossed), the crossed flag saying whether the edge enters the
+//        cell's open square;
+//     2. the keys are sorted (LSD radix, 4-bit digits, stable) and reduced
+//        to one key per cell (crossed if any edge crossed it);
+//     3. edges are bucketed by the cell row whose centre line they cross;
+//     4. one point-in-polygon test at the first cell of every gap between
+//        consecutive touched ids (a gap is wholly inside or outside: Sec.
+//        6.2) and at every touched cell no edge crosses (Full when its
+//        centre is inside);
+//     5. the A- and F-intervals come out of block scans over the cells:
+//        an A interval breaks at a non-empty gap outside the polygon, an F
+//        interval runs over consecutive Full gaps and cells.
+// Each polygon's lists go to a slot range sized from T (|A| <= T and
+// |F| <= T + 1), so no second pass is needed; unused slots stay unused.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <string>
+
+#include "april_internal.h"
+#include "geom.h"
+
+using april::fail;
+using namespace april_geom;
+
+namespace {
+
+constexpr uint32_t kFull = 0xffffffffu;
+constexpr unsigned kBB = 256;  // build CTA size
+constexpr unsigned kBW = kBB / 32;
+
+struct GridP {
+    int64_t ox, oy, h, G;
+    uint32_t order;
+};
+
+// Per polygon, written by k_bcount and k_bscan.
+struct PolyMeta {
+    uint64_t key_off;   // into the key and temp arrays (keys)
+    uint64_t rb_off;    // into the row-bucket array (uint32)
+    uint64_t slot_off;  // into the image's interval slots
+    uint32_t T;         // touched-cell incidences
+    uint32_t inc;       // centre-line incidences
+    int32_t wi0, wj0, wi1, wj1;
+    int32_t mbr[4];
+    uint32_t err;       // 0 ok; 1 fewer than 3 vertices; 2 outside the grid; 3 too many cells; 4 meets no cell
+    uint32_t pad;
+};
+
+struct Totals {
+    unsigned long long keys, rb, slots;
+    unsigned int n_err, first_err;
+    unsigned int err_code, pad;
+};
+
+__device__ __forceinline__ uint64_t even_up(uint64_t v) { return (v + 1) & ~1ull; }
+
+__device__ __forceinline__ int2 vtx(const int2 *xy, uint64_t b, uint64_t nv, uint64_t k) {
+    return xy[b + (k == nv ? 0 : k)];
+}
+
+// ------------------------------------------------------------------ count
+__global__ void __launch_bounds__(256) k_bcount(const int2 *__restrict__ xy, const uint64_t *__restrict__ off,
+                                                uint32_t n, GridP g, PolyMeta *meta, Totals *tot) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t nw = gridDim.x * (blockDim.x / 32);
+    for (uint32_t p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n; p += nw) {
+        const uint64_t b = off[p], e = off[p + 1];
+        uint32_t err = 0;
+        const uint64_t nv = e >= b ? e - b : 0;
+        if (e < b || nv < 3) err = 1;
+        int64_t xmn = INT64_MAX, ymn = INT64_MAX, xmx = INT64_MIN, ymx = INT64_MIN;
+        if (!err)
+            for (uint64_t k = lane; k < nv; k += 32) {
+                const int2 v = xy[b + k];
+                xmn = imin(xmn, v.x), xmx = imax(xmx, v.x), ymn = imin(ymn, v.y), ymx = imax(ymx, v.y);
+            }
+        for (int o = 16; o; o >>= 1) {
+            xmn = imin(xmn, __shfl_xor_sync(kFull, xmn, o));
+            ymn = imin(ymn, __shfl_xor_sync(kFull, ymn, o));
+            xmx = imax(xmx, __shfl_xor_sync(kFull, xmx, o));
+            ymx = imax(ymx, __shfl_xor_sync(kFull, ymx, o));
+        }
+        int64_t wi0 = 0, wj0 = 0, wi1 = -1, wj1 = -1;
+        if (!err) {
+            cell_window(xmn, ymn, xmx, ymx, g.ox, g.oy, g.h, g.G, wi0, wj0, wi1, wj1);
+            if (wi0 > wi1 || wj0 > wj1) err = 2;
+        }
+        unsigned long long T = 0, inc = 0;
+        if (!err)
+            for (uint64_t k = lane; k < nv; k += 32) {
+                const int2 a = vtx(xy, b, nv, k), c = vtx(xy, b, nv, k + 1);
+                const EdgeUp ed = edge_up(a.x, a.y, c.x, c.y);
+                int64_t j0, j1, r0, r1;
+                edge_rows(ed, g.oy, g.h, g.G, j0, j1);
+                for (int64_t j = j0; j <= j1; ++j) {
+                    int64_t i0, i1;
+                    if (edge_cells_in_row(ed, g.ox, g.oy, g.h, g.G, j, i0, i1)) T += (unsigned long long)(i1 - i0 + 1);
+                }
+                centre_rows(ed, g.oy, g.h, wj0, wj1, r0, r1);
+                if (r1 >= r0) inc += (unsigned long long)(r1 - r0 + 1);
+            }
+        for (int o = 16; o; o >>= 1) {
+            T += __shfl_xor_sync(kFull, T, o);
+            inc += __shfl_xor_sync(kFull, inc, o);
+        }
+        if (!err && (T > 0x7FFFFFFFull || inc > 0x7FFFFFFFull)) err = 3;
+        if (!err && T == 0) {
+            // no edge meets a cell: the polygon holds the whole grid or misses
+            // it; the centre of cell (0, 0) tells which (crossing parity)
+            const int64_t xc = g.ox + g.h / 2, yc = g.oy + g.h / 2;
+            uint32_t par = 0;
+            for (uint64_t k = lane; k < nv; k += 32) {
+                const int2 a = vtx(xy, b, nv, k), c = vtx(xy, b, nv, k + 1);
+                const EdgeUp ed = edge_up(a.x, a.y, c.x, c.y);
+                if (ed.ay <= yc && yc < ed.by && turn(ed.ax, ed.ay, ed.bx, ed.by, xc, yc) > 0) par ^= 1u;
+            }
+            for (int o = 16; o; o >>= 1) par ^= __shfl_xor_sync(kFull, par, o);
+            if (!par) err = 4;
+        }
+        if (lane == 0) {
+            PolyMeta m{};
+            m.T = err ? 0u : (uint32_t)T;
+            m.inc = err ? 0u : (uint32_t)inc;
+            m.wi0 = (int32_t)wi0, m.wj0 = (int32_t)wj0, m.wi1 = (int32_t)wi1, m.wj1 = (int32_t)wj1;
+            m.mbr[0] = (int32_t)xmn, m.mbr[1] = (int32_t)ymn, m.mbr[2] = (int32_t)xmx, m.mbr[3] = (int32_t)ymx;
+            m.err = err;
+            meta[p] = m;
+            if (err) {
+                atomicAdd(&tot->n_err, 1u);
+                if (atomicMin(&tot->first_err, p) > p) atomicExch(&tot->err_code, err);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------- scan
+// Exclusive offsets of keys (T), row buckets (2 rows + 1 + inc) and slots
+// (2 even(T + 1): |A| <= max(T, 1) and |F| <= T + 1) over the polygons, by
+// one CTA in contiguous chunks.
+constexpr unsigned kScanT = 1024;
+__global__ void __launch_bounds__(kScanT) k_bscan(PolyMeta *meta, uint32_t n, Totals *tot) {
+    __shared__ unsigned long long s_w[3][kScanT / 32];
+    const uint32_t t = threadIdx.x, lane = t & 31u, warp = t >> 5;
+    const uint32_t chunk = (n + kScanT - 1) / kScanT;
+    const uint32_t b = min(n, t * chunk), e = min(n, b + chunk);
+    unsigned long long s[3] = {0, 0, 0};
+    auto amounts = [&](const PolyMeta &m, unsigned long long *a) {
+        const unsigned long long rows = m.err ? 0 : (unsigned long long)(m.wj1 - m.wj0 + 1);
+        a[0] = m.T;
+        a[1] = m.err ? 0 : 2 * rows + 1 + m.inc;
+        a[2] = 2 * even_up((uint64_t)m.T + 1);
+    };
+    for (uint32_t k = b; k < e; ++k) {
+        unsigned long long a[3];
+        amounts(meta[k], a);
+        s[0] += a[0], s[1] += a[1], s[2] += a[2];
+    }
+    unsigned long long incl[3];
+    for (int f = 0; f < 3; ++f) {
+        incl[f] = s[f];
+        for (uint32_t d = 1; d < 32; d <<= 1) {
+            const unsigned long long v = __shfl_up_sync(kFull, incl[f], d);
+            if (lane >= d) incl[f] += v;
+        }
+        if (lane == 31) s_w[f][warp] = incl[f];
+    }
+    __syncthreads();
+    if (warp == 0)
+        for (int f = 0; f < 3; ++f) {
+            unsigned long long w = s_w[f][lane];
+            for (uint32_t d = 1; d < 32; d <<= 1) {
+                const unsigned long long v = __shfl_up_sync(kFull, w, d);
+                if (lane >= d) w += v;
+            }
+            s_w[f][lane] = w;
+        }
+    __syncthreads();
+    unsigned long long run[3];
+    for (int f = 0; f < 3; ++f) run[f] = incl[f] - s[f] + (warp ? s_w[f][warp - 1] : 0ull);
+    for (uint32_t k = b; k < e; ++k) {
+        unsigned long long a[3];
+        amounts(meta[k], a);
+        meta[k].key_off = run[0];
+        meta[k].rb_off = run[1];
+        meta[k].slot_off = run[2];
+        run[0] += a[0], run[1] += a[1], run[2] += a[2];
+    }
+    if (t == kScanT - 1) {
+        tot->keys = s_w[0][31];
+        tot->rb = s_w[1][31];
+        tot->slots = s_w[2][31];
+    }
+}
+
+// ------------------------------------------------------------ CTA helpers
+struct BuildShared {
+    uint32_t warp_sum[kBW];
+    uint32_t hist[16];
+    uint32_t base[16];
+    uint32_t wcnt[kBW][16];
+    uint32_t wpre[kBW][16];
+    unsigned long long red[kBW][2];
+    uint32_t item;
+    uint32_t carry;
+    uint32_t k_count;
+};
+
+// Exclusive scan of one value per thread over the CTA; *total gets the sum.
+__device__ __forceinline__ uint32_t block_scan(uint32_t v, uint32_t &total, BuildShared &sh) {
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+    for (uint32_t d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) sh.warp_sum[warp] = x;
+    __syncthreads();
+    uint32_t before = 0, all = 0;
+    for (uint32_t w = 0; w < kBW; ++w) {
+        if (w < warp) before += sh.warp_sum[w];
+        all += sh.warp_sum[w];
+    }
+    __syncthreads();
+    total = all;
+    return before + x - v;
+}
+
+// Point-in-polygon at the centre of cell (i, j): a crossing count over the
+// edges bucketed at row j (host builder's rule: an upward edge toggles when
+// the centre is strictly left of it).  Cells outside the window are outside.
+__device__ bool inside_cell(uint32_t i, uint32_t j, const PolyMeta &M, const GridP &g, const int2 *xy, uint64_t b,
+                            uint64_t nv, const uint32_t *row_start, const uint32_t *row_edges) {
+    if ((int64_t)i < M.wi0 || (int64_t)i > M.wi1 || (int64_t)j < M.wj0 || (int64_t)j > M.wj1) return false;
+    const int64_t xc = g.ox + (int64_t)i * g.h + g.h / 2, yc = g.oy + (int64_t)j * g.h + g.h / 2;
+    const uint32_t r = j - (uint32_t)M.wj0;
+    bool in = false;
+    for (uint32_t q = row_start[r]; q < row_start[r + 1]; ++q) {
+        const uint32_t k = row_edges[q];
+        const int2 a = vtx(xy, b, nv, k), c = vtx(xy, b, nv, k + 1);
+        const EdgeUp ed = edge_up(a.x, a.y, c.x, c.y);
+        if (turn(ed.ax, ed.ay, ed.bx, ed.by, xc, yc) > 0) in = !in;
+    }
+    return in;
+}
+
+// Stable LSD radix sort of keys[0..T) (4-bit digits of key - kmin, `passes`
+// passes), ping-ponging with tmp; returns the buffer holding the result.
+__device__ unsigned long long *cta_radix_sort(unsigned long long *keys, unsigned long long *tmp, uint32_t T,
+                                              unsigned long long kmin, uint32_t passes, BuildShared &sh) {
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    unsigned long long *src = keys, *dst = tmp;
+    for (uint32_t pass = 0; pass < passes; ++pass) {
+        const uint32_t sft = 4 * pass;
+        if (tid < 16) sh.hist[tid] = 0;
+        __syncthreads();
+        for (uint32_t k = tid; k < T; k += kBB) atomicAdd(&sh.hist[((src[k] - kmin) >> sft) & 15u], 1u);
+        __syncthreads();
+        if (tid == 0) {
+            uint32_t run = 0;
+            for (int v = 0; v < 16; ++v) {
+                sh.base[v] = run;
+                run += sh.hist[v];
+            }
+        }
+        __syncthreads();
+        for (uint32_t t0 = 0; t0 < T; t0 += kBB) {
+            const uint32_t k = t0 + tid;
+            const bool valid = k < T;
+            const unsigned long long key = valid ? src[k] : 0ull;
+            const uint32_t dg = valid ? (uint32_t)((key - kmin) >> sft) & 15u : 16u;
+            uint32_t mine = 0, cnt = 0;
+            for (uint32_t v = 0; v < 16; ++v) {
+                const uint32_t m = __ballot_sync(kFull, dg == v);
+                if (lane == v) cnt = __popc(m);
+                if (dg == v) mine = m;
+            }
+            if (lane < 16) sh.wcnt[warp][lane] = cnt;
+            __syncthreads();
+            if (tid < 16) {
+                uint32_t run = 0;
+                for (uint32_t w = 0; w < kBW; ++w) {
+                    sh.wpre[w][tid] = run;
+                    run += sh.wcnt[w][tid];
+                }
+                sh.hist[tid] = run;  // this tile's count of digit tid
+            }
+            __syncthreads();
+            if (valid) dst[sh.base[dg] + sh.wpre[warp][dg] + __popc(mine & ((1u << lane) - 1u))] = key;
+            __syncthreads();
+            if (tid < 16) sh.base[tid] += sh.hist[tid];
+            __syncthreads();
+        }
+        unsigned long long *t = src;
+        src = dst;
+        dst = t;
+    }
+    return src;
+}
+
+// ------------------------------------------------------------------ build
+__global__ void __launch_bounds__(kBB) k_bconstruct(const int2 *__restrict__ xy, const uint64_t *__restrict__ off,
+                                                    uint32_t n, GridP g, const PolyMeta *__restrict__ meta,
+                                                    unsigned long long *keys_all, unsigned long long *tmp_all,
+                                                    uint8_t *flags_all, uint32_t *rb_all, uint32_t *desc_out,
+                                                    int4 *mbr_out, uint2 *iv_out, uint32_t *counter) {
+    __shared__ BuildShared sh;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint64_t ncells = (uint64_t)g.G * (uint64_t)g.G;
+    for (;;) {
+        if (tid == 0) sh.item = atomicAdd(counter, 1u);
+        __syncthreads();
+        const uint32_t p = sh.item;
+        __syncthreads();
+        if (p >= n) break;
+        const PolyMeta M = meta[p];
+        const uint64_t b = off[p], nv = off[p + 1] - b;
+        const uint32_t T = M.T;
+        unsigned long long *keys = keys_all + M.key_off, *tmp = tmp_all + M.key_off;
+        uint8_t *flags = flags_all + M.key_off;
+        const uint32_t rows = (uint32_t)(M.wj1 - M.wj0 + 1);
+        uint32_t *row_start = rb_all + M.rb_off, *row_cur = row_start + rows + 1, *row_edges = row_cur + rows;
+        if (tid == 0) mbr_out[p] = make_int4(M.mbr[0], M.mbr[1], M.mbr[2], M.mbr[3]);
+        if (T == 0) {  // the polygon holds the whole grid (the count pass checked)
+            if (tid == 0) {
+                uint2 *lists = iv_out + M.slot_off;
+                lists[0] = make_uint2(0u, (uint32_t)ncells);  // 2^32 wraps to 0 by design
+                lists[2] = make_uint2(0u, (uint32_t)ncells);
+                uint32_t *dsc = desc_out + 4 * (size_t)p;
+                dsc[0] = (uint32_t)M.slot_off, dsc[1] = 1u, dsc[2] = (uint32_t)(M.slot_off + 2), dsc[3] = 1u;
+            }
+            continue;
+        }
+
+        // 1. touched-cell keys, edge by edge; kmin / kmax for the sort
+        unsigned long long kmin = ~0ull, kmax = 0;
+        uint32_t carry = 0;
+        for (uint64_t e0 = 0; e0 < nv; e0 += kBB) {
+            const uint64_t k = e0 + tid;
+            EdgeUp ed{0, 0, 0, 0};
+            int64_t j0 = 0, j1 = -1;
+            uint32_t cnt = 0;
+            if (k < nv) {
+                const int2 a = vtx(xy, b, nv, k), c = vtx(xy, b, nv, k + 1);
+                ed = edge_up(a.x, a.y, c.x, c.y);
+                edge_rows(ed, g.oy, g.h, g.G, j0, j1);
+                for (int64_t j = j0; j <= j1; ++j) {
+                    int64_t i0, i1;
+                    if (edge_cells_in_row(ed, g.ox, g.oy, g.h, g.G, j, i0, i1)) cnt += (uint32_t)(i1 - i0 + 1);
+                }
+            }
+            uint32_t total;
+            uint32_t pos = carry + block_scan(cnt, total, sh);
+            carry += total;
+            if (k < nv)
+                for (int64_t j = j0; j <= j1; ++j) {
+                    int64_t i0, i1;
+                    if (!edge_cells_in_row(ed, g.ox, g.oy, g.h, g.G, j, i0, i1)) continue;
+                    const int64_t Y0 = g.oy + j * g.h;
+                    for (int64_t i = i0; i <= i1; ++i) {
+                        const bool crossed = enters_open_square(ed.ax, ed.ay, ed.bx, ed.by, g.ox + i * g.h, Y0, g.h);
+                        const unsigned long long key =
+                            (hilbert_id(g.order, (uint32_t)i, (uint32_t)j) << 1) | (crossed ? 1ull : 0ull);
+                        if (pos < T) keys[pos] = key;
+                        ++pos;
+                        kmin = key < kmin ? key : kmin;
+                        kmax = key > kmax ? key : kmax;
+                    }
+                }
+        }
+        for (int o = 16; o; o >>= 1) {
+            const unsigned long long a = __shfl_xor_sync(kFull, kmin, o), c = __shfl_xor_sync(kFull, kmax, o);
+            kmin = a < kmin ? a : kmin;
+            kmax = c > kmax ? c : kmax;
+        }
+        if (lane == 0) sh.red[warp][0] = kmin, sh.red[warp][1] = kmax;
+        __syncthreads();
+        kmin = ~0ull, kmax = 0;
+        for (uint32_t w = 0; w < kBW; ++w) {
+            kmin = sh.red[w][0] < kmin ? sh.red[w][0] : kmin;
+            kmax = sh.red[w][1] > kmax ? sh.red[w][1] : kmax;
+        }
+        __syncthreads();
+
+        // 2. sort, then one key per cell (the last of a cell's run carries
+        //    the crossed flag when any edge crossed it: (d << 1) | 1 sorts last)
+        const unsigned long long span = kmax - kmin;
+        const uint32_t bits = span ? 64u - (uint32_t)__clzll((long long)span) : 1u;
+        unsigned long long *sorted = cta_radix_sort(keys, tmp, T, kmin, (bits + 3) / 4, sh);
+        unsigned long long *U = sorted == keys ? tmp : keys;
+        carry = 0;
+        for (uint32_t t0 = 0; t0 < T; t0 += kBB) {
+            const uint32_t k = t0 + tid;
+            bool last = false;
+            unsigned long long key = 0;
+            if (k < T) {
+                key = sorted[k];
+                last = k + 1 == T || (sorted[k + 1] >> 1) != (key >> 1);
+            }
+            uint32_t total;
+            const uint32_t pos = carry + block_scan(last ? 1u : 0u, total, sh);
+            if (last) U[pos] = key;
+            carry += total;
+        }
+        const uint32_t K = carry;
+
+        // 3. edges bucketed by the row whose centre line they cross
+        for (uint32_t r = tid; r < 2 * rows + 1; r += kBB) row_start[r] = 0;
+        __syncthreads();
+        for (uint64_t k = tid; k < nv; k += kBB) {
+            const int2 a = vtx(xy, b, nv, k), c = vtx(xy, b, nv, k + 1);
+            int64_t r0, r1;
+            centre_rows(edge_up(a.x, a.y, c.x, c.y), g.oy, g.h, M.wj0, M.wj1, r0, r1);
+            for (int64_t r = r0; r <= r1; ++r) atomicAdd(&row_start[r - M.wj0 + 1], 1u);
+        }
+        __syncthreads();
+        carry = 0;
+        for (uint32_t r0 = 0; r0 < rows + 1; r0 += kBB) {
+            const uint32_t r = r0 + tid;
+            const uint32_t v = r < rows + 1 ? row_start[r] : 0u;
+            uint32_t total;
+            const uint32_t ex = carry + block_scan(v, total, sh);
+            if (r < rows + 1) row_start[r] = ex + v;  // inclusive: row_start[r] = first edge of row r
+            carry += total;
+        }
+        for (uint32_t r = tid; r < rows; r += kBB) row_cur[r] = 0;
+        __syncthreads();
+        for (uint64_t k = tid; k < nv; k += kBB) {
+            const int2 a = vtx(xy, b, nv, k), c = vtx(xy, b, nv, k + 1);
+            int64_t r0, r1;
+            centre_rows(edge_up(a.x, a.y, c.x, c.y), g.oy, g.h, M.wj0, M.wj1, r0, r1);
+            for (int64_t r = r0; r <= r1; ++r) {
+                const uint32_t rr = (uint32_t)(r - M.wj0);
+                row_edges[row_start[rr] + atomicAdd(&row_cur[rr], 1u)] = (uint32_t)k;
+            }
+        }
+        __syncthreads();
+
+        // 4. classification: bit 0 gap before the cell non-empty, bit 1 that
+        //    gap Full, bit 2 the cell Full
+        for (uint32_t u = tid; u < K; u += kBB) {
+            const unsigned long long key = U[u];
+            const uint64_t d = key >> 1;
+            const uint64_t first_gap = u ? (U[u - 1] >> 1) + 1 : 0;
+            uint8_t f = 0;
+            uint32_t x, y;
+            if (d > first_gap) {
+                f |= 1;
+                hilbert_cell(g.order, first_gap, x, y);
+                if (inside_cell(x, y, M, g, xy, b, nv, row_start, row_edges)) f |= 2;
+            }
+            if (!(key & 1ull)) {
+                hilbert_cell(g.order, d, x, y);
+                if (inside_cell(x, y, M, g, xy, b, nv, row_start, row_edges)) f |= 4;
+            }
+            flags[u] = f;
+        }
+        if (tid == 0) {
+            const uint64_t nxt = (U[K - 1] >> 1) + 1;
+            bool tail = false;
+            if (nxt < ncells) {
+                uint32_t x, y;
+                hilbert_cell(g.order, nxt, x, y);
+                tail = inside_cell(x, y, M, g, xy, b, nv, row_start, row_edges);
+            }
+            sh.k_count = tail ? 1u : 0u;
+        }
+        __syncthreads();
+        const bool tailF = sh.k_count != 0;
+
+        // 5. intervals
+        uint2 *Aout = iv_out + M.slot_off;
+        uint2 *Fout = iv_out + M.slot_off + even_up((uint64_t)T + 1);
+        uint32_t na = 0, nf = 0;
+        {
+            // A: a new interval at every cell after a non-empty gap that is not Full
+            uint32_t ca = 0, cf = 0;
+            for (uint32_t t0 = 0; t0 < K; t0 += kBB) {
+                const uint32_t u = t0 + tid;
+                const bool ok = u < K;
+                const uint8_t f = ok ? flags[u] : 0;
+                const uint64_t d = ok ? (U[u] >> 1) : 0;
+                const uint64_t prev_end = (ok && u) ? (U[u - 1] >> 1) + 1 : 0;  // end of the previous cell
+                const bool brk = ok && u > 0 && (f & 1) && !(f & 2);
+                uint32_t ta;
+                const uint32_t ia = ca + block_scan(brk ? 1u : 0u, ta, sh);
+                if (brk) {
+                    Aout[ia].y = (uint32_t)prev_end;  // the interval before closes
+                    Aout[ia + 1].x = (uint32_t)d;
+                }
+                if (ok && u == 0) Aout[0].x = ((f & 1) && (f & 2)) ? 0u : (uint32_t)d;
+                ca += ta;
+                // F: slots gap(u) then cell(u); a run starts where an F slot
+                // follows a non-F one and ends where a non-F one follows
+                const bool gF = ok && (f & 2);
+                const bool cF = ok && (f & 4);
+                const bool prevCellF = ok && u > 0 && (flags[u - 1] & 4);
+                const bool prev_of_cell = (f & 1) ? gF : prevCellF;
+                bool next_of_cell = tailF;
+                if (ok && u + 1 < K) {
+                    const uint8_t fn = flags[u + 1];
+                    next_of_cell = (fn & 1) ? (fn & 2) != 0 : (fn & 4) != 0;
+                }
+                const bool sg = gF && !prevCellF, sc = cF && !prev_of_cell;
+                const bool eg = gF && !cF, ec = cF && !next_of_cell;
+                uint32_t tf;
+                const uint32_t i0 = cf + block_scan((sg ? 1u : 0u) + (sc ? 1u : 0u), tf, sh);
+                if (sg) Fout[i0].x = (uint32_t)prev_end;                     // gap starts after the previous cell
+                if (eg) Fout[i0 + (sg ? 1u : 0u) - 1u].y = (uint32_t)d;        // and ends at this cell
+                if (sc) Fout[i0 + (sg ? 1u : 0u)].x = (uint32_t)d;
+                if (ec) Fout[i0 + (sg ? 1u : 0u) + (sc ? 1u : 0u) - 1u].y = (uint32_t)(d + 1);
+                cf += tf;
+            }
+            na = ca + 1;
+            nf = cf;
+            if (tid == 0) {
+                const uint64_t last_end = (U[K - 1] >> 1) + 1;
+                Aout[na - 1].y = (uint32_t)(tailF ? ncells : last_end);  // 2^32 wraps to 0 by design
+                const bool lastCellF = (flags[K - 1] & 4) != 0;
+                if (tailF) {
+                    if (!lastCellF) Fout[nf].x = (uint32_t)last_end;
+                    Fout[lastCellF ? nf - 1 : nf].y = (uint32_t)ncells;
+                }
+            }
+            if (tailF && !(flags[K - 1] & 4)) nf += 1;
+        }
+        if (tid == 0) {
+            uint32_t *dsc = desc_out + 4 * (size_t)p;
+            dsc[0] = (uint32_t)M.slot_off;
+            dsc[1] = na;
+            dsc[2] = (uint32_t)(M.slot_off + even_up((uint64_t)T + 1));
+            dsc[3] = nf;
+        }
+        __syncthreads();
+    }
+}
+
+april_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(APRIL_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+inline uint64_t r256(uint64_t b) { return april_round256(b); }
+
+struct WorkLayout {
+    uint64_t totals, meta, keys, tmp, flags, rb, total;
+};
+
+WorkLayout work_layout(uint32_t n, uint64_t keys, uint64_t rb) {
+    WorkLayout L{};
+    uint64_t o = 0;
+    L.totals = o;
+    o += 256;
+    L.meta = o;
+    o += r256((uint64_t)n * sizeof(PolyMeta));
+    const uint64_t min_total = o;
+    L.keys = o;
+    o += r256(keys * 8);
+    L.tmp = o;
+    o += r256(keys * 8);
+    L.flags = o;
+    o += r256(keys);
+    L.rb = o;
+    o += r256(rb * 4);
+    L.total = keys || rb ? o : min_total;
+    return L;
+}
+
+}  // namespace
+
+extern "C" april_status april_build_sets_device(april_ctx *ctx, const int32_t *d_xy, const uint64_t *d_vert_off,
+                                                uint32_t n_polys, const april_grid *grid, void *d_work,
+                                                size_t work_bytes, void *d_image, size_t image_bytes,
+                                                april_dev_sets *out, april_device_build_info *info, void *stream) {
+    if (!ctx || !info || !out) return fail(APRIL_ERR_INVALID_ARG, "NULL argument");
+    *info = april_device_build_info{};
+    GridP g{};
+    april_status st = april::check_grid_params(grid, g.ox, g.oy, g.h, g.order, g.G);
+    if (st) return st;
+    if (n_polys == 0) return fail(APRIL_ERR_INVALID_ARG, "no polygons");
+    if (!d_xy || !d_vert_off) return fail(APRIL_ERR_INVALID_ARG, "NULL polygon arrays");
+    if ((((uintptr_t)d_xy) & 7u) || (((uintptr_t)d_vert_off) & 7u))
+        return fail(APRIL_ERR_INVALID_ARG, "polygon arrays must be 8-byte aligned");
+    const WorkLayout L0 = work_layout(n_polys, 0, 0);
+    info->work_bytes = L0.total;
+    if (!d_work || work_bytes < L0.total) return fail(APRIL_ERR_OVER_BUDGET, "work buffer below the counting size");
+    if (((uintptr_t)d_work) & 255u) return fail(APRIL_ERR_INVALID_ARG, "work buffer must be 256-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    char *work = (char *)d_work;
+    auto *tot = (Totals *)(work + L0.totals);
+    auto *meta = (PolyMeta *)(work + L0.meta);
+    cudaError_t e = cudaMemsetAsync(tot, 0, sizeof(Totals), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&tot->first_err, 0xFF, 4, s);
+    const int sms = april_ctx_num_sms(ctx);
+    const unsigned gcount = (unsigned)std::max<uint64_t>(
+        1, std::min<uint64_t>(((uint64_t)n_polys * 32 + 255) / 256, (uint64_t)sms * 8));
+    if (e == cudaSuccess) {
+        k_bcount<<<gcount, 256, 0, s>>>((const int2 *)d_xy, d_vert_off, n_polys, g, meta, tot);
+        k_bscan<<<1, kScanT, 0, s>>>(meta, n_polys, tot);
+        e = cudaGetLastError();
+    }
+    Totals h{};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, tot, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "counting cells on the device");
+    if (h.n_err) {
+        char m[160];
+        const char *why = h.err_code == 1   ? "fewer than 3 vertices (or offsets not monotone)"
+                          : h.err_code == 2 ? "outside the grid"
+                          : h.err_code == 4 ? "meets no cell"
+                                            : "more than 2^31 cells";
+        std::snprintf(m, sizeof m, "polygon %u: %s (%u polygons rejected)", h.first_err, why, h.n_err);
+        return fail(h.err_code == 3 ? APRIL_ERR_INVALID_ARG : APRIL_ERR_GEOMETRY, m);
+    }
+    const WorkLayout L = work_layout(n_polys, h.keys, h.rb);
+    const uint64_t desc_b = r256((uint64_t)n_polys * 16), mbr_b = r256((uint64_t)n_polys * 16);
+    const uint64_t img = desc_b + mbr_b + r256(h.slots * 8 + 16);
+    info->touched_cells = h.keys;
+    info->work_bytes = L.total;
+    info->image_bytes = img;
+    info->iv_slots = h.slots;
+    if (h.slots > 0xFFFFFFF0ull) return fail(APRIL_ERR_INVALID_ARG, "more than 2^32 interval slots in one set");
+    if (work_bytes < L.total) return fail(APRIL_ERR_OVER_BUDGET, "work buffer too small");
+    if (!d_image || image_bytes < img) return fail(APRIL_ERR_OVER_BUDGET, "image buffer too small");
+    if (((uintptr_t)d_image) & 255u) return fail(APRIL_ERR_INVALID_ARG, "image buffer must be 256-byte aligned");
+    char *image = (char *)d_image;
+    uint32_t *counter = (uint32_t *)&tot->pad;
+    e = cudaMemsetAsync(counter, 0, 4, s);
+    int occ = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bconstruct, kBB, 0);
+    const unsigned gbuild = (unsigned)std::max<uint64_t>(
+        1, std::min<uint64_t>(n_polys, (uint64_t)sms * (uint64_t)std::max(occ, 1)));
+    if (e == cudaSuccess) {
+        k_bconstruct<<<gbuild, kBB, 0, s>>>((const int2 *)d_xy, d_vert_off, n_polys, g, meta,
+                                            (unsigned long long *)(work + L.keys), (unsigned long long *)(work + L.tmp),
+                                            (uint8_t *)(work + L.flags), (uint32_t *)(work + L.rb), (uint32_t *)image,
+                                            (int4 *)(image + desc_b), (uint2 *)(image + desc_b + mbr_b), counter);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "building lists on the device");
+    *out = april_dev_sets{};
+    out->desc = (const uint32_t *)image;
+    out->iv = (const uint32_t *)(image + desc_b + mbr_b);
+    out->mbr = (const int32_t *)(image + desc_b);
+    out->n_objects = n_polys;
+    out->order = g.order;
+    out->iv_slots = h.slots;
+    out->n_entries = n_polys;
+    return APRIL_OK;
+}

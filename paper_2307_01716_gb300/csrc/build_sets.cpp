@@ -31,6 +31,7 @@
 #include <thread>
 
 #include "april_internal.h"
+#include "geom.h"
 
 namespace april {
 
@@ -43,80 +44,7 @@ april_status fail(april_status code, const std::string &msg) {
 
 namespace {
 
-// ---------------------------------------------------------------- Hilbert
-// The curve of Sec. 3.2 (orientation: the order-1 curve visits (0,0), (0,1),
-// (1,1), (1,0)).  Walking down the levels, the sub-square the point lies in
-// is traversed by the base curve under one of four symmetries of the square:
-// identity, transpose (x<->y), anti-transpose ((x,y) -> (~y,~x) per bit) and
-// the half turn ((x,y) -> (~x,~y)).  Quadrant 0 of the base curve carries the
-// transpose, quadrant 3 the anti-transpose, quadrants 1 and 2 the identity;
-// these four maps form a Klein group, so the state update is a table lookup.
-enum : uint8_t { SYM_I = 0, SYM_T = 1, SYM_A = 2, SYM_R = 3 };
-static const uint8_t kAfterT[4] = {SYM_T, SYM_I, SYM_R, SYM_A};
-static const uint8_t kAfterA[4] = {SYM_A, SYM_R, SYM_I, SYM_T};
-
-inline void apply_sym(uint8_t s, uint32_t &bx, uint32_t &by) {
-    uint32_t x = bx, y = by;
-    switch (s) {
-        case SYM_I: break;
-        case SYM_T: bx = y; by = x; break;
-        case SYM_A: bx = y ^ 1u; by = x ^ 1u; break;
-        default: bx = x ^ 1u; by = y ^ 1u; break;
-    }
-}
-
-inline uint64_t hilbert_id(uint32_t order, uint32_t x, uint32_t y) {
-    uint8_t s = SYM_I;
-    uint64_t d = 0;
-    for (int k = (int)order - 1; k >= 0; --k) {
-        uint32_t bx = (x >> k) & 1u, by = (y >> k) & 1u;
-        apply_sym(s, bx, by);
-        uint32_t digit = (bx << 1) | (bx ^ by);  // (0,0)->0 (0,1)->1 (1,1)->2 (1,0)->3
-        d = (d << 2) | digit;
-        if (digit == 0) s = kAfterT[s];
-        else if (digit == 3) s = kAfterA[s];
-    }
-    return d;
-}
-
-inline void hilbert_cell(uint32_t order, uint64_t d, uint32_t &x, uint32_t &y) {
-    uint8_t s = SYM_I;
-    x = y = 0;
-    for (int k = (int)order - 1; k >= 0; --k) {
-        uint32_t digit = (uint32_t)(d >> (2 * k)) & 3u;
-        uint32_t bx = digit >> 1, by = (digit >> 1) ^ (digit & 1u);
-        apply_sym(s, bx, by);  // every symmetry here is its own inverse
-        x |= bx << k;
-        y |= by << k;
-        if (digit == 0) s = kAfterT[s];
-        else if (digit == 3) s = kAfterA[s];
-    }
-}
-
-// ------------------------------------------------------------- predicates
-inline int64_t floor_div(int64_t a, int64_t b) {  // b > 0
-    int64_t q = a / b;
-    return (a % b != 0 && a < 0) ? q - 1 : q;
-}
-inline int64_t ceil_div(int64_t a, int64_t b) { return -floor_div(-a, b); }
-
-inline int64_t turn(int64_t ax, int64_t ay, int64_t bx, int64_t by, int64_t px, int64_t py) {
-    return (bx - ax) * (py - ay) - (by - ay) * (px - ax);
-}
-
-// Closed segment vs open square (x0,x0+h) x (y0,y0+h): they are disjoint iff
-// weakly separated along x, along y, or along the segment's normal.
-inline bool enters_open_square(int64_t ax, int64_t ay, int64_t bx, int64_t by, int64_t x0, int64_t y0,
-                               int64_t h) {
-    int64_t x1 = x0 + h, y1 = y0 + h;
-    if (std::max(ax, bx) <= x0 || std::min(ax, bx) >= x1) return false;
-    if (std::max(ay, by) <= y0 || std::min(ay, by) >= y1) return false;
-    int64_t t[4] = {turn(ax, ay, bx, by, x0, y0), turn(ax, ay, bx, by, x1, y0),
-                    turn(ax, ay, bx, by, x1, y1), turn(ax, ay, bx, by, x0, y1)};
-    bool pos = t[0] >= 0 && t[1] >= 0 && t[2] >= 0 && t[3] >= 0;
-    bool neg = t[0] <= 0 && t[1] <= 0 && t[2] <= 0 && t[3] <= 0;
-    return !(pos || neg);
-}
+using namespace april_geom;
 
 struct GridI {
     int64_t ox, oy, h;
@@ -171,54 +99,31 @@ april_status build_one(const int32_t *xy, uint64_t nv, const GridI &g, Scratch &
         ymx = std::max<int64_t>(ymx, xy[2 * k + 1]);
     }
     // window of cells meeting the MBR
-    int64_t wi0 = std::max<int64_t>(ceil_div(xmn - ox, h) - 1, 0);
-    int64_t wi1 = std::min<int64_t>(floor_div(xmx - ox, h), G - 1);
-    int64_t wj0 = std::max<int64_t>(ceil_div(ymn - oy, h) - 1, 0);
-    int64_t wj1 = std::min<int64_t>(floor_div(ymx - oy, h), G - 1);
+    int64_t wi0, wj0, wi1, wj1;
+    cell_window(xmn, ymn, xmx, ymx, ox, oy, h, G, wi0, wj0, wi1, wj1);
     if (wi0 > wi1 || wj0 > wj1) return fail(APRIL_ERR_GEOMETRY, "polygon outside the grid");
 
     // edges, upward
     sc.ex0.resize(nv); sc.ey0.resize(nv); sc.ex1.resize(nv); sc.ey1.resize(nv);
     for (uint64_t k = 0; k < nv; ++k) {
-        uint64_t kn = (k + 1 == nv) ? 0 : k + 1;
-        int64_t ax = xy[2 * k], ay = xy[2 * k + 1], bx = xy[2 * kn], by = xy[2 * kn + 1];
-        if (ay > by || (ay == by && ax > bx)) {
-            std::swap(ax, bx);
-            std::swap(ay, by);
-        }
-        sc.ex0[k] = ax; sc.ey0[k] = ay; sc.ex1[k] = bx; sc.ey1[k] = by;
+        const uint64_t kn = (k + 1 == nv) ? 0 : k + 1;
+        const EdgeUp e = edge_up(xy[2 * k], xy[2 * k + 1], xy[2 * kn], xy[2 * kn + 1]);
+        sc.ex0[k] = e.ax; sc.ey0[k] = e.ay; sc.ex1[k] = e.bx; sc.ey1[k] = e.by;
     }
 
     // 1. touched cells, row by row per edge
     sc.keys.clear();
     for (uint64_t k = 0; k < nv; ++k) {
-        const int64_t ax = sc.ex0[k], ay = sc.ey0[k], bx = sc.ex1[k], by = sc.ey1[k];
-        int64_t j0 = std::max<int64_t>(ceil_div(ay - oy, h) - 1, 0);
-        int64_t j1 = std::min<int64_t>(floor_div(by - oy, h), G - 1);
-        const int64_t den = by - ay;  // >= 0
+        const EdgeUp e{sc.ex0[k], sc.ey0[k], sc.ex1[k], sc.ey1[k]};
+        int64_t j0, j1;
+        edge_rows(e, oy, h, G, j0, j1);
         for (int64_t j = j0; j <= j1; ++j) {
-            const int64_t Y0 = oy + j * h, Y1 = Y0 + h;
             int64_t i0, i1;
-            if (den == 0) {
-                // horizontal edge: in this closed strip iff Y0 <= ay <= Y1
-                if (ay < Y0 || ay > Y1) continue;
-                i0 = ceil_div(ax - ox, h) - 1;
-                i1 = floor_div(bx - ox, h);
-            } else {
-                const int64_t ya = std::max(ay, Y0), yb = std::min(by, Y1);
-                if (ya > yb) continue;
-                const int64_t dx = bx - ax;
-                const int64_t n1 = ax * den + (ya - ay) * dx;  // x(ya) * den
-                const int64_t n2 = ax * den + (yb - ay) * dx;  // x(yb) * den
-                const int64_t lo = std::min(n1, n2) - ox * den, hi = std::max(n1, n2) - ox * den;
-                i0 = ceil_div(lo, den * h) - 1;
-                i1 = floor_div(hi, den * h);
-            }
-            i0 = std::max<int64_t>(i0, 0);
-            i1 = std::min<int64_t>(i1, G - 1);
+            if (!edge_cells_in_row(e, ox, oy, h, G, j, i0, i1)) continue;
+            const int64_t Y0 = oy + j * h;
             for (int64_t i = i0; i <= i1; ++i) {
-                bool crossed = enters_open_square(ax, ay, bx, by, ox + i * h, Y0, h);
-                uint64_t d = hilbert_id(g.order, (uint32_t)i, (uint32_t)j);
+                const bool crossed = enters_open_square(e.ax, e.ay, e.bx, e.by, ox + i * h, Y0, h);
+                const uint64_t d = hilbert_id(g.order, (uint32_t)i, (uint32_t)j);
                 sc.keys.push_back((d << 1) | (crossed ? 1u : 0u));
             }
         }
@@ -230,11 +135,7 @@ april_status build_one(const int32_t *xy, uint64_t nv, const GridI &g, Scratch &
     const int64_t nrows = wj1 - wj0 + 1;
     sc.row_start.assign((size_t)nrows + 1, 0);
     auto row_span = [&](uint64_t k, int64_t &r0, int64_t &r1) {
-        // rows j with ey0 <= oy + j*h + h/2 < ey1
-        r0 = ceil_div(sc.ey0[k] - oy - h / 2, h);
-        r1 = ceil_div(sc.ey1[k] - oy - h / 2, h) - 1;
-        r0 = std::max(r0, wj0);
-        r1 = std::min(r1, wj1);
+        centre_rows(EdgeUp{sc.ex0[k], sc.ey0[k], sc.ex1[k], sc.ey1[k]}, oy, h, wj0, wj1, r0, r1);
     };
     for (uint64_t k = 0; k < nv; ++k) {
         int64_t r0, r1;
@@ -398,6 +299,15 @@ inline void part_range(int64_t lo, int64_t hi, int64_t side, int64_t parts, int6
 }
 
 }  // namespace
+
+april_status check_grid_params(const april_grid *grid, int64_t &ox, int64_t &oy, int64_t &h, uint32_t &order,
+                               int64_t &G) {
+    GridI g{};
+    const april_status st = check_grid(grid, g);
+    if (st) return st;
+    ox = g.ox, oy = g.oy, h = g.h, order = g.order, G = g.G;
+    return APRIL_OK;
+}
 
 }  // namespace april
 
