@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--serving-requests", type=int, default=120)
     ap.add_argument("--no-selection", action="store_true", help="skip the selection-query measurement")
     ap.add_argument("--no-variants", action="store_true", help="skip the within / mixed-granularity measurement")
+    ap.add_argument("--no-construction", action="store_true", help="skip the GPU construction measurement")
     return ap.parse_args()
 
 
@@ -248,8 +249,38 @@ def selection_bench(ctx, A, torch, dev, stream, flush, R, dR, steps, warmup):
         h_v.copy_(d_v, non_blocking=True)
         stream.synchronize()
         e2e.append(time.perf_counter() - t0)
+    # end to end with the query lists built on the GPU: pinned host polygons
+    # copied in, construction, selection, verdicts back
+    h_xy = torch.from_numpy(np.ascontiguousarray(s.Q.xy, dtype=np.int32)).pin_memory()
+    h_off = torch.from_numpy(np.ascontiguousarray(s.Q.off, dtype=np.int64)).pin_memory()
+    d_xy = torch.empty_like(h_xy, device=dev)
+    d_off = torch.empty_like(h_off, device=dev)
+    d_xy.copy_(h_xy)
+    d_off.copy_(h_off)
+    _, binfo = ctx.april_build_sets_device(d_xy, d_off, g, stream=stream)
+    bwork = torch.empty(int(binfo.work_bytes), dtype=torch.uint8, device=dev)
+    bimage = torch.empty(int(binfo.image_bytes), dtype=torch.uint8, device=dev)
+    e2e_dev = []
+    for k in range(max(3, steps)):
+        flush.fill_(k & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d_xy.copy_(h_xy, non_blocking=True)
+        d_off.copy_(h_off, non_blocking=True)
+        dQk, _ = ctx.april_build_sets_device(d_xy, d_off, g, work=bwork, image=bimage, stream=stream)
+        ctx.april_select(dI, dR, dQk, n, d_r, d_q, d_v, off, scratch, stream)
+        h_v.copy_(d_v, non_blocking=True)
+        stream.synchronize()
+        e2e_dev.append(time.perf_counter() - t0)
+    if not np.array_equal(h_v.numpy(), hv):
+        raise SystemExit("selection with GPU-built query lists differs")
     ms = statistics.mean(t)
+    e2e_dev_ms = statistics.mean(e2e_dev[1:]) * 1e3
     return {"workload": s.name, "queries": int(s.Q.n), "candidate_pairs": int(n), "ms_per_batch": ms,
+            "e2e_gpu_construction": {"ms_per_batch": e2e_dev_ms, "queries_per_s": s.Q.n / (e2e_dev_ms * 1e-3),
+                                     "h2d_bytes": int(h_xy.numel() * 4 + h_off.numel() * 8), "d2h_bytes": int(n),
+                                     "path": "pinned query polygons to the GPU + april_build_sets_device + "
+                                             "april_select + verdicts to host"},
             "queries_per_s": s.Q.n / (ms * 1e-3), "pairs_per_s": n / (ms * 1e-3),
             "query_list_build_ms_host": build_s * 1e3,
             "e2e": {"ms_per_batch": statistics.mean(e2e) * 1e3,
@@ -258,6 +289,42 @@ def selection_bench(ctx, A, torch, dev, stream, flush, R, dR, steps, warmup):
             "cpu_alg2": {"threads_1_pairs_per_s": k1 / host_one, "threads_all_pairs_per_s": n / host_all,
                          "threads": os.cpu_count()},
             "verdict_mix": (np.bincount(v, minlength=3)[:3] / max(n, 1)).round(4).tolist()}
+
+
+def construction_bench(ctx, A, torch, dev, stream, flush, w, S, dS, host_v, steps, warmup):
+    """Construction of the R side (200k polygons of config 2) on the GPU
+    (april_build_sets_device, polygons already in device memory) against the
+    host builder on all host cores; parity through the filter: the
+    GPU-built R with the host-built S gives the same verdicts."""
+    g = A.global_grid(w.order)
+    d_xy = torch.from_numpy(np.ascontiguousarray(w.R.xy, dtype=np.int32)).to(dev)
+    d_off = torch.from_numpy(np.ascontiguousarray(w.R.off, dtype=np.int64)).to(dev)
+    dR, info = ctx.april_build_sets_device(d_xy, d_off, g, stream=stream)
+    work = torch.empty(int(info.work_bytes), dtype=torch.uint8, device=dev)
+    image = dR.buf
+
+    def run():
+        ctx.april_build_sets_device(d_xy, d_off, g, work=work, image=image, stream=stream)
+    t = _event_times(torch, stream, flush, run, steps, warmup)
+    n = len(w.pr)
+    d_r = torch.from_numpy(w.pr.view(np.int32)).to(dev)
+    d_s = torch.from_numpy(w.ps.view(np.int32)).to(dev)
+    out = torch.empty(n, dtype=torch.uint8, device=dev)
+    scratch = torch.empty(ctx.scratch_bytes(A.MODE_BATCHED, n), dtype=torch.uint8, device=dev)
+    dR2, _ = ctx.april_build_sets_device(d_xy, d_off, g, work=work, image=image, stream=stream)
+    ctx.april_filter_pairs(dR2, dS, d_r, d_s, n, out, A.MODE_BATCHED, scratch, stream)
+    ctx.april_sync_status(stream)
+    if not np.array_equal(out.cpu().numpy(), host_v):
+        raise SystemExit("GPU-built sets filter to other verdicts")
+    t0 = time.perf_counter()
+    A.april_build_sets(w.R.xy, w.R.off, g)
+    host_s = time.perf_counter() - t0
+    ms = statistics.mean(t)
+    return {"polygons": int(w.R.n), "ms_gpu": ms, "polygons_per_s_gpu": w.R.n / (ms * 1e-3),
+            "touched_cells": int(info.touched_cells), "work_bytes": int(info.work_bytes),
+            "image_bytes": int(info.image_bytes), "ms_host_all_cores": host_s * 1e3, "host_threads": os.cpu_count(),
+            "speedup": host_s * 1e3 / ms,
+            "timed": "april_build_sets_device (count, one size read-back, build), polygons resident on the GPU"}
 
 
 def variants_bench(ctx, A, torch, dev, stream, flush, w, R, S, dR, dS, steps, warmup):
@@ -571,6 +638,9 @@ def main():
     if rank == 0 and not args.no_variants and not w.partitions:
         line["variants"] = variants_bench(ctx, A, torch, dev, stream, flush, w, R, S, dR, dS, args.steps,
                                           args.warmup)
+    if rank == 0 and not args.no_construction and not w.partitions:
+        line["construction"] = construction_bench(ctx, A, torch, dev, stream, flush, w, S, dS, host_v, args.steps,
+                                                  args.warmup)
     if rank == 0 and not args.no_selection:
         same = args.config == 2 and not w.partitions
         line["selection"] = selection_bench(ctx, A, torch, dev, stream, flush, R if same else None,
