@@ -239,11 +239,14 @@ void april_ctx_destroy(april_ctx *ctx);
 /* Knobs of APRIL_MODE_BATCHED (a build-side addition; the paper's CPU
  * filter has none).  Defaults: {8192, 8, 16, 256, 0}. */
 typedef struct april_tune {
-    uint32_t cta_threshold;  /* pairs with |A(r)| + |A(s)| above this are joined by a whole CTA */
+    uint32_t cta_threshold;  /* pairs with |A(r)| + |A(s)| above this ("long pairs") are joined
+                                first, each by one warp or by a whole CTA (see cta_window) */
     uint32_t group_lanes;    /* lanes that share one pair below the threshold: 4, 8, 16 or 32 */
     uint32_t group_window;   /* first window of such a join, intervals per list: a power of two
                                 in [group_lanes, 8 * group_lanes]; later windows double */
-    uint32_t cta_window;     /* first window of a CTA join: 256..2048, power of 2 */
+    uint32_t cta_window;     /* first window of a long pair's join, a power of 2: 32..128 = the
+                                pair is joined by one warp (eight long pairs per CTA at once),
+                                256..2048 = by the whole CTA */
     uint32_t blocks_per_sm;  /* persistent grid: CTAs per SM (0 = as many as fit) */
     float ms;                /* output of april_autotune: best time of the sample (ms) */
 } april_tune;
@@ -255,8 +258,9 @@ april_status april_get_tune(const april_ctx *ctx, april_tune *tune);
  * workload) for a grid of candidate tunings, keeps the
  * fastest in the context, and returns it in *out (candidates: cta_threshold in
  * {2048, 4096, 8192, 16384, none} x (group_lanes, group_window) in
- * {(4,8), (4,16), (8,16), (8,32), (16,32), (16,64), (32,64)}).  Arguments as for
- * april_filter_pairs; synchronizes `stream`. */
+ * {(4,8), (4,16), (8,16), (8,32), (16,32), (16,64), (32,64)} x long pairs by a
+ * warp (cta_window 64) or by the CTA (the context's cta_window if >= 256, else
+ * 256)).  Arguments as for april_filter_pairs; synchronizes `stream`. */
 april_status april_autotune(april_ctx *ctx, const april_dev_sets *R, const april_dev_sets *S,
                             const uint32_t *d_r, const uint32_t *d_s, uint64_t n, uint8_t *d_verdict,
                             void *d_scratch, size_t scratch_bytes, void *stream, april_tune *out);

@@ -311,27 +311,57 @@ __device__ __forceinline__ bool join_lists(const DevSet &R, const DevSet &S, con
     return nX != 0 && nY != 0;
 }
 
-// The search of group_lower_bound for the G lanes of every group of a warp at
-// once (warp-collective; a group with lo == hi takes no part): on return lo
-// is the first k in [lo, hi) whose interval's last cell is at least `key`.
+// The start search of a fresh join for every group of a warp at once
+// (warp-collective; a group with need == false takes no part): X is searched
+// for its first interval whose last cell reaches Y's first start, and Y for
+// X's first start, both lists in the same rounds.  Each round every lane
+// probes P evenly spaced positions per list (fan-out G*P) and the group
+// counts the probes below the key (a prefix, the keys being sorted), which
+// leaves one gap of the spacing; the keys themselves are loaded with the
+// first round's probes, whose positions do not depend on them.  Only lists
+// longer than a first window (w0) are searched.
+constexpr uint32_t kSearchProbes = 1;
 template <uint32_t G>
-__device__ __forceinline__ void group_search(const uint2 *p, uint32_t key, uint32_t &lo, uint32_t &hi, uint32_t t,
-                                             uint32_t gbits) {
-    while (__any_sync(kFull, lo < hi)) {
-        bool below = false;
-        uint32_t step = 1;
-        if (lo < hi) {
-            step = (hi - lo + G - 1) / G;
-            const uint32_t q = lo + (t + 1) * step - 1;
-            below = q < hi && (__ldg(&p[q].y) - 1u) < key;
+__device__ __forceinline__ void dual_search(const uint2 *X, uint32_t nX, const uint2 *Y, uint32_t nY, bool need,
+                                            uint32_t w0, uint32_t t, uint32_t gbits, uint32_t &i0, uint32_t &j0) {
+    constexpr uint32_t P = kSearchProbes, F = G * P;
+    uint32_t loX = 0, hiX = (need && nX > w0) ? nX : 0;
+    uint32_t loY = 0, hiY = (need && nY > w0) ? nY : 0;
+    uint32_t kx = 0, ky = 0;  // Y's first start (X's key), X's first start (Y's key)
+    bool first = true;
+    while (__any_sync(kFull, loX < hiX || loY < hiY)) {
+        const bool ax = loX < hiX, ay = loY < hiY;
+        const uint32_t sX = ax ? (hiX - loX + F - 1) / F : 1, sY = ay ? (hiY - loY + F - 1) / F : 1;
+        uint32_t vX[P], vY[P];
+#pragma unroll
+        for (uint32_t q = 0; q < P; ++q) {
+            const uint32_t px = loX + (t * P + q + 1) * sX - 1, py = loY + (t * P + q + 1) * sY - 1;
+            vX[q] = (ax && px < hiX) ? __ldg(&X[px].y) - 1u : 0u;
+            vY[q] = (ay && py < hiY) ? __ldg(&Y[py].y) - 1u : 0u;
         }
-        const uint32_t c = __popc(__ballot_sync(kFull, below) & gbits);
-        if (lo < hi) {
-            const uint32_t probes = (hi - lo) / step;
-            if (c < probes) hi = lo + (c + 1) * step - 1;
-            lo += c * step;
+        if (first && need) {
+            kx = __ldg(&Y->x);
+            ky = __ldg(&X->x);
+        }
+        first = false;
+        uint32_t cX = 0, cY = 0;
+#pragma unroll
+        for (uint32_t q = 0; q < P; ++q) {
+            const uint32_t px = loX + (t * P + q + 1) * sX - 1, py = loY + (t * P + q + 1) * sY - 1;
+            cX += __popc(__ballot_sync(kFull, ax && px < hiX && vX[q] < kx) & gbits);
+            cY += __popc(__ballot_sync(kFull, ay && py < hiY && vY[q] < ky) & gbits);
+        }
+        if (ax) {
+            if (cX < (hiX - loX) / sX) hiX = loX + (cX + 1) * sX - 1;
+            loX += cX * sX;
+        }
+        if (ay) {
+            if (cY < (hiY - loY) / sY) hiY = loY + (cY + 1) * sY - 1;
+            loY += cY * sY;
         }
     }
+    if (need && nX > w0) i0 = loX;
+    if (need && nY > w0) j0 = loY;
 }
 
 template <uint32_t G>
@@ -411,21 +441,7 @@ __device__ __forceinline__ void group_engine(const DevSet &R, const DevSet &S, c
         // -------- a join that has just started skips, in each list longer
         // than a window, the intervals ending before the other list's first
         // start (they meet nothing; the merge would pass over them)
-        if (__any_sync(kFull, active && fresh)) {
-            const bool need = active && fresh;
-            uint32_t kx = 0, ky = 0;
-            if (need) {
-                kx = __ldg(&Y->x);
-                ky = __ldg(&X->x);
-            }
-            uint32_t lo = 0, hi = (need && nX > w0) ? nX : 0;
-            group_search<G>(X, kx, lo, hi, t, gbits);
-            if (need && nX > w0) i0 = lo;
-            lo = 0;
-            hi = (need && nY > w0) ? nY : 0;
-            group_search<G>(Y, ky, lo, hi, t, gbits);
-            if (need && nY > w0) j0 = lo;
-        }
+        if (__any_sync(kFull, active && fresh)) dual_search<G>(X, nX, Y, nY, active && fresh, w0, t, gbits, i0, j0);
         fresh = false;
         const bool ran_out = active && (i0 >= nX || j0 >= nY);  // the search passed a whole list
 
@@ -511,29 +527,51 @@ __global__ void APRIL_PERSISTENT_BOUNDS k_persistent(SetsT R, SetsT S,
                                                        uint32_t *counters, uint32_t w0_group, uint32_t w0_cta) {
     __shared__ __align__(16) uint2 sm[kSharedIv];
     __shared__ uint32_t s_item, s_slot;
-    // mbarriers: [0] the CTA phase, [1 + warp * 8 + group] the group engine
-    __shared__ uint64_t bars[1 + kWarpsPerBlock * 8];
-    init_barriers(bars, 1 + kWarpsPerBlock * 8);
+    // mbarriers: [0] the CTA phase, [1 + warp * 8 + group] the group engine,
+    // [1 + 8 * 8 + warp] long pairs joined by warps
+    __shared__ uint64_t bars[1 + kWarpsPerBlock * 9];
+    init_barriers(bars, 1 + kWarpsPerBlock * 9);
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const uint32_t nbig = *((volatile uint32_t *)&counters[C_BIG_COUNT]);
-    JoinSync cs{smem_addr(&bars[0]), 0u, false};
-    for (;;) {
-        if (tid == 0) s_item = atomicAdd(&counters[C_BIG_HEAD], 1u);
-        __syncthreads();
-        const uint32_t it = s_item;
-        __syncthreads();
-        if (it >= nbig) break;
-        const uint64_t k = big_list[it];
-        const typename SetsT::Desc dr = R.load(__ldg(pr + k)), ds = S.load(__ldg(ps + k));
-        const uint8_t v = cta_verdict(R, S, dr, ds, sm, sm + kCtaBuf, &s_slot, tid, w0_cta, cs);
-        if (tid == 0) out[k] = v;
-        if (cs.timeout) {  // a bounded wait ran out: report and stop this CTA
-            if (tid == 0) atomicOr(status, ST_TIMEOUT);
-            return;
-        }
-    }
-    __syncthreads();
     uint2 *wbuf = sm + warp * kWarpShare;
+    if (w0_cta < kBlock) {
+        // long pairs one per warp (first window w0_cta): the CTA's warps work
+        // on eight long pairs at once
+        JoinSync ws{smem_addr(&bars[1 + kWarpsPerBlock * 8 + warp]), 0u, false};
+        for (;;) {
+            uint32_t it = 0;
+            if (lane == 0) it = atomicAdd(&counters[C_BIG_HEAD], 1u);
+            it = __shfl_sync(kFull, it, 0);
+            if (it >= nbig) break;
+            const uint64_t k = big_list[it];
+            const typename SetsT::Desc dr = R.load(__ldg(pr + k)), ds = S.load(__ldg(ps + k));
+            const uint8_t v = warp_verdict(R, S, dr, ds, wbuf, wbuf + kWarpBuf, lane, w0_cta, ws);
+            if (lane == 0) out[k] = v;
+            if (ws.timeout) break;
+        }
+        const bool dead = ws.timeout;
+        if (dead && lane == 0) atomicOr(status, ST_TIMEOUT);
+        __syncthreads();
+        if (dead) return;  // a bounded wait ran out: this warp stops (after the CTA's only barrier)
+    } else {
+        JoinSync cs{smem_addr(&bars[0]), 0u, false};
+        for (;;) {
+            if (tid == 0) s_item = atomicAdd(&counters[C_BIG_HEAD], 1u);
+            __syncthreads();
+            const uint32_t it = s_item;
+            __syncthreads();
+            if (it >= nbig) break;
+            const uint64_t k = big_list[it];
+            const typename SetsT::Desc dr = R.load(__ldg(pr + k)), ds = S.load(__ldg(ps + k));
+            const uint8_t v = cta_verdict(R, S, dr, ds, sm, sm + kCtaBuf, &s_slot, tid, w0_cta, cs);
+            if (tid == 0) out[k] = v;
+            if (cs.timeout) {  // a bounded wait ran out: report and stop this CTA
+                if (tid == 0) atomicOr(status, ST_TIMEOUT);
+                return;
+            }
+        }
+        __syncthreads();
+    }
     if constexpr (G == 32 || SetsT::kPacked) {
         JoinSync js{smem_addr(&bars[1 + warp * 8]), 0u, false};
         const uint64_t nchunks = (n + 31) / 32;
@@ -592,7 +630,7 @@ __global__ void __launch_bounds__(kBlock) k_general(Plan P, DevSet Rd, DevSet Sd
                                                     const uint32_t *__restrict__ ps, uint64_t n,
                                                     uint8_t *__restrict__ out, uint32_t *status,
                                                     uint32_t cta_threshold, const uint32_t *__restrict__ big_list,
-                                                    uint32_t *counters) {
+                                                    uint32_t *counters, uint32_t long_window) {
     __shared__ __align__(16) uint2 sm[kSharedIv];
     __shared__ uint32_t s_item, s_slot;
     __shared__ uint64_t bars[1 + kWarpsPerBlock];
@@ -600,26 +638,45 @@ __global__ void __launch_bounds__(kBlock) k_general(Plan P, DevSet Rd, DevSet Sd
     const RawSets R{Rd}, S{Sd};
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const uint32_t nbig = *((volatile uint32_t *)&counters[C_BIG_COUNT]);
-    JoinSync cs{smem_addr(&bars[0]), 0u, false};
-    for (;;) {
-        if (tid == 0) s_item = atomicAdd(&counters[C_BIG_HEAD], 1u);
-        __syncthreads();
-        const uint32_t it = s_item;
-        __syncthreads();
-        if (it >= nbig) break;
-        const uint64_t k = big_list[it];
-        const uint4 dr = R.load(__ldg(pr + k)), ds = S.load(__ldg(ps + k));
-        const uint8_t v = plan_verdict<CtaScope, kBlock, kCtaWMax>(P, R, S, dr, ds, sm, sm + kCtaBuf, &s_slot, tid,
-                                                                    256u, cs);
-        if (tid == 0) out[k] = v;
-        if (cs.timeout) {
-            if (tid == 0) atomicOr(status, ST_TIMEOUT);
-            return;
-        }
-    }
-    __syncthreads();
     uint2 *xs = sm + warp * kWarpShare, *ys = xs + kWarpBuf;
     JoinSync js{smem_addr(&bars[1 + warp]), 0u, false};
+    if (long_window < kBlock) {  // long pairs one per warp
+        for (;;) {
+            uint32_t it = 0;
+            if (lane == 0) it = atomicAdd(&counters[C_BIG_HEAD], 1u);
+            it = __shfl_sync(kFull, it, 0);
+            if (it >= nbig) break;
+            const uint64_t k = big_list[it];
+            const uint4 dr = R.load(__ldg(pr + k)), ds = S.load(__ldg(ps + k));
+            const uint8_t v = plan_verdict<WarpScope, 32, kWarpWMax>(P, R, S, dr, ds, xs, ys, nullptr, lane,
+                                                                      long_window, js);
+            if (lane == 0) out[k] = v;
+            if (js.timeout) break;
+        }
+        const bool dead = js.timeout;
+        if (dead && lane == 0) atomicOr(status, ST_TIMEOUT);
+        __syncthreads();
+        if (dead) return;  // a bounded wait ran out: this warp stops (after the CTA's only barrier)
+    } else {
+        JoinSync cs{smem_addr(&bars[0]), 0u, false};
+        for (;;) {
+            if (tid == 0) s_item = atomicAdd(&counters[C_BIG_HEAD], 1u);
+            __syncthreads();
+            const uint32_t it = s_item;
+            __syncthreads();
+            if (it >= nbig) break;
+            const uint64_t k = big_list[it];
+            const uint4 dr = R.load(__ldg(pr + k)), ds = S.load(__ldg(ps + k));
+            const uint8_t v = plan_verdict<CtaScope, kBlock, kCtaWMax>(P, R, S, dr, ds, sm, sm + kCtaBuf, &s_slot,
+                                                                        tid, long_window, cs);
+            if (tid == 0) out[k] = v;
+            if (cs.timeout) {
+                if (tid == 0) atomicOr(status, ST_TIMEOUT);
+                return;
+            }
+        }
+        __syncthreads();
+    }
     const uint64_t nchunks = (n + 31) / 32;
     for (;;) {
         uint32_t c = 0;
@@ -753,8 +810,8 @@ static april_status check_tune(const april_tune &t) {
     const uint32_t gmax = G == 32 ? kWarpWMax : kGroupPer * G;
     if (t.group_window < G || t.group_window > gmax || (t.group_window & (t.group_window - 1)))
         return fail(APRIL_ERR_INVALID_ARG, "group_window must be a power of two in [group_lanes, 8*group_lanes]");
-    if (t.cta_window < kBlock || t.cta_window > kCtaWMax || (t.cta_window & (t.cta_window - 1)))
-        return fail(APRIL_ERR_INVALID_ARG, "cta_window must be a power of two in [256, 2048]");
+    if (t.cta_window < 32 || t.cta_window > kCtaWMax || (t.cta_window & (t.cta_window - 1)))
+        return fail(APRIL_ERR_INVALID_ARG, "cta_window must be a power of two in [32, 2048]");
     return APRIL_OK;
 }
 
@@ -1103,7 +1160,7 @@ extern "C" april_status april_filter_pairs_ex(april_ctx *ctx, const april_dev_se
     k_bin<<<grid_bin, 256, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, ctx->d_status, ctx->tune.cta_threshold, big_list,
                                     counters);
     k_general<<<grid_main, kBlock, 0, st>>>(P, dR.s, dS.s, d_r, d_s, n, d_verdict, ctx->d_status,
-                                            ctx->tune.cta_threshold, big_list, counters);
+                                            ctx->tune.cta_threshold, big_list, counters, ctx->tune.cta_window);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return APRIL_OK;
@@ -1128,12 +1185,17 @@ extern "C" april_status april_autotune(april_ctx *ctx, const april_dev_sets *R, 
     if (e == cudaSuccess) e = cudaEventCreate(&b);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
     april_status rc = APRIL_OK;
+    // long pairs joined by one warp (first window 64) or by the whole CTA
+    const uint32_t long_windows[] = {64u, saved.cta_window >= kBlock ? saved.cta_window : kBlock};
     for (uint32_t T : thresholds) {
-        for (const auto &gw : groups) {
+        for (const auto &gw : groups)
+        for (const uint32_t lw : long_windows) {
+            if (T == 0xffffffffu && lw != long_windows[0]) continue;  // no long pairs: one scope is enough
             april_tune t = saved;
             t.cta_threshold = T;
             t.group_lanes = gw[0];
             t.group_window = gw[1];
+            t.cta_window = lw;
             ctx->tune = t;
             float best_here = 1e30f;
             for (int rep = 0; rep < 3 && rc == APRIL_OK; ++rep) {

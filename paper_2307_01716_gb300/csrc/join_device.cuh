@@ -232,28 +232,6 @@ struct CtaScope {
     }
 };
 
-// First k in [0, n) whose interval's last cell, shifted right by sh, is at
-// least t (n if none): an NT-ary search by the group over the list in global
-// memory.  Each round the NT threads probe evenly spaced positions and count
-// the probes below t (a prefix, the keys being sorted), which leaves one gap
-// of the spacing to search; with NT = 32 a list of 10^4 intervals takes three
-// rounds.  Every thread of the group gets the same answer.
-template <class Scope, uint32_t NT>
-__device__ __forceinline__ uint32_t group_lower_bound(const uint2 *p, uint32_t n, uint32_t sh, uint32_t t,
-                                                      uint32_t tid) {
-    uint32_t lo = 0, hi = n;  // the answer lies in [lo, hi]
-    while (lo < hi) {
-        const uint32_t step = (hi - lo + NT - 1) / NT;
-        const uint32_t q = lo + (tid + 1) * step - 1;
-        const bool below = q < hi && ((__ldg(&p[q].y) - 1u) >> sh) < t;
-        const uint32_t c = Scope::count(below);
-        const uint32_t probes = (hi - lo) / step;  // probes that fell inside [lo, hi)
-        if (c < probes) hi = lo + (c + 1) * step - 1;
-        lo += c * step;
-    }
-    return lo;
-}
-
 // ----- TMA bulk copies and mbarriers (sm_90+ PTX; used on sm_103a) -----
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
@@ -355,11 +333,11 @@ struct RawList {
         return smem_addr(buf) + 8u * (uint32_t)(((uintptr_t)(p + i0) >> 3) & 1u);
     }
     __device__ __forceinline__ uint32_t first_start() const { return __ldg(&p->x); }
-    // First interval whose last cell (shifted right by sh) is at least t.
-    template <class Scope, uint32_t NT>
-    __device__ __forceinline__ uint32_t search(uint32_t sh, uint32_t t, uint32_t tid) const {
-        return group_lower_bound<Scope, NT>(p, n, sh, t, tid);
-    }
+    // Start search: the keys are the intervals' last cells; a count c of keys
+    // below the target makes interval c the first that can meet.
+    __device__ __forceinline__ uint32_t keys_n() const { return n; }
+    __device__ __forceinline__ uint32_t key(uint32_t q) const { return __ldg(&p[q].y) - 1u; }
+    __device__ __forceinline__ uint32_t start_of(uint32_t c) const { return c; }
 };
 
 struct PackedList {
@@ -415,26 +393,35 @@ struct PackedList {
     __device__ __forceinline__ uint32_t issue(uint2 *, uint32_t, uint32_t, uint32_t) const { return 0; }
     __device__ __forceinline__ uint32_t window(const uint2 *buf, uint32_t) const { return smem_addr(buf); }
     __device__ __forceinline__ uint32_t first_start() const { return __ldg(&blocks->x); }
-    // A start at or before the first interval whose last cell (shifted by sh)
-    // reaches t, at a block boundary: block b's anchor is the start of its
-    // interval 16b, so with c blocks anchored below t every interval before
-    // 16 (c - 1) ends below t as well.
-    template <class Scope, uint32_t NT>
-    __device__ __forceinline__ uint32_t search(uint32_t sh, uint32_t t, uint32_t tid) const {
-        const uint32_t nb = (2 * n + 31) / 32;
-        uint32_t lo = 0, hi = nb;  // count of blocks whose anchor lies below t
-        while (lo < hi) {
-            const uint32_t step = (hi - lo + NT - 1) / NT;
-            const uint32_t q = lo + (tid + 1) * step - 1;
-            const bool below = q < hi && (__ldg(&blocks[q].x) >> sh) < t;
-            const uint32_t c = Scope::count(below);
-            const uint32_t probes = (hi - lo) / step;
-            if (c < probes) hi = lo + (c + 1) * step - 1;
-            lo += c * step;
-        }
-        return lo ? 16u * (lo - 1) : 0u;
-    }
+    // Start search over the block anchors: block b's anchor is the start of
+    // its interval 16b, so with c blocks anchored below the target every
+    // interval before 16 (c - 1) ends below it as well; the search starts at
+    // that block boundary, at or before the first interval that can meet.
+    __device__ __forceinline__ uint32_t keys_n() const { return (2 * n + 31) / 32; }
+    __device__ __forceinline__ uint32_t key(uint32_t q) const { return __ldg(&blocks[q].x); }
+    __device__ __forceinline__ uint32_t start_of(uint32_t c) const { return c ? 16u * (c - 1) : 0u; }
 };
+
+// Count of a list's search keys (interval last cells, or block anchors for
+// compressed lists; sorted) that lie below t after a right shift by sh: an
+// NT-ary search by the group.  Each round the NT threads probe evenly spaced
+// keys and count those below t (a prefix, the keys being sorted), which
+// leaves one gap of the spacing; with NT = 32 a list of 10^4 intervals takes
+// three rounds.  Every thread of the group gets the same answer.
+template <class Scope, uint32_t NT, class ListT>
+__device__ __forceinline__ uint32_t start_search(const ListT &L, uint32_t sh, uint32_t t, uint32_t tid) {
+    uint32_t lo = 0, hi = L.keys_n();  // the answer lies in [lo, hi]
+    while (lo < hi) {
+        const uint32_t step = (hi - lo + NT - 1) / NT;
+        const uint32_t q = lo + (tid + 1) * step - 1;
+        const bool below = q < hi && (L.key(q) >> sh) < t;
+        const uint32_t c = Scope::count(below);
+        const uint32_t probes = (hi - lo) / step;  // probes that fell inside [lo, hi)
+        if (c < probes) hi = lo + (c + 1) * step - 1;
+        lo += c * step;
+    }
+    return lo;
+}
 
 // Any overlap between lists X and Y, by a group of NT threads (thread
 // index tid) with shared buffers xb, yb of WMAX + 2 intervals each (16-byte
@@ -461,13 +448,13 @@ __device__ __noinline__ bool tile_join(const ListT X, const ListT Y, uint2 *xb, 
     if (n && m && (n > w0 || m > w0)) {
         const uint32_t xs = X.first_start() >> sx, ys = Y.first_start() >> sy;
         if (PRED == kOverlap) {
-            if (n > w0) i0 = X.template search<Scope, NT>(sx, ys, tid);
+            if (n > w0) i0 = X.start_of(start_search<Scope, NT>(X, sx, ys, tid));
         } else {
             static_assert(PRED == kOverlap || ListT::kRandomAccess, "containment joins read raw lists");
             if constexpr (ListT::kRandomAccess)
                 if (((__ldg(&X.p->y) - 1u) >> sx) < ys) return true;  // X's first interval ends before Y starts
         }
-        if (m > w0) j0 = Y.template search<Scope, NT>(sy, xs, tid);
+        if (m > w0) j0 = Y.start_of(start_search<Scope, NT>(Y, sy, xs, tid));
     }
     while (i0 < n && j0 < m) {
         const uint32_t nx = min(w, n - i0), ny = min(w, m - j0);

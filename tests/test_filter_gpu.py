@@ -133,15 +133,19 @@ def test_full_size_config2_sampled(torch_cuda, ctx, full_config2, mode):
     assert np.array_equal(got, hv)
 
 
+@pytest.mark.parametrize("long_window", [32, 128, 256, 2048])
 @pytest.mark.parametrize("threshold", [0, 64, 0xFFFFFFFF])
 @pytest.mark.parametrize("group", [(4, 4), (4, 32), (8, 8), (8, 64), (16, 16), (16, 128), (32, 32), (32, 256)])
-def test_batched_tunings(torch_cuda, ctx, threshold, group):
-    """Every pair joined by a whole CTA (threshold 0), a mix, or none; every
-    group size with its smallest and largest first window."""
+def test_batched_tunings(torch_cuda, ctx, threshold, group, long_window):
+    """Every pair joined as a long pair (threshold 0), a mix, or none; long
+    pairs by one warp (first window 32 or 128) or by the whole CTA (256 or
+    2048); every group size with its smallest and largest first window."""
+    if threshold == 0xFFFFFFFF and long_window != 256:
+        pytest.skip("no long pairs: the long-pair scope is unused")
     w = _data.workload(3, 0.01)
     _, _, dR, dS = _device_sets(w)
     saved = ctx.get_tune()
-    t = A.april_tune(threshold, group[0], group[1], 256, 0, 0.0)
+    t = A.april_tune(threshold, group[0], group[1], long_window, 0, 0.0)
     ctx.set_tune(t)
     try:
         got = run_filter(torch_cuda, ctx, dR, dS, w.pr, w.ps, "batched")
@@ -174,7 +178,8 @@ def test_autotune_then_batched(torch_cuda, ctx):
 
 
 def test_tune_validation(ctx):
-    for bad in [(100, 6, 8, 256), (100, 8, 4, 256), (100, 8, 128, 256), (100, 8, 24, 256), (100, 32, 64, 4096)]:
+    for bad in [(100, 6, 8, 256), (100, 8, 4, 256), (100, 8, 128, 256), (100, 8, 24, 256), (100, 32, 64, 4096),
+                (100, 8, 32, 16), (100, 8, 32, 96)]:
         with pytest.raises(A.AprilError):
             ctx.set_tune(A.april_tune(*bad, 0, 0.0))
 

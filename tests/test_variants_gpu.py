@@ -61,12 +61,16 @@ def test_variants_equal_oracle(torch_cuda, ctx, cfg, scale):
             assert np.array_equal(got, _data.oracle_verdicts(cfg, scale))
 
 
+@pytest.mark.parametrize("long_window", [64, 256])
 @pytest.mark.parametrize("threshold", [0, 64, 0xFFFFFFFF])
-def test_variants_both_paths(torch_cuda, ctx, threshold):
-    """Threshold 0 sends every pair to whole-CTA joins, the maximum none."""
+def test_variants_both_paths(torch_cuda, ctx, threshold, long_window):
+    """Threshold 0 makes every pair a long pair, the maximum none; long pairs
+    are joined by one warp (first window 64) or by the whole CTA (256)."""
+    if threshold == 0xFFFFFFFF and long_window != 256:
+        pytest.skip("no long pairs: the long-pair scope is unused")
     w = _data.workload(2, 0.01)
     saved = ctx.get_tune()
-    ctx.set_tune(A.april_tune(threshold, saved.group_lanes, saved.group_window, saved.cta_window, 0, 0.0))
+    ctx.set_tune(A.april_tune(threshold, saved.group_lanes, saved.group_window, long_window, 0, 0.0))
     try:
         for (o_r, o_s), pred in _variants(w.order):
             _, _, dR, dS = _sets(w, o_r, o_s)
