@@ -351,12 +351,14 @@ __device__ __forceinline__ void dual_search(const uint2 *X, uint32_t nX, const u
             cX += __popc(__ballot_sync(kFull, ax && px < hiX && vX[q] < kx) & gbits);
             cY += __popc(__ballot_sync(kFull, ay && py < hiY && vY[q] < ky) & gbits);
         }
+        // c below-probes leave the gap after the c-th probe, if that probe
+        // exists (c < probes in [lo, hi)), else the tail after the last one
         if (ax) {
-            if (cX < (hiX - loX) / sX) hiX = loX + (cX + 1) * sX - 1;
+            if (loX + (cX + 1) * sX <= hiX) hiX = loX + (cX + 1) * sX - 1;
             loX += cX * sX;
         }
         if (ay) {
-            if (cY < (hiY - loY) / sY) hiY = loY + (cY + 1) * sY - 1;
+            if (loY + (cY + 1) * sY <= hiY) hiY = loY + (cY + 1) * sY - 1;
             loY += cY * sY;
         }
     }
@@ -475,8 +477,8 @@ __device__ __forceinline__ void group_engine(const DevSet &R, const DevSet &S, c
         uint32_t state = 0xffffffffu, D = 0, owner = 0;
         if (active && !ran_out) {
             D = min(w, nx + ny);
-            const uint32_t per = w / G;
-            owner = (D - 1) / per;
+            const uint32_t per = w / G;  // a power of two
+            owner = (D - 1) >> (__ffs(per) - 1);
             found = window_walk<C::WMAX / G>(xa, nx, ya, ny, w, D, per, t * per, state);
         }
         const uint32_t fmask = __ballot_sync(kFull, found);  // every read of the windows is done here

@@ -416,8 +416,9 @@ __device__ __forceinline__ uint32_t start_search(const ListT &L, uint32_t sh, ui
         const uint32_t q = lo + (tid + 1) * step - 1;
         const bool below = q < hi && (L.key(q) >> sh) < t;
         const uint32_t c = Scope::count(below);
-        const uint32_t probes = (hi - lo) / step;  // probes that fell inside [lo, hi)
-        if (c < probes) hi = lo + (c + 1) * step - 1;
+        // c below-probes leave the gap after the c-th probe, if that probe
+        // exists (c < probes in [lo, hi)), else the tail after the last one
+        if (lo + (c + 1) * step <= hi) hi = lo + (c + 1) * step - 1;
         lo += c * step;
     }
     return lo;
@@ -492,8 +493,8 @@ __device__ __noinline__ bool tile_join(const ListT X, const ListT Y, uint2 *xb, 
         // D diagonals of the merge path lie in this window; thread tid walks
         // [d0, d0 + per).  No list can run out inside a full window.
         const uint32_t D = min(w, nx + ny);
-        const uint32_t per = w / NT;
-        const uint32_t owner = (D - 1) / per;  // walks the window's last diagonal
+        const uint32_t per = w / NT;                          // a power of two
+        const uint32_t owner = (D - 1) >> (__ffs(per) - 1);  // walks the window's last diagonal
         uint32_t state;
         const bool found = window_walk<WMAX / NT, PRED>(xa, nx, ya, ny, w, D, per, tid * per, state);
         if (Scope::vote(found, state, owner, slot)) return true;
