@@ -370,7 +370,7 @@ template <uint32_t G>
 __device__ __forceinline__ void group_engine(const DevSet &R, const DevSet &S, const uint32_t *__restrict__ pr,
                                              const uint32_t *__restrict__ ps, uint64_t n, uint8_t *__restrict__ out,
                                              uint32_t *status, uint32_t *counters, uint32_t cta_threshold, uint2 *wbuf,
-                                             uint32_t bars, uint32_t lane, uint32_t w0) {
+                                             uint4 *chunk_desc, uint32_t bars, uint32_t lane, uint32_t w0) {
     using C = GroupCfg<G>;
     const uint32_t g = lane / G, t = lane % G, glead = g * G;
     const uint32_t gbits = (G == 32 ? kFull : ((1u << G) - 1u)) << glead;
@@ -378,14 +378,15 @@ __device__ __forceinline__ void group_engine(const DevSet &R, const DevSet &S, c
     const uint32_t bar = bars + 8u * g;  // this group's mbarrier
     uint32_t phase = 0;
     const uint64_t nchunks = (n + 31) / 32;
-    // the warp's chunk: lane l holds pair base + l
-    uint64_t qk = 0;
-    uint4 qdr = make_uint4(0, 0, 0, 0), qds = make_uint4(0, 0, 0, 0);
+    // the warp's chunk of 32 pairs from pair `base`: pair base + l has its two
+    // descriptors in chunk_desc[l] and chunk_desc[32 + l]; bit l of `avail`
+    // says it is still to be handed out
+    uint32_t base = 0;
     uint32_t avail = 0;
     bool exhausted = false;
     // this group's pair and join
     bool active = false;
-    uint64_t k = 0;
+    uint32_t k = 0;
     uint4 dr = make_uint4(0, 0, 0, 0), ds = make_uint4(0, 0, 0, 0);
     uint32_t stage = 0, nX = 0, nY = 0, i0 = 0, j0 = 0, w = w0;
     bool fresh = false;  // the join has just started: its start has not been searched yet
@@ -403,30 +404,31 @@ __device__ __forceinline__ void group_engine(const DevSet &R, const DevSet &S, c
                     exhausted = true;
                     break;
                 }
-                qk = (uint64_t)c * 32 + lane;
+                base = c * 32;  // n < 2^32 pairs
+                const uint32_t qk = base + lane;
                 bool take = false;
+                __syncwarp();  // every group has read its descriptors from the previous chunk
                 if (qk < n) {
                     const uint32_t r = __ldg(pr + qk), s2 = __ldg(ps + qk);
                     if (r < R.n && s2 < S.n) {  // out-of-range ids were reported by the binning kernel
-                        qdr = __ldg(R.desc + r);
-                        qds = __ldg(S.desc + s2);
+                        const uint4 qdr = __ldg(R.desc + r), qds = __ldg(S.desc + s2);
+                        chunk_desc[lane] = qdr;
+                        chunk_desc[32 + lane] = qds;
                         take = (uint64_t)qdr.y + qds.y <= (uint64_t)cta_threshold;
                     }
                 }
                 avail = __ballot_sync(kFull, take);
+                __syncwarp();
                 continue;
             }
             const uint32_t cnt = min((uint32_t)__popc(needg), (uint32_t)__popc(avail));
             const uint32_t grank = __popc(needg & ((1u << glead) - 1u));
             const bool gets = ((needg >> glead) & 1u) && grank < cnt;
-            const uint32_t src = gets ? __fns(avail, 0, (int)grank + 1) : lane;
-            const uint32_t klo = __shfl_sync(kFull, (uint32_t)qk, src);
-            const uint32_t khi = __shfl_sync(kFull, (uint32_t)(qk >> 32), src);
-            const uint4 a = shfl4(qdr, src), b = shfl4(qds, src);
             if (gets) {
-                k = ((uint64_t)khi << 32) | klo;
-                dr = a;
-                ds = b;
+                const uint32_t src = __fns(avail, 0, (int)grank + 1);
+                k = base + src;
+                dr = chunk_desc[src];
+                ds = chunk_desc[32 + src];
                 stage = 0;
                 i0 = j0 = 0;
                 w = w0;
@@ -532,6 +534,7 @@ __global__ void APRIL_PERSISTENT_BOUNDS k_persistent(SetsT R, SetsT S,
     // mbarriers: [0] the CTA phase, [1 + warp * 8 + group] the group engine,
     // [1 + 8 * 8 + warp] long pairs joined by warps
     __shared__ uint64_t bars[1 + kWarpsPerBlock * 9];
+    __shared__ uint4 s_chunk[kWarpsPerBlock][64];  // group engine: each warp's chunk descriptors
     init_barriers(bars, 1 + kWarpsPerBlock * 9);
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const uint32_t nbig = *((volatile uint32_t *)&counters[C_BIG_COUNT]);
@@ -587,7 +590,8 @@ __global__ void APRIL_PERSISTENT_BOUNDS k_persistent(SetsT R, SetsT S,
                 return;
         }
     } else {
-        group_engine<G>(R.s, S.s, pr, ps, n, out, status, counters, cta_threshold, wbuf, smem_addr(&bars[1 + warp * 8]),
+        group_engine<G>(R.s, S.s, pr, ps, n, out, status, counters, cta_threshold, wbuf, s_chunk[warp],
+                        smem_addr(&bars[1 + warp * 8]),
                         lane, w0_group);
     }
 }
