@@ -109,6 +109,18 @@ typedef struct april_sets april_sets;
 april_status april_build_sets(const int32_t *xy, const uint64_t *vert_off, uint32_t n_polys,
                               const april_grid *grid, uint32_t n_threads, april_sets **out);
 
+/* Quantizes polygons given in data-space coordinates (doubles over the unit
+ * square [0,1]^2, the paper's map extent) to the integer lattice of 2^24
+ * units per side that april_build_sets takes: each coordinate becomes
+ * nearest-integer(x * 2^24) with ties to even (the product is exact), clamped
+ * to [0, 2^24]; consecutive equal vertices, and a closing vertex equal to the
+ * first, are dropped.  out_xy (int32 pairs) needs room for every input
+ * vertex, out_off for n_polys + 1 offsets.  A non-finite coordinate:
+ * APRIL_ERR_INVALID_ARG.  A polygon may come out with fewer than 3
+ * vertices, which april_build_sets then rejects. */
+april_status april_quantize_polygons(const double *xy, const uint64_t *vert_off, uint32_t n_polys, int32_t *out_xy,
+                                     uint64_t *out_off);
+
 void april_sets_destroy(april_sets *sets);
 
 /* Sets from interval lists computed elsewhere (another construction, another

@@ -120,6 +120,7 @@ SIGNATURES = {
                                     _u64, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
     "april_host_filter_ex": (_st, [_vp, _vp, _vp, _vp, _u64, ctypes.c_int, _u32, _vp, _vp]),
     "april_sets_lengths": (_st, [_vp, _vp, _vp]),
+    "april_quantize_polygons": (_st, [_vp, _vp, _u32, _vp, _vp]),
     "april_build_sets_device": (_st, [_vp, _vp, _vp, _u32, ctypes.POINTER(april_grid), _vp, ctypes.c_size_t, _vp,
                                       ctypes.c_size_t, ctypes.POINTER(april_dev_sets),
                                       ctypes.POINTER(april_device_build_info), _vp]),
@@ -279,6 +280,17 @@ class Sets:
         if n.value == 0:
             return np.zeros((0, 2), dtype=np.uint32)
         return np.ctypeslib.as_array(p, shape=(n.value * 2,)).reshape(-1, 2).copy()
+
+
+def april_quantize_polygons(xy, vert_off):
+    """Data-space polygons (float64 (V, 2) in [0,1]^2, int offsets) to lattice
+    polygons: (int32 (V', 2), uint64 offsets)."""
+    xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)
+    off = np.ascontiguousarray(vert_off, dtype=np.uint64)
+    out = np.zeros_like(xy, dtype=np.int32)
+    out_off = np.zeros(len(off), dtype=np.uint64)
+    check(load().april_quantize_polygons(_ptr(xy), _ptr(off), len(off) - 1, _ptr(out), _ptr(out_off)))
+    return out[:int(out_off[-1])], out_off
 
 
 def april_sets_from_lists(order: int, a_lists, f_lists, mbr=None) -> Sets:

@@ -25,6 +25,8 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cfenv>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -422,6 +424,41 @@ extern "C" april_status april_sets_from_lists(uint32_t n, uint32_t order, const 
     } catch (const std::bad_alloc &) {
         return fail(APRIL_ERR_NO_MEMORY, "host allocation failed while importing lists");
     }
+}
+
+extern "C" april_status april_quantize_polygons(const double *xy, const uint64_t *vert_off, uint32_t n_polys,
+                                               int32_t *out_xy, uint64_t *out_off) {
+    if (n_polys && (!xy || !vert_off || !out_xy || !out_off)) return fail(APRIL_ERR_INVALID_ARG, "NULL argument");
+    if (!n_polys) {
+        if (out_off) out_off[0] = 0;
+        return APRIL_OK;
+    }
+    if (std::fegetround() != FE_TONEAREST) return fail(APRIL_ERR_INVALID_ARG, "the FPU must round to nearest");
+    const double scale = (double)(1 << 24);
+    uint64_t o = 0;
+    out_off[0] = 0;
+    for (uint32_t p = 0; p < n_polys; ++p) {
+        if (vert_off[p + 1] < vert_off[p]) return fail(APRIL_ERR_INVALID_ARG, "vert_off is not monotone");
+        const uint64_t first = o;
+        for (uint64_t k = vert_off[p]; k < vert_off[p + 1]; ++k) {
+            int32_t q[2];
+            for (int c = 0; c < 2; ++c) {
+                const double v = xy[2 * k + c];
+                if (!std::isfinite(v)) return fail(APRIL_ERR_INVALID_ARG, "non-finite coordinate");
+                // x * 2^24 is exact; nearbyint rounds half to even in the default mode
+                const double r = std::nearbyint(std::min(std::max(v * scale, 0.0), scale));
+                q[c] = (int32_t)r;
+            }
+            if (o > first && out_xy[2 * (o - 1)] == q[0] && out_xy[2 * (o - 1) + 1] == q[1]) continue;
+            out_xy[2 * o] = q[0];
+            out_xy[2 * o + 1] = q[1];
+            ++o;
+        }
+        while (o - first > 1 && out_xy[2 * (o - 1)] == out_xy[2 * first] && out_xy[2 * (o - 1) + 1] == out_xy[2 * first + 1])
+            --o;  // a closing vertex equal to the first
+        out_off[p + 1] = o;
+    }
+    return APRIL_OK;
 }
 
 extern "C" void april_sets_destroy(april_sets *sets) { delete sets; }

@@ -125,3 +125,31 @@ def test_searched_host_filter(cfg, scale):
     probes = 3 * (bw(np.maximum(a_r, f_r)[w.pr]) + bw(np.maximum(a_s, f_s)[w.ps]))
     assert np.all(c1.astype(np.int64) <= c0.astype(np.int64) + probes)
     assert c1.sum() < c0.sum()
+
+
+def test_quantize_polygons():
+    """Reading C3: x -> nearest integer of x * 2^24 (ties to even), clamped to
+    [0, 2^24], consecutive and closing duplicates dropped; checked against
+    numpy's rint (ties to even) on random and hand-made inputs."""
+    rng = np.random.default_rng(4)
+    polys = [rng.random((int(k), 2)) * 1.2 - 0.1 for k in rng.integers(3, 40, 50)]
+    half = (np.array([[0.5, 1.5], [2.5, 3.5], [4.5, 4.5], [4.5, 4.5], [0.5, 1.5]]) / (1 << 24))
+    polys.append(half)  # ties, a duplicate and a closing copy of the first vertex
+    off = np.zeros(len(polys) + 1, dtype=np.int64)
+    off[1:] = np.cumsum([len(p) for p in polys])
+    q, qoff = A.april_quantize_polygons(np.concatenate(polys), off)
+    for i, p in enumerate(polys):
+        want = np.clip(np.rint(p * (1 << 24)), 0, 1 << 24).astype(np.int64)
+        keep = [0] + [k for k in range(1, len(want)) if not np.array_equal(want[k], want[k - 1])]
+        want = want[keep]
+        while len(want) > 1 and np.array_equal(want[-1], want[0]):
+            want = want[:-1]
+        assert np.array_equal(q[qoff[i]:qoff[i + 1]], want), i
+    assert q[qoff[-2]:qoff[-1]].tolist() == [[0, 2], [2, 4], [4, 4]]
+    with pytest.raises(A.AprilError):
+        A.april_quantize_polygons(np.array([[0.1, np.nan], [0.2, 0.2], [0.3, 0.1]]), [0, 3])
+    # quantized polygons build
+    ok = np.array([[0.1, 0.1], [0.2, 0.1], [0.15, 0.2]])
+    qq, qo = A.april_quantize_polygons(ok, [0, 3])
+    S = A.april_build_sets(qq, qo.astype(np.int64), A.global_grid(10))
+    assert S.list(0, 0).shape[0] > 0
