@@ -571,7 +571,6 @@ __global__ void __launch_bounds__(kBB) k_bconstruct(const int2 *__restrict__ xy,
         __syncthreads();
         if (p >= n) break;
         const PolyMeta M = meta[p];
-        const uint64_t b = off[p], nv = off[p + 1] - b;
         const uint32_t T = M.T;
         const unsigned long long *sorted = sorted_all + M.key_off;
         unsigned long long *U = other_all + M.key_off;

@@ -56,7 +56,10 @@ constexpr uint32_t kCtaBuf = kCtaWMax + 2;
 #ifdef APRIL_MIN_BLOCKS
 #define APRIL_PERSISTENT_BOUNDS __launch_bounds__(256, APRIL_MIN_BLOCKS)
 #else
-#define APRIL_PERSISTENT_BOUNDS __launch_bounds__(256)
+// the lane-group instances over raw lists run five CTAs per SM (at most 51
+// registers a thread: their warps wait on memory, more of them hide more);
+// the others leave the register count to the compiler
+#define APRIL_PERSISTENT_BOUNDS __launch_bounds__(256, (G < 32 && !SetsT::kPacked) ? 5 : 0)
 #endif
 #ifndef APRIL_GROUP_PER
 #define APRIL_GROUP_PER 8
