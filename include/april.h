@@ -249,7 +249,7 @@ void april_ctx_destroy(april_ctx *ctx);
 /* ------------------------------------------------------------------ tuning */
 
 /* Knobs of APRIL_MODE_BATCHED (a build-side addition; the paper's CPU
- * filter has none).  Defaults: {8192, 8, 16, 256, 0}. */
+ * filter has none).  Defaults: {2048, 4, 16, 64, 0}. */
 typedef struct april_tune {
     uint32_t cta_threshold;  /* pairs with |A(r)| + |A(s)| above this ("long pairs") are joined
                                 first, each by one warp or by a whole CTA (see cta_window) */

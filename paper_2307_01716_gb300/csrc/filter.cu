@@ -804,10 +804,10 @@ static april_status cuda_fail(cudaError_t e, const char *what) {
 
 static april_tune default_tune() {
     april_tune t{};
-    t.cta_threshold = 8192;
-    t.group_lanes = 8;
+    t.cta_threshold = 2048;  // the shape the autotuner picks on the paper-scale and skewed workloads
+    t.group_lanes = 4;
     t.group_window = 16;
-    t.cta_window = 256;
+    t.cta_window = 64;       // long pairs one per warp
     t.blocks_per_sm = 0;
     t.ms = 0.f;
     return t;
@@ -1325,6 +1325,18 @@ NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
 
 }  // namespace
 
+// The persistent kernel instance for the default tuning's lane groups.
+using PersistentRaw = void (*)(RawSets, RawSets, const uint32_t *, const uint32_t *, uint64_t, uint8_t *,
+                               uint32_t *, uint32_t, const uint32_t *, uint32_t *, uint32_t, uint32_t);
+static PersistentRaw noalloc_kernel(uint32_t group_lanes) {
+    switch (group_lanes) {
+        case 4: return k_persistent<4, RawSets>;
+        case 8: return k_persistent<8, RawSets>;
+        case 16: return k_persistent<16, RawSets>;
+        default: return k_persistent<32, RawSets>;
+    }
+}
+
 extern "C" april_status april_filter_pairs_noalloc(const april_dev_sets *R, const april_dev_sets *S,
                                                    const uint32_t *d_r, const uint32_t *d_s, uint64_t n,
                                                    uint8_t *d_verdict, void *stream) {
@@ -1354,7 +1366,7 @@ extern "C" april_status april_filter_pairs_noalloc(const april_dev_sets *R, cons
             int sms = 0, bps = 0;
             e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             if (e == cudaSuccess)
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_persistent<8, RawSets>, kBlock, 0);
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, noalloc_kernel(t.group_lanes), kBlock, 0);
             if (e != cudaSuccess) return cuda_fail(e, "april_filter_pairs_noalloc set-up");
             slot.scratch = ptr;
             slot.num_sms = sms;
@@ -1374,8 +1386,9 @@ extern "C" april_status april_filter_pairs_noalloc(const april_dev_sets *R, cons
     const unsigned grid_bin = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)nd.num_sms * 8);
     const unsigned grid_main = (unsigned)std::max(1, nd.num_sms * nd.blocks_per_sm);
     k_bin<<<grid_bin, 256, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, status, t.cta_threshold, big_list, counters);
-    k_persistent<8, RawSets><<<grid_main, kBlock, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, status, t.cta_threshold,
-                                                           big_list, counters, t.group_window, t.cta_window);
+    noalloc_kernel(t.group_lanes)<<<grid_main, kBlock, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, status,
+                                                                t.cta_threshold, big_list, counters, t.group_window,
+                                                                t.cta_window);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "april_filter_pairs_noalloc launch");
     return APRIL_OK;
