@@ -304,16 +304,16 @@ static_assert(GroupCfg<16>::NG * 2 * GroupCfg<16>::BUF <= kWarpShare, "group buf
 static_assert(2 * kWarpBuf <= kWarpShare, "warp buffers fit in a warp's share");
 
 // Lists of join `stage` of a pair: 0 = A(r) x A(s), 1 = A(r) x F(s), 2 = F(r) x A(s).
-__device__ __forceinline__ bool join_lists(const DevSet &R, const DevSet &S, const uint4 &dr, const uint4 &ds,
-                                           uint32_t stage, const uint2 *&X, uint32_t &nX, const uint2 *&Y,
-                                           uint32_t &nY) {
-    X = R.iv + (stage == 2 ? dr.z : dr.x);
-    nX = stage == 2 ? dr.w : dr.y;
-    Y = S.iv + (stage == 1 ? ds.z : ds.x);
-    nY = stage == 1 ? ds.w : ds.y;
-    return nX != 0 && nY != 0;
+template <class SetsT, class ListT>
+__device__ __forceinline__ bool join_lists(const SetsT &R, const SetsT &S, const uint4 &dr, const uint4 &ds,
+                                           uint32_t stage, ListT &X, ListT &Y) {
+    X = R.list(dr, stage == 2);
+    Y = S.list(ds, stage == 1);
+    return X.n != 0 && Y.n != 0;
 }
 
+// (The keys are the lists' search keys: interval last cells, or block
+// anchors for compressed lists, whose start is then the block boundary.)
 // The start search of a fresh join for every group of a warp at once
 // (warp-collective; a group with need == false takes no part): X is searched
 // for its first interval whose last cell reaches Y's first start, and Y for
@@ -324,12 +324,13 @@ __device__ __forceinline__ bool join_lists(const DevSet &R, const DevSet &S, con
 // first round's probes, whose positions do not depend on them.  Only lists
 // longer than a first window (w0) are searched.
 constexpr uint32_t kSearchProbes = 1;
-template <uint32_t G>
-__device__ __forceinline__ void dual_search(const uint2 *X, uint32_t nX, const uint2 *Y, uint32_t nY, bool need,
-                                            uint32_t w0, uint32_t t, uint32_t gbits, uint32_t &i0, uint32_t &j0) {
+template <uint32_t G, class ListT>
+__device__ __forceinline__ void dual_search(const ListT &X, const ListT &Y, bool need, uint32_t w0, uint32_t t,
+                                            uint32_t gbits, uint32_t &i0, uint32_t &j0) {
     constexpr uint32_t P = kSearchProbes, F = G * P;
-    uint32_t loX = 0, hiX = (need && nX > w0) ? nX : 0;
-    uint32_t loY = 0, hiY = (need && nY > w0) ? nY : 0;
+    const uint32_t nX = X.n, nY = Y.n;
+    uint32_t loX = 0, hiX = (need && nX > w0) ? X.keys_n() : 0;
+    uint32_t loY = 0, hiY = (need && nY > w0) ? Y.keys_n() : 0;
     uint32_t kx = 0, ky = 0;  // Y's first start (X's key), X's first start (Y's key)
     bool first = true;
     while (__any_sync(kFull, loX < hiX || loY < hiY)) {
@@ -339,12 +340,12 @@ __device__ __forceinline__ void dual_search(const uint2 *X, uint32_t nX, const u
 #pragma unroll
         for (uint32_t q = 0; q < P; ++q) {
             const uint32_t px = loX + (t * P + q + 1) * sX - 1, py = loY + (t * P + q + 1) * sY - 1;
-            vX[q] = (ax && px < hiX) ? __ldg(&X[px].y) - 1u : 0u;
-            vY[q] = (ay && py < hiY) ? __ldg(&Y[py].y) - 1u : 0u;
+            vX[q] = (ax && px < hiX) ? X.key(px) : 0u;
+            vY[q] = (ay && py < hiY) ? Y.key(py) : 0u;
         }
         if (first && need) {
-            kx = __ldg(&Y->x);
-            ky = __ldg(&X->x);
+            kx = Y.first_start();
+            ky = X.first_start();
         }
         first = false;
         uint32_t cX = 0, cY = 0;
@@ -365,12 +366,12 @@ __device__ __forceinline__ void dual_search(const uint2 *X, uint32_t nX, const u
             loY += cY * sY;
         }
     }
-    if (need && nX > w0) i0 = loX;
-    if (need && nY > w0) j0 = loY;
+    if (need && nX > w0) i0 = X.start_of(loX);
+    if (need && nY > w0) j0 = Y.start_of(loY);
 }
 
-template <uint32_t G>
-__device__ __forceinline__ void group_engine(const DevSet &R, const DevSet &S, const uint32_t *__restrict__ pr,
+template <uint32_t G, class SetsT>
+__device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, const uint32_t *__restrict__ pr,
                                              const uint32_t *__restrict__ ps, uint64_t n, uint8_t *__restrict__ out,
                                              uint32_t *status, uint32_t *counters, uint32_t cta_threshold, uint2 *wbuf,
                                              uint4 *chunk_desc, uint32_t bars, uint32_t lane, uint32_t w0) {
@@ -391,9 +392,10 @@ __device__ __forceinline__ void group_engine(const DevSet &R, const DevSet &S, c
     bool active = false;
     uint32_t k = 0;
     uint4 dr = make_uint4(0, 0, 0, 0), ds = make_uint4(0, 0, 0, 0);
-    uint32_t stage = 0, nX = 0, nY = 0, i0 = 0, j0 = 0, w = w0;
+    uint32_t stage = 0, i0 = 0, j0 = 0, w = w0;
     bool fresh = false;  // the join has just started: its start has not been searched yet
-    const uint2 *X = nullptr, *Y = nullptr;
+    using ListT = decltype(R.list(dr, false));
+    ListT X = R.list(dr, false), Y = S.list(ds, false);
 
     for (;;) {
         // -------- hand pairs to idle groups
@@ -413,8 +415,8 @@ __device__ __forceinline__ void group_engine(const DevSet &R, const DevSet &S, c
                 __syncwarp();  // every group has read its descriptors from the previous chunk
                 if (qk < n) {
                     const uint32_t r = __ldg(pr + qk), s2 = __ldg(ps + qk);
-                    if (r < R.n && s2 < S.n) {  // out-of-range ids were reported by the binning kernel
-                        const uint4 qdr = __ldg(R.desc + r), qds = __ldg(S.desc + s2);
+                    if (r < R.n() && s2 < S.n()) {  // out-of-range ids were reported by the binning kernel
+                        const uint4 qdr = R.load(r), qds = S.load(s2);
                         chunk_desc[lane] = qdr;
                         chunk_desc[32 + lane] = qds;
                         take = (uint64_t)qdr.y + qds.y <= (uint64_t)cta_threshold;
@@ -435,7 +437,7 @@ __device__ __forceinline__ void group_engine(const DevSet &R, const DevSet &S, c
                 stage = 0;
                 i0 = j0 = 0;
                 w = w0;
-                active = join_lists(R, S, dr, ds, 0, X, nX, Y, nY);
+                active = join_lists(R, S, dr, ds, 0, X, Y);
                 fresh = true;
                 if (!active && t == 0) out[k] = APRIL_TRUE_NEGATIVE;  // an empty A-list meets nothing
             }
@@ -448,32 +450,40 @@ __device__ __forceinline__ void group_engine(const DevSet &R, const DevSet &S, c
         // -------- a join that has just started skips, in each list longer
         // than a window, the intervals ending before the other list's first
         // start (they meet nothing; the merge would pass over them)
-        if (__any_sync(kFull, active && fresh)) dual_search<G>(X, nX, Y, nY, active && fresh, w0, t, gbits, i0, j0);
+        if (__any_sync(kFull, active && fresh)) dual_search<G>(X, Y, active && fresh, w0, t, gbits, i0, j0);
         fresh = false;
+        const uint32_t nX = X.n, nY = Y.n;
         const bool ran_out = active && (i0 >= nX || j0 >= nY);  // the search passed a whole list
 
-        // -------- one window of every active group's join
-        // each active group's window arrives by two bulk copies on its mbarrier
+        // -------- one window of every active group's join: raw lists arrive
+        // by two bulk copies on the group's mbarrier, compressed lists are
+        // decoded by the group's lanes (one block each)
         uint32_t nx = 0, ny = 0, xa = 0, ya = 0;
         bool ok = true;
         if (active && !ran_out) {
             nx = min(w, nX - i0);
             ny = min(w, nY - j0);
-            if (t == 0) {
-                fence_proxy_async();
-                const uint2 *a;
-                uint32_t bx, by, ox, oy;
-                bulk_span(X + i0, nx, a, bx, ox);
-                bulk_span(Y + j0, ny, a, by, oy);
-                mbar_arrive_expect_tx(bar, bx + by);
-                bulk_load(smem_addr(xb), X + i0 - ox, bx, bar);
-                bulk_load(smem_addr(yb), Y + j0 - oy, by, bar);
+            if constexpr (ListT::kBulk) {
+                if (t == 0) {
+                    fence_proxy_async();
+                    const uint2 *a;
+                    uint32_t bx, by, ox, oy;
+                    bulk_span(X.p + i0, nx, a, bx, ox);
+                    bulk_span(Y.p + j0, ny, a, by, oy);
+                    mbar_arrive_expect_tx(bar, bx + by);
+                    bulk_load(smem_addr(xb), X.p + i0 - ox, bx, bar);
+                    bulk_load(smem_addr(yb), Y.p + j0 - oy, by, bar);
+                }
+                ok = mbar_wait(bar, phase);
+                phase ^= 1u;
+            } else {
+                X.template stage<G>(xb, i0, nx, t);
+                Y.template stage<G>(yb, j0, ny, t);
             }
-            ok = mbar_wait(bar, phase);
-            phase ^= 1u;
-            xa = smem_addr(xb) + 8u * (uint32_t)(((uintptr_t)(X + i0) >> 3) & 1u);
-            ya = smem_addr(yb) + 8u * (uint32_t)(((uintptr_t)(Y + j0) >> 3) & 1u);
+            xa = X.window(xb, i0);
+            ya = Y.window(yb, j0);
         }
+        if constexpr (!ListT::kBulk) __syncwarp();  // the decoded windows are visible to the group
         if (!__all_sync(kFull, ok)) {  // a bounded wait ran out: report and stop this warp
             if (lane == 0) atomicOr(status, ST_TIMEOUT);
             return;
@@ -509,7 +519,7 @@ __device__ __forceinline__ void group_engine(const DevSet &R, const DevSet &S, c
                     i0 = j0 = 0;
                     w = w0;
                     fresh = true;
-                    if (join_lists(R, S, dr, ds, stage, X, nX, Y, nY)) break;
+                    if (join_lists(R, S, dr, ds, stage, X, Y)) break;
                     if (stage == 2) verdict = APRIL_INCONCLUSIVE;
                 }
                 if (verdict >= 0) {
@@ -580,7 +590,7 @@ __global__ void APRIL_PERSISTENT_BOUNDS k_persistent(SetsT R, SetsT S,
         }
         __syncthreads();
     }
-    if constexpr (G == 32 || SetsT::kPacked) {
+    if constexpr (G == 32) {
         JoinSync js{smem_addr(&bars[1 + warp * 8]), 0u, false};
         const uint64_t nchunks = (n + 31) / 32;
         for (;;) {
@@ -593,7 +603,7 @@ __global__ void APRIL_PERSISTENT_BOUNDS k_persistent(SetsT R, SetsT S,
                 return;
         }
     } else {
-        group_engine<G>(R.s, S.s, pr, ps, n, out, status, counters, cta_threshold, wbuf, s_chunk[warp],
+        group_engine<G>(R, S, pr, ps, n, out, status, counters, cta_threshold, wbuf, s_chunk[warp],
                         smem_addr(&bars[1 + warp * 8]),
                         lane, w0_group);
     }
@@ -787,7 +797,8 @@ struct april_ctx {
     int device = 0;
     uint32_t *d_status = nullptr;  // 256-byte status block (word 0: ST_* bits)
     int num_sms = 0;
-    int persistent_blocks_per_sm[5] = {1, 1, 1, 1, 1};  // occupancy of k_persistent<4, 8, 16, 32>, packed
+    // occupancy of k_persistent<4, 8, 16, 32> over raw lists, then over packed lists
+    int persistent_blocks_per_sm[8] = {1, 1, 1, 1, 1, 1, 1, 1};
     april_tune tune{};
     cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
     cudaGraphExec_t graph = nullptr;    // the batched pipeline, captured once per argument set
@@ -847,6 +858,15 @@ extern "C" april_status april_ctx_create(int device, april_ctx **out) {
                                                           kBlock, 0);
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->persistent_blocks_per_sm[4],
+                                                          k_persistent<4, PackedSets>, kBlock, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->persistent_blocks_per_sm[5],
+                                                          k_persistent<8, PackedSets>, kBlock, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->persistent_blocks_per_sm[6],
+                                                          k_persistent<16, PackedSets>, kBlock, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->persistent_blocks_per_sm[7],
                                                           k_persistent<32, PackedSets>, kBlock, 0);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_status, 256);
@@ -979,9 +999,16 @@ static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, con
     if (packed) {
         const PackedSets R = packed_set(Rd), S = packed_set(Sd);
         k_bin<<<grid_bin, 256, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold, big_list, counters);
-        k_persistent<32, PackedSets><<<grid_main, kBlock, 0, st>>>(R, S, d_r, d_s, n, out, status,
-                                                                   t.cta_threshold, big_list, counters, 64u,
-                                                                   t.cta_window);
+#define APRIL_LAUNCH_PACKED(G)                                                                                  \
+    k_persistent<G, PackedSets><<<grid_main, kBlock, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold,   \
+                                                              big_list, counters, t.group_window, t.cta_window)
+        switch (t.group_lanes) {
+            case 4: APRIL_LAUNCH_PACKED(4); break;
+            case 8: APRIL_LAUNCH_PACKED(8); break;
+            case 16: APRIL_LAUNCH_PACKED(16); break;
+            default: APRIL_LAUNCH_PACKED(32); break;
+        }
+#undef APRIL_LAUNCH_PACKED
         return cudaGetLastError();
     }
     const RawSets R{dev_set(Rd)}, S{dev_set(Sd)};
@@ -1007,7 +1034,7 @@ static april_status launch_batched(april_ctx *ctx, const april_dev_sets *R, cons
                                    void *scratch, bool packed, cudaStream_t st) {
     const unsigned grid_bin = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx->num_sms * 8);
     const uint32_t gl = ctx->tune.group_lanes;
-    const int occ = ctx->persistent_blocks_per_sm[packed ? 4 : gl == 4 ? 0 : gl == 8 ? 1 : gl == 16 ? 2 : 3];
+    const int occ = ctx->persistent_blocks_per_sm[(packed ? 4 : 0) + (gl == 4 ? 0 : gl == 8 ? 1 : gl == 16 ? 2 : 3)];
     const int bps = ctx->tune.blocks_per_sm ? (int)std::min<uint32_t>(ctx->tune.blocks_per_sm, (uint32_t)occ) : occ;
     const unsigned grid_main = (unsigned)std::max(1, ctx->num_sms * bps);
     GraphKey key{R->desc, R->iv, S->desc, S->iv, R->n_objects, S->n_objects, d_r, d_s, out, scratch, n,
@@ -1051,7 +1078,7 @@ april_status april_enqueue_request(april_ctx *ctx, const april_dev_sets *R, cons
     const bool packed = false;  // serving reads the raw lists
     const unsigned grid_bin = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx->num_sms * 8));
     const uint32_t gl = ctx->tune.group_lanes;
-    const int occ = ctx->persistent_blocks_per_sm[packed ? 4 : gl == 4 ? 0 : gl == 8 ? 1 : gl == 16 ? 2 : 3];
+    const int occ = ctx->persistent_blocks_per_sm[(packed ? 4 : 0) + (gl == 4 ? 0 : gl == 8 ? 1 : gl == 16 ? 2 : 3)];
     unsigned grid_main = (unsigned)std::max(1, ctx->num_sms * occ);
     grid_main = std::min<unsigned>(grid_main, std::max<unsigned>(1, max_ctas));
     cudaError_t e = enqueue_batched(ctx, R, S, d_r, d_s, n, d_verdict, d_scratch, packed, grid_bin, grid_main,
