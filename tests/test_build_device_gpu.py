@@ -174,3 +174,27 @@ def test_selection_with_device_built_queries(torch_cuda, ctx):
     for a, b in zip(res[0], res[1]):
         assert np.array_equal(a, b)
     assert len(res[0][0]) > 300
+
+
+def test_device_sets_variants_equal_host(torch_cuda, ctx):
+    """The filter variants over GPU-built sets (within; S on a coarser grid)
+    give the host execution's verdicts over host-built sets."""
+    torch = torch_cuda
+    w = _data.workload(2, 0.01)
+    gR, gS2 = A.global_grid(w.order), A.global_grid(w.order - 2)
+    R = A.april_build_sets(w.R.xy, w.R.off, gR)
+    S = A.april_build_sets(w.S.xy, w.S.off, gR)
+    S2 = A.april_build_sets(w.S.xy, w.S.off, gS2)
+    dR, _ = ctx.april_build_sets_device(*_device_polys(torch, w.R.xy, w.R.off), gR)
+    dS, _ = ctx.april_build_sets_device(*_device_polys(torch, w.S.xy, w.S.off), gR)
+    dS2, _ = ctx.april_build_sets_device(*_device_polys(torch, w.S.xy, w.S.off), gS2)
+    n = len(w.pr)
+    d_r = torch.from_numpy(w.pr.view(np.int32)).cuda()
+    d_s = torch.from_numpy(w.ps.view(np.int32)).cuda()
+    scratch = torch.empty(ctx.scratch_bytes(A.MODE_BATCHED, n), dtype=torch.uint8, device="cuda")
+    for host_S, dev_S, pred in ((S, dS, A.PREDICATE_WITHIN), (S2, dS2, A.PREDICATE_INTERSECTS)):
+        out = torch.full((n,), 0xEE, dtype=torch.uint8, device="cuda")
+        ctx.april_filter_pairs_ex(dR, dev_S, d_r, d_s, n, out, pred, scratch)
+        ctx.april_sync_status()
+        want, _ = A.april_host_filter_ex(R, host_S, w.pr, w.ps, pred)
+        assert np.array_equal(out.cpu().numpy(), want), pred

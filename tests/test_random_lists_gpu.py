@@ -135,9 +135,11 @@ def test_random_lists_variants_equal_host(torch_cuda, ctx, data, which):
         assert len(bad) == 0, (which, long_window, len(bad), bad[:10])
 
 
-def test_random_lists_packed_equal_host(torch_cuda, ctx, data):
+@pytest.mark.parametrize("tune", [None, (2048, 4, 16, 64), (0, 8, 8, 64), (512, 16, 128, 256), (0xFFFFFFFF, 32, 64, 256)])
+def test_random_lists_packed_equal_host(torch_cuda, ctx, data, tune):
     """The compressed form of random lists (per-block uint16/uint32 gaps)
-    filters to the same verdicts as the host over the raw lists."""
+    filters to the same verdicts as the host over the raw lists, with lane
+    groups of every size and long pairs by warps or CTAs."""
     torch = torch_cuda
     _, _, _, pr, ps = data
     Rc = _random_sets(np.random.default_rng(11), 1500, 16, 1 << 30)
@@ -150,5 +152,11 @@ def test_random_lists_packed_equal_host(torch_cuda, ctx, data):
     def fn(d_r, d_s, out, n):
         scratch = torch.empty(ctx.scratch_bytes(A.MODE_BATCHED_PACKED, n), dtype=torch.uint8, device="cuda")
         ctx.april_filter_pairs(dR, dS, d_r, d_s, n, out, A.MODE_BATCHED_PACKED, scratch)
-    got = _run(torch, ctx, dR, dS, pr, ps, fn)
+    saved = ctx.get_tune()
+    if tune:
+        ctx.set_tune(A.april_tune(*tune, 0, 0.0))
+    try:
+        got = _run(torch, ctx, dR, dS, pr, ps, fn)
+    finally:
+        ctx.set_tune(saved)
     assert np.array_equal(got, want), np.flatnonzero(got != want)[:10]
