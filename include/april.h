@@ -129,9 +129,12 @@ void april_sets_destroy(april_sets *sets);
  * in [a_off[o], a_off[o+1]) as [st, end) pairs, likewise its F-list from
  * f_off / f_iv; at order 16 an end of 2^32 is written as 0.  The filter only
  * needs each list sorted and disjoint (Sec. 4.2's merge), so any cell order
- * works as long as both join inputs use the same one.  mbr (4 int32 per
- * object, as april_sets_mbrs) may be NULL.  Lists that are empty-interval,
- * unsorted, overlapping or past the grid: APRIL_ERR_INVALID_ARG. */
+ * works as long as both join inputs use the same one; as for every APRIL
+ * approximation, the F cells must be among the A cells (Sec. 4.1: each F
+ * interval inside one A interval), which the GPU kernels rely on when they
+ * order the joins.  mbr (4 int32 per object, as april_sets_mbrs) may be NULL.
+ * Lists that are empty-interval, unsorted, overlapping, past the grid, or
+ * with F not inside A: APRIL_ERR_INVALID_ARG. */
 april_status april_sets_from_lists(uint32_t n, uint32_t order, const uint64_t *a_off, const uint32_t *a_iv,
                                    const uint64_t *f_off, const uint32_t *f_iv, const int32_t *mbr,
                                    april_sets **out);
@@ -573,14 +576,16 @@ april_status april_host_filter(const april_sets *R, const april_sets *S, const u
                                const uint32_t *ps, uint64_t n, uint32_t n_threads, uint8_t *verdict,
                                uint64_t *consumed);
 
-/* Algorithm 2 with every merge join started where the GPU kernels start it:
- * each list at its first interval whose last cell reaches the other list's
- * first start (found by binary search; the sequential merge from the front
- * passes over the intervals before it without a verdict, so the verdicts
- * equal april_host_filter's).  consumed[k] counts, for every join that ran,
- * the intervals the merge reads from the start positions plus the search's
- * probes (the bit width of each list's length): the bytes model of the
- * kernels' reading, used for their roofline. */
+/* Algorithm 2 run the way the batched GPU kernels run it: the joins in the
+ * order AF, AA, FA (an AF or FA overlap implies an AA overlap, so the
+ * verdicts are Algorithm 2's whatever the order, Sec. 4.2) and every merge
+ * join started at each list's first interval whose last cell reaches the
+ * other list's first start (found by binary search; the sequential merge from
+ * the front passes over the intervals before it without a verdict).  The
+ * verdicts equal april_host_filter's.  consumed[k] counts, for every join
+ * that ran, the intervals the merge reads from the start positions plus the
+ * search's probes (the bit width of each list's length): the bytes model of
+ * the kernels' reading, used for their roofline. */
 april_status april_host_filter_searched(const april_sets *R, const april_sets *S, const uint32_t *pr,
                                         const uint32_t *ps, uint64_t n, uint32_t n_threads, uint8_t *verdict,
                                         uint64_t *consumed);

@@ -409,6 +409,21 @@ extern "C" april_status april_sets_from_lists(uint32_t n, uint32_t order, const 
                 }
             }
         }
+        // an approximation's Full cells are among the cells it meets (Sec.
+        // 4.1): every F interval must lie inside one A interval
+        for (uint32_t o = 0; o < n; ++o) {
+            const auto &Al = lists[o].A, &Fl = lists[o].F;
+            size_t a = 0;
+            for (size_t f = 0; f < Fl.size(); f += 2) {
+                const uint64_t fs = Fl[f], fe = Fl[f + 1] == 0 ? ncells : Fl[f + 1];
+                while (a < Al.size() && (Al[a + 1] == 0 ? ncells : Al[a + 1]) < fe) a += 2;
+                if (a >= Al.size() || Al[a] > fs) {
+                    char m[128];
+                    std::snprintf(m, sizeof m, "object %u: an F interval is not inside an A interval", o);
+                    return fail(APRIL_ERR_INVALID_ARG, m);
+                }
+            }
+        }
         auto *S = new april_sets();
         S->n = n;
         S->n_entries = n;
@@ -818,10 +833,17 @@ static april_status host_filter(const april_sets *R, const april_sets *S, const 
                 const uint32_t *dr = &R->desc[4 * (size_t)r], *ds = &S->desc[4 * (size_t)s];
                 const uint32_t *Ar = &R->iv[2 * (size_t)dr[0]], *Fr = &R->iv[2 * (size_t)dr[2]];
                 const uint32_t *As = &S->iv[2 * (size_t)ds[0]], *Fs = &S->iv[2 * (size_t)ds[2]];
-                if (!join(Ar, dr[1], As, ds[1], &used)) v = APRIL_TRUE_NEGATIVE;
-                else if (join(Ar, dr[1], Fs, ds[3], &used)) v = APRIL_TRUE_HIT;
-                else if (join(Fr, dr[3], As, ds[1], &used)) v = APRIL_TRUE_HIT;
-                else v = APRIL_INCONCLUSIVE;
+                if (!searched) {  // Algorithm 2's order: AA, AF, FA
+                    if (!join(Ar, dr[1], As, ds[1], &used)) v = APRIL_TRUE_NEGATIVE;
+                    else if (join(Ar, dr[1], Fs, ds[3], &used)) v = APRIL_TRUE_HIT;
+                    else if (join(Fr, dr[3], As, ds[1], &used)) v = APRIL_TRUE_HIT;
+                    else v = APRIL_INCONCLUSIVE;
+                } else {  // the GPU kernels' order: AF, AA, FA (same verdicts)
+                    if (join(Ar, dr[1], Fs, ds[3], &used)) v = APRIL_TRUE_HIT;
+                    else if (!join(Ar, dr[1], As, ds[1], &used)) v = APRIL_TRUE_NEGATIVE;
+                    else if (join(Fr, dr[3], As, ds[1], &used)) v = APRIL_TRUE_HIT;
+                    else v = APRIL_INCONCLUSIVE;
+                }
             }
             verdict[k] = v;
             if (consumed) consumed[k] = used;

@@ -138,6 +138,31 @@ __global__ void __launch_bounds__(256) k_plain(DevSet R, DevSet S, const uint32_
 // else AF, then FA.
 // Shared-memory synchronisation state of a warp or CTA join: the mbarrier the
 // window copies complete on, its phase bit, and a timeout flag.
+struct JoinSync;
+
+// The joins of the batched kernels run in the order AF, AA, FA.  The
+// verdicts of Sec. 4.2 do not depend on the order (F is a subset of A, so an
+// AF or FA overlap implies an AA overlap): AF first settles most true hits in
+// one join, a pair without an AF overlap takes AA (none: true negative) and
+// then FA.  Step s joins X = F(r) when s == 2 (else A(r)) with Y = F(s) when
+// s == 0 (else A(s)).  A join with an empty list has no overlap.
+__device__ __forceinline__ bool step_x_f(uint32_t s) { return s == 2; }
+__device__ __forceinline__ bool step_y_f(uint32_t s) { return s == 0; }
+// The verdict after step s found `overlap` (>= 0), or -1 with s advanced.
+__device__ __forceinline__ int step_outcome(uint32_t &s, bool overlap) {
+    if (s == 0) {
+        if (overlap) return APRIL_TRUE_HIT;
+        s = 1;
+        return -1;
+    }
+    if (s == 1) {
+        if (!overlap) return APRIL_TRUE_NEGATIVE;
+        s = 2;
+        return -1;
+    }
+    return overlap ? APRIL_TRUE_HIT : APRIL_INCONCLUSIVE;
+}
+
 struct JoinSync {
     uint32_t bar;
     uint32_t phase;
@@ -148,37 +173,29 @@ template <class SetsT>
 __device__ __forceinline__ uint8_t warp_verdict(const SetsT &R, const SetsT &S, const typename SetsT::Desc &dr,
                                                 const typename SetsT::Desc &ds, uint2 *xs, uint2 *ys, uint32_t lane,
                                                 uint32_t w0, JoinSync &js) {
-    const uint32_t b = js.bar;
-    if (!tile_join<WarpScope, 32, kWarpWMax>(R.list(dr, false), S.list(ds, false), xs, ys, nullptr, lane, w0, b,
-                                              &js.phase, &js.timeout))
-        return js.timeout ? APRIL_VERDICT_ERROR : APRIL_TRUE_NEGATIVE;
-    if (tile_join<WarpScope, 32, kWarpWMax>(R.list(dr, false), S.list(ds, true), xs, ys, nullptr, lane, w0, b,
-                                             &js.phase, &js.timeout))
-        return APRIL_TRUE_HIT;
-    if (js.timeout) return APRIL_VERDICT_ERROR;
-    if (tile_join<WarpScope, 32, kWarpWMax>(R.list(dr, true), S.list(ds, false), xs, ys, nullptr, lane, w0, b,
-                                             &js.phase, &js.timeout))
-        return APRIL_TRUE_HIT;
-    return js.timeout ? APRIL_VERDICT_ERROR : APRIL_INCONCLUSIVE;
+    uint32_t st = 0;
+    for (;;) {
+        const bool ov = tile_join<WarpScope, 32, kWarpWMax>(R.list(dr, step_x_f(st)), S.list(ds, step_y_f(st)), xs,
+                                                            ys, nullptr, lane, w0, js.bar, &js.phase, &js.timeout);
+        if (js.timeout) return APRIL_VERDICT_ERROR;
+        const int v = step_outcome(st, ov);
+        if (v >= 0) return (uint8_t)v;
+    }
 }
 
-// Algorithm 2 for one pair by the whole CTA.
+// The same for one pair by the whole CTA.
 template <class SetsT>
 __device__ __forceinline__ uint8_t cta_verdict(const SetsT &R, const SetsT &S, const typename SetsT::Desc &dr,
                                                const typename SetsT::Desc &ds, uint2 *xs, uint2 *ys, uint32_t *slot,
                                                uint32_t tid, uint32_t w0, JoinSync &js) {
-    const uint32_t b = js.bar;
-    if (!tile_join<CtaScope, kBlock, kCtaWMax>(R.list(dr, false), S.list(ds, false), xs, ys, slot, tid, w0, b,
-                                               &js.phase, &js.timeout))
-        return js.timeout ? APRIL_VERDICT_ERROR : APRIL_TRUE_NEGATIVE;
-    if (tile_join<CtaScope, kBlock, kCtaWMax>(R.list(dr, false), S.list(ds, true), xs, ys, slot, tid, w0, b,
-                                              &js.phase, &js.timeout))
-        return APRIL_TRUE_HIT;
-    if (js.timeout) return APRIL_VERDICT_ERROR;
-    if (tile_join<CtaScope, kBlock, kCtaWMax>(R.list(dr, true), S.list(ds, false), xs, ys, slot, tid, w0, b,
-                                              &js.phase, &js.timeout))
-        return APRIL_TRUE_HIT;
-    return js.timeout ? APRIL_VERDICT_ERROR : APRIL_INCONCLUSIVE;
+    uint32_t st = 0;
+    for (;;) {
+        const bool ov = tile_join<CtaScope, kBlock, kCtaWMax>(R.list(dr, step_x_f(st)), S.list(ds, step_y_f(st)), xs,
+                                                              ys, slot, tid, w0, js.bar, &js.phase, &js.timeout);
+        if (js.timeout) return APRIL_VERDICT_ERROR;
+        const int v = step_outcome(st, ov);
+        if (v >= 0) return (uint8_t)v;
+    }
 }
 
 // One warp filters the 32 pairs starting at `base`: every lane fetches the
@@ -303,12 +320,13 @@ static_assert(GroupCfg<8>::NG * 2 * GroupCfg<8>::BUF <= kWarpShare, "group buffe
 static_assert(GroupCfg<16>::NG * 2 * GroupCfg<16>::BUF <= kWarpShare, "group buffers fit in a warp's share");
 static_assert(2 * kWarpBuf <= kWarpShare, "warp buffers fit in a warp's share");
 
-// Lists of join `stage` of a pair: 0 = A(r) x A(s), 1 = A(r) x F(s), 2 = F(r) x A(s).
+// Lists of join step `stage` of a pair (the order AF, AA, FA of step_outcome);
+// false when one of them is empty (the join then has no overlap).
 template <class SetsT, class ListT>
 __device__ __forceinline__ bool join_lists(const SetsT &R, const SetsT &S, const uint4 &dr, const uint4 &ds,
                                            uint32_t stage, ListT &X, ListT &Y) {
-    X = R.list(dr, stage == 2);
-    Y = S.list(ds, stage == 1);
+    X = R.list(dr, step_x_f(stage));
+    Y = S.list(ds, step_y_f(stage));
     return X.n != 0 && Y.n != 0;
 }
 
@@ -437,9 +455,12 @@ __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, con
                 stage = 0;
                 i0 = j0 = 0;
                 w = w0;
-                active = join_lists(R, S, dr, ds, 0, X, Y);
                 fresh = true;
-                if (!active && t == 0) out[k] = APRIL_TRUE_NEGATIVE;  // an empty A-list meets nothing
+                int verdict = -1;  // steps with an empty list have no overlap
+                while (!join_lists(R, S, dr, ds, stage, X, Y))
+                    if ((verdict = step_outcome(stage, false)) >= 0) break;
+                active = verdict < 0;
+                if (!active && t == 0) out[k] = (uint8_t)verdict;
             }
             const uint32_t lastbit = __fns(avail, 0, (int)cnt);
             avail &= (lastbit >= 31) ? 0u : ~((2u << lastbit) - 1u);
@@ -509,18 +530,13 @@ __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, con
                 w = min(w * 2u, C::WMAX);
             }
             if (res >= 0) {
-                // Algorithm 2: AA false -> TN; AF or FA true -> TH; else INC
-                int verdict = -1;
-                if (stage == 0) verdict = res ? -1 : APRIL_TRUE_NEGATIVE;
-                else if (res) verdict = APRIL_TRUE_HIT;
-                else if (stage == 2) verdict = APRIL_INCONCLUSIVE;
+                int verdict = step_outcome(stage, res != 0);
                 while (verdict < 0) {
-                    ++stage;
                     i0 = j0 = 0;
                     w = w0;
                     fresh = true;
                     if (join_lists(R, S, dr, ds, stage, X, Y)) break;
-                    if (stage == 2) verdict = APRIL_INCONCLUSIVE;
+                    verdict = step_outcome(stage, false);
                 }
                 if (verdict >= 0) {
                     if (t == 0) out[k] = (uint8_t)verdict;
@@ -1148,19 +1164,23 @@ static Plan make_plan(int predicate, uint32_t order_r, uint32_t order_s) {
         P.xf[1] = 0; P.yf[1] = 1; P.pred[1] = kContain; P.on_true[1] = INC; P.on_false[1] = TH;
         return P;
     }
-    P.xf[0] = 0; P.yf[0] = 0; P.pred[0] = kOverlap; P.on_true[0] = 1; P.on_false[0] = TN;
-    if (order_r == order_s) {  // Algorithm 2
+    // intersects: the join that can give a true hit first, then AA (the
+    // order of the batched kernels, see step_outcome)
+    if (order_r == order_s) {  // Algorithm 2's verdicts in the order AF, AA, FA
         P.nst = 3;
-        P.xf[1] = 0; P.yf[1] = 1; P.pred[1] = kOverlap; P.on_true[1] = TH; P.on_false[1] = 2;
+        P.xf[0] = 0; P.yf[0] = 1; P.pred[0] = kOverlap; P.on_true[0] = TH; P.on_false[0] = 1;
+        P.xf[1] = 0; P.yf[1] = 0; P.pred[1] = kOverlap; P.on_true[1] = 2; P.on_false[1] = TN;
         P.xf[2] = 1; P.yf[2] = 0; P.pred[2] = kOverlap; P.on_true[2] = TH; P.on_false[2] = INC;
     } else if (order_r > order_s) {  // Sec. 5.3: coarsen r, use only the coarse side's F-list
         P.nst = 2;
         P.sx = (uint8_t)(2 * (order_r - order_s));
-        P.xf[1] = 0; P.yf[1] = 1; P.pred[1] = kOverlap; P.on_true[1] = TH; P.on_false[1] = INC;
+        P.xf[0] = 0; P.yf[0] = 1; P.pred[0] = kOverlap; P.on_true[0] = TH; P.on_false[0] = 1;
+        P.xf[1] = 0; P.yf[1] = 0; P.pred[1] = kOverlap; P.on_true[1] = INC; P.on_false[1] = TN;
     } else {
         P.nst = 2;
         P.sy = (uint8_t)(2 * (order_s - order_r));
-        P.xf[1] = 1; P.yf[1] = 0; P.pred[1] = kOverlap; P.on_true[1] = TH; P.on_false[1] = INC;
+        P.xf[0] = 1; P.yf[0] = 0; P.pred[0] = kOverlap; P.on_true[0] = TH; P.on_false[0] = 1;
+        P.xf[1] = 0; P.yf[1] = 0; P.pred[1] = kOverlap; P.on_true[1] = INC; P.on_false[1] = TN;
     }
     return P;
 }

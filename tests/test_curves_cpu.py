@@ -82,6 +82,9 @@ def test_import_rejects_bad_lists():
             A.april_sets_from_lists(4, [np.array(bad, np.uint64)], ok)
     with pytest.raises(A.AprilError):
         A.april_sets_from_lists(17, ok, ok)
+    with pytest.raises(A.AprilError):  # an F interval outside the A intervals
+        A.april_sets_from_lists(4, ok, [np.array([[2, 4]], np.uint64)])
+    A.april_sets_from_lists(4, ok, [np.array([[1, 2], [5, 6]], np.uint64)])
     # an end of 2^32 at order 16 is written as 0 and accepted
     top = [np.array([[0xFFFFFFF0, 1 << 32]], np.uint64)]
     S = A.april_sets_from_lists(16, top, top)

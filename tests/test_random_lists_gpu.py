@@ -6,7 +6,9 @@ Algorithm 2 (april_host_filter, which the CPU tests pin to the oracle), and
 the filter variants likewise with april_host_filter_ex.  The lists include
 heavy-tailed lengths (up to thousands of intervals against a few), single
 cells, intervals ending at the last cell of order 16 (end 2^32 written as
-0), empty F-lists, and pairs of an object with itself."""
+0), empty F-lists, and pairs of an object with itself; F-lists are random
+sub-intervals of the A-lists, as every approximation's Full cells are among
+the cells it meets."""
 import numpy as np
 import pytest
 
@@ -45,15 +47,28 @@ def _random_list(rng, order, k, hot):
     return pts.reshape(-1, 2)
 
 
+def _inner_list(rng, a):
+    """Random F intervals inside the A intervals of `a` (an approximation's
+    Full cells are among the cells it meets): for a random subset of A's
+    intervals, one random sub-interval each."""
+    if len(a) == 0 or rng.random() < 0.2:
+        return np.zeros((0, 2), np.uint64)
+    pick = np.flatnonzero(rng.random(len(a)) < rng.uniform(0.1, 0.9))
+    out = []
+    for st, en in a[pick].astype(np.int64).tolist():
+        lo = int(rng.integers(st, en))
+        hi = int(rng.integers(lo + 1, en + 1))
+        out.append((lo, hi))
+    return np.array(out, np.uint64).reshape(-1, 2)
+
+
 def _random_sets(rng, n, order, hot):
     A_, F_ = [], []
     for _ in range(n):
         ka = int(min(6000, rng.pareto(1.2) * 8 + 1))
         a = _random_list(rng, order, ka, hot)
-        f = _random_list(rng, order, int(rng.integers(0, max(1, ka // 2) + 1)), hot) if rng.random() < 0.8 \
-            else np.zeros((0, 2), np.uint64)
         A_.append(a)
-        F_.append(f)
+        F_.append(_inner_list(rng, a))
     return A.april_sets_from_lists(order, A_, F_)
 
 
