@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tuning (profiling runs)")
-    ap.add_argument("--tune", default=None, help="T,G,W,CW: fixed batched tuning instead of the autotuner")
+    ap.add_argument("--tune", default=None,
+                    help="T,G,W,CW[,JO]: fixed batched tuning instead of the autotuner (JO: join order 0 or 1)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
     ap.add_argument("--serving-requests", type=int, default=120)
     ap.add_argument("--no-selection", action="store_true", help="skip the selection-query measurement")
@@ -86,7 +87,7 @@ def kernel_traffic(kernel: str, workload: str, tune):
         return None
     sha = kernel_source_sha()
     key = None if tune is None else [tune["cta_threshold"], tune["group_lanes"], tune["group_window"],
-                                     tune["cta_window"]]
+                                     tune["cta_window"], tune.get("join_order", 0)]
     for e in json.load(open(p)):
         if (e.get("kernel") == kernel and e.get("workload") == workload and e.get("src_sha") == sha
                 and e.get("tune") == key):
@@ -220,6 +221,14 @@ def selection_bench(ctx, A, torch, dev, stream, flush, R, dR, steps, warmup):
     d_v = torch.empty(n, dtype=torch.uint8, device=dev)
     scratch = torch.empty(ctx.select_scratch_bytes(n), dtype=torch.uint8, device=dev)
 
+    # the filter's tuning for these pairs (small data polygons against large
+    # queries), picked by the autotuner on the candidate pairs
+    ctx.april_select(dI, dR, dQ, n, d_r, d_q, d_v, off, scratch, stream)
+    stream.synchronize()
+    sc_tune = torch.empty(ctx.scratch_bytes(A.MODE_BATCHED, n), dtype=torch.uint8, device=dev)
+    tuned = ctx.april_autotune(dR, dQ, d_r, d_q, n, d_v, sc_tune, stream).as_dict()
+    del sc_tune
+
     def run():
         ctx.april_select(dI, dR, dQ, n, d_r, d_q, d_v, off, scratch, stream)
     t = _event_times(torch, stream, flush, run, steps, warmup)
@@ -277,6 +286,7 @@ def selection_bench(ctx, A, torch, dev, stream, flush, R, dR, steps, warmup):
     ms = statistics.mean(t)
     e2e_dev_ms = statistics.mean(e2e_dev[1:]) * 1e3
     return {"workload": s.name, "queries": int(s.Q.n), "candidate_pairs": int(n), "ms_per_batch": ms,
+            "filter_tune": tuned,
             "e2e_gpu_construction": {"ms_per_batch": e2e_dev_ms, "queries_per_s": s.Q.n / (e2e_dev_ms * 1e-3),
                                      "h2d_bytes": int(h_xy.numel() * 4 + h_off.numel() * 8), "d2h_bytes": int(n),
                                      "path": "pinned query polygons to the GPU + april_build_sets_device + "
@@ -545,8 +555,9 @@ def main():
     mode = args.mode
     tune = None
     if mode in ("batched", "packed") and args.tune:
-        T, G, W, CW = (int(x) for x in args.tune.split(","))
-        ctx.set_tune(A.april_tune(T, G, W, CW, 0, 0.0))
+        vals = [int(x) for x in args.tune.split(",")]
+        T, G, W, CW = vals[:4]
+        ctx.set_tune(A.april_tune(T, G, W, CW, 0, 0.0, vals[4] if len(vals) > 4 else 0))
         tune = ctx.get_tune().as_dict()
     elif mode in ("batched", "packed") and not args.no_autotune:
         # the project's autotuner picks the CTA threshold and first warp window

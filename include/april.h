@@ -252,7 +252,7 @@ void april_ctx_destroy(april_ctx *ctx);
 /* ------------------------------------------------------------------ tuning */
 
 /* Knobs of APRIL_MODE_BATCHED (a build-side addition; the paper's CPU
- * filter has none).  Defaults: {2048, 4, 16, 64, 0}. */
+ * filter has none).  Defaults: {2048, 4, 16, 64, 0, -, 0}. */
 typedef struct april_tune {
     uint32_t cta_threshold;  /* pairs with |A(r)| + |A(s)| above this ("long pairs") are joined
                                 first, each by one warp or by a whole CTA (see cta_window) */
@@ -264,6 +264,10 @@ typedef struct april_tune {
                                 256..2048 = by the whole CTA */
     uint32_t blocks_per_sm;  /* persistent grid: CTAs per SM (0 = as many as fit) */
     float ms;                /* output of april_autotune: best time of the sample (ms) */
+    uint32_t join_order;     /* order of a pair's joins in the batched kernels (the verdicts are
+                                the same, Sec. 4.2): 0 = AF, AA, FA (a true hit from AF takes
+                                one join); 1 = AA, AF, FA, Algorithm 2's (a true negative takes
+                                one join) */
 } april_tune;
 
 april_status april_set_tune(april_ctx *ctx, const april_tune *tune);
@@ -275,7 +279,8 @@ april_status april_get_tune(const april_ctx *ctx, april_tune *tune);
  * {2048, 4096, 8192, 16384, none} x (group_lanes, group_window) in
  * {(4,8), (4,16), (8,16), (8,32), (16,32), (16,64), (32,64)} x long pairs by a
  * warp (cta_window 64) or by the CTA (the context's cta_window if >= 256, else
- * 256)).  Arguments as for april_filter_pairs; synchronizes `stream`. */
+ * 256) x join_order in {0, 1}).  Arguments as for april_filter_pairs;
+ * synchronizes `stream`. */
 april_status april_autotune(april_ctx *ctx, const april_dev_sets *R, const april_dev_sets *S,
                             const uint32_t *d_r, const uint32_t *d_s, uint64_t n, uint8_t *d_verdict,
                             void *d_scratch, size_t scratch_bytes, void *stream, april_tune *out);

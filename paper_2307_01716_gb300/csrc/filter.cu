@@ -140,27 +140,24 @@ __global__ void __launch_bounds__(256) k_plain(DevSet R, DevSet S, const uint32_
 // window copies complete on, its phase bit, and a timeout flag.
 struct JoinSync;
 
-// The joins of the batched kernels run in the order AF, AA, FA.  The
-// verdicts of Sec. 4.2 do not depend on the order (F is a subset of A, so an
-// AF or FA overlap implies an AA overlap): AF first settles most true hits in
-// one join, a pair without an AF overlap takes AA (none: true negative) and
-// then FA.  Step s joins X = F(r) when s == 2 (else A(r)) with Y = F(s) when
-// s == 0 (else A(s)).  A join with an empty list has no overlap.
-__device__ __forceinline__ bool step_x_f(uint32_t s) { return s == 2; }
-__device__ __forceinline__ bool step_y_f(uint32_t s) { return s == 0; }
+// The order of a pair's joins in the batched kernels (april_tune.join_order).
+// The verdicts of Sec. 4.2 do not depend on it (F is a subset of A, so an AF
+// or FA overlap implies an AA overlap).
+//   order 0, AF AA FA: AF first settles most true hits in one join; a pair
+//     without an AF overlap takes AA (none: true negative), then FA.
+//   order 1, AA AF FA (Algorithm 2's): a true negative takes one join.
+// Step s joins X = F(r) when s == 2 (else A(r)) with Y = F(s) when s is the
+// AF step (else A(s)).  A join with an empty list has no overlap.
+__device__ __forceinline__ bool step_x_f(uint32_t s, uint32_t jo) { return s == 2; }
+__device__ __forceinline__ bool step_y_f(uint32_t s, uint32_t jo) { return s == (jo ? 1u : 0u); }
 // The verdict after step s found `overlap` (>= 0), or -1 with s advanced.
-__device__ __forceinline__ int step_outcome(uint32_t &s, bool overlap) {
-    if (s == 0) {
-        if (overlap) return APRIL_TRUE_HIT;
-        s = 1;
-        return -1;
-    }
-    if (s == 1) {
-        if (!overlap) return APRIL_TRUE_NEGATIVE;
-        s = 2;
-        return -1;
-    }
-    return overlap ? APRIL_TRUE_HIT : APRIL_INCONCLUSIVE;
+__device__ __forceinline__ int step_outcome(uint32_t &s, bool overlap, uint32_t jo) {
+    if (s == 2) return overlap ? APRIL_TRUE_HIT : APRIL_INCONCLUSIVE;
+    const bool aa = (s == 0) == (jo != 0);  // this step is AA
+    if (aa && !overlap) return APRIL_TRUE_NEGATIVE;
+    if (!aa && overlap) return APRIL_TRUE_HIT;
+    ++s;
+    return -1;
 }
 
 struct JoinSync {
@@ -172,13 +169,13 @@ struct JoinSync {
 template <class SetsT>
 __device__ __forceinline__ uint8_t warp_verdict(const SetsT &R, const SetsT &S, const typename SetsT::Desc &dr,
                                                 const typename SetsT::Desc &ds, uint2 *xs, uint2 *ys, uint32_t lane,
-                                                uint32_t w0, JoinSync &js) {
+                                                uint32_t w0, JoinSync &js, uint32_t jo) {
     uint32_t st = 0;
     for (;;) {
-        const bool ov = tile_join<WarpScope, 32, kWarpWMax>(R.list(dr, step_x_f(st)), S.list(ds, step_y_f(st)), xs,
-                                                            ys, nullptr, lane, w0, js.bar, &js.phase, &js.timeout);
+        const bool ov = tile_join<WarpScope, 32, kWarpWMax>(R.list(dr, step_x_f(st, jo)), S.list(ds, step_y_f(st, jo)),
+                                                            xs, ys, nullptr, lane, w0, js.bar, &js.phase, &js.timeout);
         if (js.timeout) return APRIL_VERDICT_ERROR;
-        const int v = step_outcome(st, ov);
+        const int v = step_outcome(st, ov, jo);
         if (v >= 0) return (uint8_t)v;
     }
 }
@@ -187,13 +184,13 @@ __device__ __forceinline__ uint8_t warp_verdict(const SetsT &R, const SetsT &S, 
 template <class SetsT>
 __device__ __forceinline__ uint8_t cta_verdict(const SetsT &R, const SetsT &S, const typename SetsT::Desc &dr,
                                                const typename SetsT::Desc &ds, uint2 *xs, uint2 *ys, uint32_t *slot,
-                                               uint32_t tid, uint32_t w0, JoinSync &js) {
+                                               uint32_t tid, uint32_t w0, JoinSync &js, uint32_t jo) {
     uint32_t st = 0;
     for (;;) {
-        const bool ov = tile_join<CtaScope, kBlock, kCtaWMax>(R.list(dr, step_x_f(st)), S.list(ds, step_y_f(st)), xs,
-                                                              ys, slot, tid, w0, js.bar, &js.phase, &js.timeout);
+        const bool ov = tile_join<CtaScope, kBlock, kCtaWMax>(R.list(dr, step_x_f(st, jo)), S.list(ds, step_y_f(st, jo)),
+                                                              xs, ys, slot, tid, w0, js.bar, &js.phase, &js.timeout);
         if (js.timeout) return APRIL_VERDICT_ERROR;
-        const int v = step_outcome(st, ov);
+        const int v = step_outcome(st, ov, jo);
         if (v >= 0) return (uint8_t)v;
     }
 }
@@ -208,7 +205,7 @@ __device__ __forceinline__ bool warp_chunk(const SetsT &R, const SetsT &S, const
                                            const uint32_t *__restrict__ ps, uint64_t n, uint64_t base,
                                            uint8_t *__restrict__ out, uint32_t *status, uint2 *xs, uint2 *ys,
                                            uint32_t lane, uint32_t w0, uint32_t cta_threshold, bool flag_bad,
-                                           JoinSync &js) {
+                                           JoinSync &js, uint32_t jo) {
     const uint64_t k = base + lane;
     typename SetsT::Desc dr{}, ds{};
     bool take = false;
@@ -229,7 +226,7 @@ __device__ __forceinline__ bool warp_chunk(const SetsT &R, const SetsT &S, const
         const uint32_t t = __ffs(todo) - 1;
         todo &= todo - 1;
         const typename SetsT::Desc a = SetsT::shfl(dr, t), b = SetsT::shfl(ds, t);
-        const uint8_t v = warp_verdict(R, S, a, b, xs, ys, lane, w0, js);
+        const uint8_t v = warp_verdict(R, S, a, b, xs, ys, lane, w0, js, jo);
         if (lane == t) mine = v;
         if (js.timeout) {
             if (lane == 0) atomicOr(status, ST_TIMEOUT);
@@ -251,7 +248,8 @@ __device__ __forceinline__ void init_barriers(uint64_t *bars, uint32_t count) {
 // ------------------------------------------------------- K1: warp/pair
 __global__ void __launch_bounds__(kBlock) k_warp(DevSet R, DevSet S, const uint32_t *__restrict__ pr,
                                                  const uint32_t *__restrict__ ps, uint64_t n,
-                                                 uint8_t *__restrict__ out, uint32_t *status, uint32_t w0) {
+                                                 uint8_t *__restrict__ out, uint32_t *status, uint32_t w0,
+                                                 uint32_t jo) {
     __shared__ __align__(16) uint2 sm[kWarpsPerBlock][2][kWarpBuf];
     __shared__ uint64_t bars[kWarpsPerBlock];
     init_barriers(bars, kWarpsPerBlock);
@@ -260,7 +258,7 @@ __global__ void __launch_bounds__(kBlock) k_warp(DevSet R, DevSet S, const uint3
     const uint64_t stride = (uint64_t)gridDim.x * kWarpsPerBlock * 32;
     for (uint64_t base = ((uint64_t)blockIdx.x * kWarpsPerBlock + warp) * 32; base < n; base += stride)
         if (!warp_chunk(RawSets{R}, RawSets{S}, pr, ps, n, base, out, status, sm[warp][0], sm[warp][1], lane, w0,
-                        0xffffffffu, true, js))
+                        0xffffffffu, true, js, jo))
             return;
 }
 
@@ -320,13 +318,13 @@ static_assert(GroupCfg<8>::NG * 2 * GroupCfg<8>::BUF <= kWarpShare, "group buffe
 static_assert(GroupCfg<16>::NG * 2 * GroupCfg<16>::BUF <= kWarpShare, "group buffers fit in a warp's share");
 static_assert(2 * kWarpBuf <= kWarpShare, "warp buffers fit in a warp's share");
 
-// Lists of join step `stage` of a pair (the order AF, AA, FA of step_outcome);
+// Lists of join step `stage` of a pair (in join order jo, see step_outcome);
 // false when one of them is empty (the join then has no overlap).
 template <class SetsT, class ListT>
 __device__ __forceinline__ bool join_lists(const SetsT &R, const SetsT &S, const uint4 &dr, const uint4 &ds,
-                                           uint32_t stage, ListT &X, ListT &Y) {
-    X = R.list(dr, step_x_f(stage));
-    Y = S.list(ds, step_y_f(stage));
+                                           uint32_t stage, ListT &X, ListT &Y, uint32_t jo) {
+    X = R.list(dr, step_x_f(stage, jo));
+    Y = S.list(ds, step_y_f(stage, jo));
     return X.n != 0 && Y.n != 0;
 }
 
@@ -392,7 +390,8 @@ template <uint32_t G, class SetsT>
 __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, const uint32_t *__restrict__ pr,
                                              const uint32_t *__restrict__ ps, uint64_t n, uint8_t *__restrict__ out,
                                              uint32_t *status, uint32_t *counters, uint32_t cta_threshold, uint2 *wbuf,
-                                             uint4 *chunk_desc, uint32_t bars, uint32_t lane, uint32_t w0) {
+                                             uint4 *chunk_desc, uint32_t bars, uint32_t lane, uint32_t w0,
+                                             uint32_t jo) {
     using C = GroupCfg<G>;
     const uint32_t g = lane / G, t = lane % G, glead = g * G;
     const uint32_t gbits = (G == 32 ? kFull : ((1u << G) - 1u)) << glead;
@@ -457,8 +456,8 @@ __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, con
                 w = w0;
                 fresh = true;
                 int verdict = -1;  // steps with an empty list have no overlap
-                while (!join_lists(R, S, dr, ds, stage, X, Y))
-                    if ((verdict = step_outcome(stage, false)) >= 0) break;
+                while (!join_lists(R, S, dr, ds, stage, X, Y, jo))
+                    if ((verdict = step_outcome(stage, false, jo)) >= 0) break;
                 active = verdict < 0;
                 if (!active && t == 0) out[k] = (uint8_t)verdict;
             }
@@ -530,13 +529,13 @@ __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, con
                 w = min(w * 2u, C::WMAX);
             }
             if (res >= 0) {
-                int verdict = step_outcome(stage, res != 0);
+                int verdict = step_outcome(stage, res != 0, jo);
                 while (verdict < 0) {
                     i0 = j0 = 0;
                     w = w0;
                     fresh = true;
-                    if (join_lists(R, S, dr, ds, stage, X, Y)) break;
-                    verdict = step_outcome(stage, false);
+                    if (join_lists(R, S, dr, ds, stage, X, Y, jo)) break;
+                    verdict = step_outcome(stage, false, jo);
                 }
                 if (verdict >= 0) {
                     if (t == 0) out[k] = (uint8_t)verdict;
@@ -557,7 +556,8 @@ __global__ void APRIL_PERSISTENT_BOUNDS k_persistent(SetsT R, SetsT S,
                                                        const uint32_t *__restrict__ ps, uint64_t n,
                                                        uint8_t *__restrict__ out, uint32_t *status,
                                                        uint32_t cta_threshold, const uint32_t *__restrict__ big_list,
-                                                       uint32_t *counters, uint32_t w0_group, uint32_t w0_cta) {
+                                                       uint32_t *counters, uint32_t w0_group, uint32_t w0_cta,
+                                                       uint32_t jo) {
     __shared__ __align__(16) uint2 sm[kSharedIv];
     __shared__ uint32_t s_item, s_slot;
     // mbarriers: [0] the CTA phase, [1 + warp * 8 + group] the group engine,
@@ -579,7 +579,7 @@ __global__ void APRIL_PERSISTENT_BOUNDS k_persistent(SetsT R, SetsT S,
             if (it >= nbig) break;
             const uint64_t k = big_list[it];
             const typename SetsT::Desc dr = R.load(__ldg(pr + k)), ds = S.load(__ldg(ps + k));
-            const uint8_t v = warp_verdict(R, S, dr, ds, wbuf, wbuf + kWarpBuf, lane, w0_cta, ws);
+            const uint8_t v = warp_verdict(R, S, dr, ds, wbuf, wbuf + kWarpBuf, lane, w0_cta, ws, jo);
             if (lane == 0) out[k] = v;
             if (ws.timeout) break;
         }
@@ -597,7 +597,7 @@ __global__ void APRIL_PERSISTENT_BOUNDS k_persistent(SetsT R, SetsT S,
             if (it >= nbig) break;
             const uint64_t k = big_list[it];
             const typename SetsT::Desc dr = R.load(__ldg(pr + k)), ds = S.load(__ldg(ps + k));
-            const uint8_t v = cta_verdict(R, S, dr, ds, sm, sm + kCtaBuf, &s_slot, tid, w0_cta, cs);
+            const uint8_t v = cta_verdict(R, S, dr, ds, sm, sm + kCtaBuf, &s_slot, tid, w0_cta, cs, jo);
             if (tid == 0) out[k] = v;
             if (cs.timeout) {  // a bounded wait ran out: report and stop this CTA
                 if (tid == 0) atomicOr(status, ST_TIMEOUT);
@@ -615,13 +615,13 @@ __global__ void APRIL_PERSISTENT_BOUNDS k_persistent(SetsT R, SetsT S,
             c = __shfl_sync(kFull, c, 0);
             if (c >= nchunks) break;
             if (!warp_chunk(R, S, pr, ps, n, (uint64_t)c * 32, out, status, wbuf, wbuf + kWarpBuf, lane, w0_group,
-                            cta_threshold, false, js))
+                            cta_threshold, false, js, jo))
                 return;
         }
     } else {
         group_engine<G>(R, S, pr, ps, n, out, status, counters, cta_threshold, wbuf, s_chunk[warp],
                         smem_addr(&bars[1 + warp * 8]),
-                        lane, w0_group);
+                        lane, w0_group, jo);
     }
 }
 
@@ -835,6 +835,7 @@ static april_tune default_tune() {
     t.group_lanes = 4;
     t.group_window = 16;
     t.cta_window = 64;       // long pairs one per warp
+    t.join_order = 0;        // AF, AA, FA
     t.blocks_per_sm = 0;
     t.ms = 0.f;
     return t;
@@ -848,6 +849,7 @@ static april_status check_tune(const april_tune &t) {
         return fail(APRIL_ERR_INVALID_ARG, "group_window must be a power of two in [group_lanes, 8*group_lanes]");
     if (t.cta_window < 32 || t.cta_window > kCtaWMax || (t.cta_window & (t.cta_window - 1)))
         return fail(APRIL_ERR_INVALID_ARG, "cta_window must be a power of two in [32, 2048]");
+    if (t.join_order > 1) return fail(APRIL_ERR_INVALID_ARG, "join_order must be 0 (AF AA FA) or 1 (AA AF FA)");
     return APRIL_OK;
 }
 
@@ -1017,7 +1019,8 @@ static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, con
         k_bin<<<grid_bin, 256, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold, big_list, counters);
 #define APRIL_LAUNCH_PACKED(G)                                                                                  \
     k_persistent<G, PackedSets><<<grid_main, kBlock, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold,   \
-                                                              big_list, counters, t.group_window, t.cta_window)
+                                                              big_list, counters, t.group_window, t.cta_window,   \
+                                                              t.join_order)
         switch (t.group_lanes) {
             case 4: APRIL_LAUNCH_PACKED(4); break;
             case 8: APRIL_LAUNCH_PACKED(8); break;
@@ -1031,7 +1034,8 @@ static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, con
     k_bin<<<grid_bin, 256, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold, big_list, counters);
 #define APRIL_LAUNCH_PERSISTENT(G)                                                                            \
     k_persistent<G, RawSets><<<grid_main, kBlock, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold,       \
-                                                           big_list, counters, t.group_window, t.cta_window)
+                                                           big_list, counters, t.group_window, t.cta_window,      \
+                                                           t.join_order)
     switch (t.group_lanes) {
         case 4: APRIL_LAUNCH_PERSISTENT(4); break;
         case 8: APRIL_LAUNCH_PERSISTENT(8); break;
@@ -1134,7 +1138,8 @@ extern "C" april_status april_filter_pairs(april_ctx *ctx, const april_dev_sets 
         case APRIL_MODE_WARP: {
             uint64_t blocks = (n + kBlock - 1) / kBlock;
             unsigned grid = (unsigned)std::min<uint64_t>(blocks, (uint64_t)sms * 16);
-            k_warp<<<grid, kBlock, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, ctx->d_status, kWarpFirstWindow);
+            k_warp<<<grid, kBlock, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, ctx->d_status, kWarpFirstWindow,
+                                            ctx->tune.join_order);
             break;
         }
         case APRIL_MODE_BATCHED:
@@ -1153,7 +1158,7 @@ extern "C" april_status april_filter_pairs(april_ctx *ctx, const april_dev_sets 
 }
 
 // Decision plans (see K7).  Verdict v is encoded as -(v + 1).
-static Plan make_plan(int predicate, uint32_t order_r, uint32_t order_s) {
+static Plan make_plan(int predicate, uint32_t order_r, uint32_t order_s, uint32_t jo) {
     Plan P{};
     const int8_t TN = -1, TH = -2, INC = -3;
     if (predicate == APRIL_PREDICATE_WITHIN) {
@@ -1164,8 +1169,24 @@ static Plan make_plan(int predicate, uint32_t order_r, uint32_t order_s) {
         P.xf[1] = 0; P.yf[1] = 1; P.pred[1] = kContain; P.on_true[1] = INC; P.on_false[1] = TH;
         return P;
     }
-    // intersects: the join that can give a true hit first, then AA (the
-    // order of the batched kernels, see step_outcome)
+    // intersects in join order jo (step_outcome): 1 is Algorithm 2's AA AF FA
+    // (for different granularity: AA, then the coarse side's F-list join)
+    if (jo == 1) {
+        P.xf[0] = 0; P.yf[0] = 0; P.pred[0] = kOverlap; P.on_true[0] = 1; P.on_false[0] = TN;
+        if (order_r == order_s) {
+            P.nst = 3;
+            P.xf[1] = 0; P.yf[1] = 1; P.pred[1] = kOverlap; P.on_true[1] = TH; P.on_false[1] = 2;
+            P.xf[2] = 1; P.yf[2] = 0; P.pred[2] = kOverlap; P.on_true[2] = TH; P.on_false[2] = INC;
+        } else {
+            P.nst = 2;
+            const bool r_finer = order_r > order_s;
+            P.sx = r_finer ? (uint8_t)(2 * (order_r - order_s)) : 0;
+            P.sy = r_finer ? 0 : (uint8_t)(2 * (order_s - order_r));
+            P.xf[1] = r_finer ? 0 : 1; P.yf[1] = r_finer ? 1 : 0; P.pred[1] = kOverlap;
+            P.on_true[1] = TH; P.on_false[1] = INC;
+        }
+        return P;
+    }
     if (order_r == order_s) {  // Algorithm 2's verdicts in the order AF, AA, FA
         P.nst = 3;
         P.xf[0] = 0; P.yf[0] = 1; P.pred[0] = kOverlap; P.on_true[0] = TH; P.on_false[0] = 1;
@@ -1206,7 +1227,7 @@ extern "C" april_status april_filter_pairs_ex(april_ctx *ctx, const april_dev_se
     uint32_t *counters = (uint32_t *)d_scratch;
     uint32_t *big_list = (uint32_t *)((char *)d_scratch + kCounterBytes);
     const RawSets dR{dev_set(R)}, dS{dev_set(S)};
-    const Plan P = make_plan(predicate, R->order, S->order);
+    const Plan P = make_plan(predicate, R->order, S->order, ctx->tune.join_order);
     const unsigned grid_bin = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx->num_sms * 8);
     int bps = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_general, kBlock, 0);
@@ -1243,6 +1264,7 @@ extern "C" april_status april_autotune(april_ctx *ctx, const april_dev_sets *R, 
     april_status rc = APRIL_OK;
     // long pairs joined by one warp (first window 64) or by the whole CTA
     const uint32_t long_windows[] = {64u, saved.cta_window >= kBlock ? saved.cta_window : kBlock};
+    for (uint32_t jo = 0; jo < 2; ++jo)
     for (uint32_t T : thresholds) {
         for (const auto &gw : groups)
         for (const uint32_t lw : long_windows) {
@@ -1252,6 +1274,7 @@ extern "C" april_status april_autotune(april_ctx *ctx, const april_dev_sets *R, 
             t.group_lanes = gw[0];
             t.group_window = gw[1];
             t.cta_window = lw;
+            t.join_order = jo;
             ctx->tune = t;
             float best_here = 1e30f;
             for (int rep = 0; rep < 3 && rc == APRIL_OK; ++rep) {
@@ -1374,7 +1397,7 @@ NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
 
 // The persistent kernel instance for the default tuning's lane groups.
 using PersistentRaw = void (*)(RawSets, RawSets, const uint32_t *, const uint32_t *, uint64_t, uint8_t *,
-                               uint32_t *, uint32_t, const uint32_t *, uint32_t *, uint32_t, uint32_t);
+                               uint32_t *, uint32_t, const uint32_t *, uint32_t *, uint32_t, uint32_t, uint32_t);
 static PersistentRaw noalloc_kernel(uint32_t group_lanes) {
     switch (group_lanes) {
         case 4: return k_persistent<4, RawSets>;
@@ -1435,7 +1458,7 @@ extern "C" april_status april_filter_pairs_noalloc(const april_dev_sets *R, cons
     k_bin<<<grid_bin, 256, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, status, t.cta_threshold, big_list, counters);
     noalloc_kernel(t.group_lanes)<<<grid_main, kBlock, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, status,
                                                                 t.cta_threshold, big_list, counters, t.group_window,
-                                                                t.cta_window);
+                                                                t.cta_window, t.join_order);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "april_filter_pairs_noalloc launch");
     return APRIL_OK;

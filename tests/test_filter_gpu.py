@@ -182,6 +182,8 @@ def test_tune_validation(ctx):
                 (100, 8, 32, 16), (100, 8, 32, 96)]:
         with pytest.raises(A.AprilError):
             ctx.set_tune(A.april_tune(*bad, 0, 0.0))
+    with pytest.raises(A.AprilError):
+        ctx.set_tune(A.april_tune(100, 8, 32, 64, 0, 0.0, 2))
 
 
 def test_batched_scratch_checks(torch_cuda, ctx):

@@ -97,10 +97,11 @@ def _run(torch, ctx, dR, dS, pr, ps, fn):
     return out.cpu().numpy()
 
 
-@pytest.mark.parametrize("mode,tune", [("plain", None), ("warp", None),
+@pytest.mark.parametrize("mode,tune", [("plain", None), ("warp", None), ("warp", (2048, 4, 16, 64, 1)),
                                        ("batched", (2048, 4, 16, 64)), ("batched", (0, 8, 32, 64)),
                                        ("batched", (64, 16, 32, 256)), ("batched", (0xFFFFFFFF, 32, 64, 256)),
-                                       ("batched", (512, 4, 4, 2048))])
+                                       ("batched", (512, 4, 4, 2048)), ("batched", (2048, 4, 16, 64, 1)),
+                                       ("batched", (0, 8, 32, 256, 1)), ("batched", (0xFFFFFFFF, 16, 32, 64, 1))])
 def test_random_lists_equal_host(torch_cuda, ctx, data, mode, tune):
     torch = torch_cuda
     R, S, _, pr, ps = data
@@ -110,7 +111,7 @@ def test_random_lists_equal_host(torch_cuda, ctx, data, mode, tune):
     m = A.MODES[mode]
     saved = ctx.get_tune()
     if tune:
-        ctx.set_tune(A.april_tune(*tune, 0, 0.0))
+        ctx.set_tune(A.april_tune(*tune[:4], 0, 0.0, tune[4] if len(tune) > 4 else 0))
     try:
         def fn(d_r, d_s, out, n):
             sb = ctx.scratch_bytes(m, n)
@@ -123,8 +124,9 @@ def test_random_lists_equal_host(torch_cuda, ctx, data, mode, tune):
     assert len(bad) == 0, (len(bad), bad[:10])
 
 
+@pytest.mark.parametrize("join_order", [0, 1])
 @pytest.mark.parametrize("which", ["within", "coarser S", "coarser R"])
-def test_random_lists_variants_equal_host(torch_cuda, ctx, data, which):
+def test_random_lists_variants_equal_host(torch_cuda, ctx, data, which, join_order):
     torch = torch_cuda
     R, S, S14, pr, ps = data
     if which == "within":
@@ -138,7 +140,7 @@ def test_random_lists_variants_equal_host(torch_cuda, ctx, data, which):
     dX, dY = A.april_upload(X), A.april_upload(Y)
     for long_window in (64, 256):
         saved = ctx.get_tune()
-        ctx.set_tune(A.april_tune(1024, saved.group_lanes, saved.group_window, long_window, 0, 0.0))
+        ctx.set_tune(A.april_tune(1024, saved.group_lanes, saved.group_window, long_window, 0, 0.0, join_order))
         try:
             def fn(d_r, d_s, out, n):
                 scratch = torch.empty(ctx.scratch_bytes(A.MODE_BATCHED, n), dtype=torch.uint8, device="cuda")
@@ -150,7 +152,8 @@ def test_random_lists_variants_equal_host(torch_cuda, ctx, data, which):
         assert len(bad) == 0, (which, long_window, len(bad), bad[:10])
 
 
-@pytest.mark.parametrize("tune", [None, (2048, 4, 16, 64), (0, 8, 8, 64), (512, 16, 128, 256), (0xFFFFFFFF, 32, 64, 256)])
+@pytest.mark.parametrize("tune", [None, (2048, 4, 16, 64), (0, 8, 8, 64), (512, 16, 128, 256), (0xFFFFFFFF, 32, 64, 256),
+                                  (2048, 4, 16, 64, 1)])
 def test_random_lists_packed_equal_host(torch_cuda, ctx, data, tune):
     """The compressed form of random lists (per-block uint16/uint32 gaps)
     filters to the same verdicts as the host over the raw lists, with lane
@@ -169,7 +172,7 @@ def test_random_lists_packed_equal_host(torch_cuda, ctx, data, tune):
         ctx.april_filter_pairs(dR, dS, d_r, d_s, n, out, A.MODE_BATCHED_PACKED, scratch)
     saved = ctx.get_tune()
     if tune:
-        ctx.set_tune(A.april_tune(*tune, 0, 0.0))
+        ctx.set_tune(A.april_tune(*tune[:4], 0, 0.0, tune[4] if len(tune) > 4 else 0))
     try:
         got = _run(torch, ctx, dR, dS, pr, ps, fn)
     finally:
