@@ -303,9 +303,11 @@ __global__ void __launch_bounds__(256) k_bin(SetsT R, SetsT S, const uint32_t *_
 // One pass of the loop below advances every group's current join by one
 // window, so the fixed cost of a window step (staging, the per-thread merge-
 // path search, the vote) is shared by 32/G joins.  When a group finishes its
-// pair it takes the next one from the 32-pair chunk the warp holds in its
-// lanes; the warp pops a new chunk from a global counter when the chunk is
-// used up.  Pairs above the CTA threshold are skipped here (phase 1 did them).
+// pair it takes the next one from the warp's current chunk of 32 pairs, whose
+// eligible pairs are listed compacted in shared memory (a group takes the
+// entry at the list's cursor plus its rank among the groups asking); the warp
+// pops a new chunk from a global counter when the list is used up.  Pairs above the
+// CTA threshold are skipped here (phase 1 did them).
 template <uint32_t G>
 struct GroupCfg {
     static constexpr uint32_t NG = 32 / G;
@@ -390,8 +392,8 @@ template <uint32_t G, class SetsT>
 __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, const uint32_t *__restrict__ pr,
                                              const uint32_t *__restrict__ ps, uint64_t n, uint8_t *__restrict__ out,
                                              uint32_t *status, uint32_t *counters, uint32_t cta_threshold, uint2 *wbuf,
-                                             uint4 *chunk_desc, uint32_t bars, uint32_t lane, uint32_t w0,
-                                             uint32_t jo) {
+                                             uint4 *chunk_desc, uint8_t *chunk_lane, uint32_t bars, uint32_t lane,
+                                             uint32_t w0, uint32_t jo) {
     using C = GroupCfg<G>;
     const uint32_t g = lane / G, t = lane % G, glead = g * G;
     const uint32_t gbits = (G == 32 ? kFull : ((1u << G) - 1u)) << glead;
@@ -400,10 +402,11 @@ __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, con
     uint32_t phase = 0;
     const uint64_t nchunks = (n + 31) / 32;
     // the warp's chunk of 32 pairs from pair `base`: pair base + l has its two
-    // descriptors in chunk_desc[l] and chunk_desc[32 + l]; bit l of `avail`
-    // says it is still to be handed out
+    // descriptors in chunk_desc[l] and chunk_desc[32 + l]; chunk_lane lists
+    // the lanes of the eligible pairs in order, and its entries
+    // [cur, cur + left) are still to be handed out
     uint32_t base = 0;
-    uint32_t avail = 0;
+    uint32_t cur = 0, left = 0;
     bool exhausted = false;
     // this group's pair and join
     bool active = false;
@@ -418,7 +421,7 @@ __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, con
         // -------- hand pairs to idle groups
         uint32_t needg = __ballot_sync(kFull, !active) & C::LEADS;
         while (needg && !exhausted) {
-            if (!avail) {
+            if (!left) {
                 uint32_t c = 0;
                 if (lane == 0) c = atomicAdd(&counters[C_CHUNK_HEAD], 1u);
                 c = __shfl_sync(kFull, c, 0);
@@ -439,15 +442,18 @@ __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, con
                         take = (uint64_t)qdr.y + qds.y <= (uint64_t)cta_threshold;
                     }
                 }
-                avail = __ballot_sync(kFull, take);
+                const uint32_t tb = __ballot_sync(kFull, take);
+                if (take) chunk_lane[__popc(tb & ((1u << lane) - 1u))] = (uint8_t)lane;
+                cur = 0;
+                left = __popc(tb);
                 __syncwarp();
                 continue;
             }
-            const uint32_t cnt = min((uint32_t)__popc(needg), (uint32_t)__popc(avail));
+            const uint32_t cnt = min((uint32_t)__popc(needg), left);
             const uint32_t grank = __popc(needg & ((1u << glead) - 1u));
             const bool gets = ((needg >> glead) & 1u) && grank < cnt;
             if (gets) {
-                const uint32_t src = __fns(avail, 0, (int)grank + 1);
+                const uint32_t src = chunk_lane[cur + grank];
                 k = base + src;
                 dr = chunk_desc[src];
                 ds = chunk_desc[32 + src];
@@ -461,8 +467,8 @@ __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, con
                 active = verdict < 0;
                 if (!active && t == 0) out[k] = (uint8_t)verdict;
             }
-            const uint32_t lastbit = __fns(avail, 0, (int)cnt);
-            avail &= (lastbit >= 31) ? 0u : ~((2u << lastbit) - 1u);
+            cur += cnt;
+            left -= cnt;
             needg = __ballot_sync(kFull, !active) & C::LEADS;
         }
         if (!__any_sync(kFull, active)) break;  // only reachable once the pairs are exhausted
@@ -546,10 +552,10 @@ __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, con
     }
 }
 
-// Phase 1: each CTA pops long pairs and joins each with all its warps (the
-// merge path of one join split over 256 threads).  Phase 2: the group engine
-// on the short pairs.  Work is handed out by atomic counters; nothing waits
-// on another CTA.
+// Phase 1: the long pairs, each joined by one warp (first window below 256)
+// or by the whole CTA (the merge path of one join split over 256 threads).
+// Phase 2: the group engine on the short pairs (whole warps when G = 32).
+// Work is handed out by atomic counters; nothing waits on another CTA.
 template <uint32_t G, class SetsT>
 __global__ void APRIL_PERSISTENT_BOUNDS k_persistent(SetsT R, SetsT S,
                                                                          const uint32_t *__restrict__ pr,
@@ -563,7 +569,8 @@ __global__ void APRIL_PERSISTENT_BOUNDS k_persistent(SetsT R, SetsT S,
     // mbarriers: [0] the CTA phase, [1 + warp * 8 + group] the group engine,
     // [1 + 8 * 8 + warp] long pairs joined by warps
     __shared__ uint64_t bars[1 + kWarpsPerBlock * 9];
-    __shared__ uint4 s_chunk[kWarpsPerBlock][64];  // group engine: each warp's chunk descriptors
+    __shared__ uint4 s_chunk[kWarpsPerBlock][64];     // group engine: each warp's chunk descriptors
+    __shared__ uint8_t s_chunk_lane[kWarpsPerBlock][32];  // and the chunk lanes they came from
     init_barriers(bars, 1 + kWarpsPerBlock * 9);
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const uint32_t nbig = *((volatile uint32_t *)&counters[C_BIG_COUNT]);
@@ -581,12 +588,14 @@ __global__ void APRIL_PERSISTENT_BOUNDS k_persistent(SetsT R, SetsT S,
             const typename SetsT::Desc dr = R.load(__ldg(pr + k)), ds = S.load(__ldg(ps + k));
             const uint8_t v = warp_verdict(R, S, dr, ds, wbuf, wbuf + kWarpBuf, lane, w0_cta, ws, jo);
             if (lane == 0) out[k] = v;
-            if (ws.timeout) break;
+            if (ws.timeout) {  // a bounded wait ran out: report and stop this warp
+                if (lane == 0) atomicOr(status, ST_TIMEOUT);
+                return;
+            }
         }
-        const bool dead = ws.timeout;
-        if (dead && lane == 0) atomicOr(status, ST_TIMEOUT);
-        __syncthreads();
-        if (dead) return;  // a bounded wait ran out: this warp stops (after the CTA's only barrier)
+        // no CTA barrier here: the warp's phase-2 buffers and mbarriers are
+        // its own, so it starts on short pairs while its CTA's other warps
+        // still join long ones
     } else {
         JoinSync cs{smem_addr(&bars[0]), 0u, false};
         for (;;) {
@@ -620,8 +629,7 @@ __global__ void APRIL_PERSISTENT_BOUNDS k_persistent(SetsT R, SetsT S,
         }
     } else {
         group_engine<G>(R, S, pr, ps, n, out, status, counters, cta_threshold, wbuf, s_chunk[warp],
-                        smem_addr(&bars[1 + warp * 8]),
-                        lane, w0_group, jo);
+                        s_chunk_lane[warp], smem_addr(&bars[1 + warp * 8]), lane, w0_group, jo);
     }
 }
 
