@@ -273,6 +273,12 @@ typedef struct april_tune {
 april_status april_set_tune(april_ctx *ctx, const april_tune *tune);
 april_status april_get_tune(const april_ctx *ctx, april_tune *tune);
 
+/* Counts of the batched pipeline's CUDA graph on this context since its
+ * creation: captures (one for every new argument set or tuning) and launches
+ * (one per APRIL_MODE_BATCHED / BATCHED_PACKED call).  Either pointer may be
+ * NULL.  Host-only; no device work. */
+april_status april_ctx_graph_stats(const april_ctx *ctx, uint64_t *captures, uint64_t *launches);
+
 /* Times APRIL_MODE_BATCHED on the given pairs (typically a sample of the
  * workload) for a grid of candidate tunings, keeps the
  * fastest in the context, and returns it in *out (candidates: cta_threshold in

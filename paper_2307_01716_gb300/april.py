@@ -107,6 +107,7 @@ SIGNATURES = {
     "april_upload": (_st, [_vp, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(april_dev_sets)]),
     "april_ctx_create": (_st, [ctypes.c_int, ctypes.POINTER(_vp)]),
     "april_ctx_destroy": (None, [_vp]),
+    "april_ctx_graph_stats": (_st, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     "april_filter_scratch_bytes": (_st, [ctypes.c_int, _u64, ctypes.POINTER(ctypes.c_size_t)]),
     "april_filter_pairs": (_st, [_vp, ctypes.POINTER(april_dev_sets), ctypes.POINTER(april_dev_sets), _vp, _vp,
                                  _u64, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
@@ -505,6 +506,12 @@ class Context:
         return check(load().april_filter_pairs_host(self.handle, ctypes.byref(R.c), ctypes.byref(S.c), _ptr(h_r),
                                                     _ptr(h_s), n, _ptr(h_verdict), mode, _ptr(work),
                                                     int(work.numel()), st.cuda_stream))
+
+    def april_ctx_graph_stats(self):
+        """(captures, launches) of the batched pipeline's CUDA graph."""
+        c, l = ctypes.c_uint64(), ctypes.c_uint64()
+        check(load().april_ctx_graph_stats(self.handle, ctypes.byref(c), ctypes.byref(l)))
+        return c.value, l.value
 
     def april_sync_status(self, stream=None) -> int:
         import torch

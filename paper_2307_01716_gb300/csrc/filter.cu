@@ -813,7 +813,7 @@ struct GraphKey {
                sn == o.sn && d_r == o.d_r && d_s == o.d_s && out == o.out && scratch == o.scratch && n == o.n &&
                tune.cta_threshold == o.tune.cta_threshold && tune.group_lanes == o.tune.group_lanes &&
                tune.group_window == o.tune.group_window && tune.cta_window == o.tune.cta_window &&
-               grid_bin == o.grid_bin && grid_main == o.grid_main;
+               tune.join_order == o.tune.join_order && grid_bin == o.grid_bin && grid_main == o.grid_main;
     }
 };
 
@@ -922,6 +922,13 @@ extern "C" april_status april_set_tune(april_ctx *ctx, const april_tune *t) {
     april_status st = check_tune(*t);
     if (st) return st;
     ctx->tune = *t;
+    return APRIL_OK;
+}
+
+extern "C" april_status april_ctx_graph_stats(const april_ctx *ctx, uint64_t *captures, uint64_t *launches) {
+    if (!ctx) return fail(APRIL_ERR_INVALID_ARG, "NULL context");
+    if (captures) *captures = ctx->graph_captures;
+    if (launches) *launches = ctx->graph_launches;
     return APRIL_OK;
 }
 

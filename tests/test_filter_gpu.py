@@ -177,6 +177,46 @@ def test_autotune_then_batched(torch_cuda, ctx):
         ctx.set_tune(saved)
 
 
+def test_graph_recaptured_on_every_tuning_change(torch_cuda, ctx):
+    """The batched pipeline's graph is replayed for the same arguments and
+    tuning, and captured again when any knob changes, the join order alone
+    included (the replayed kernels would otherwise keep the old order)."""
+    torch = torch_cuda
+    w = _data.workload(1, 1.0)
+    _, _, dR, dS = _device_sets(w)
+    n = len(w.pr)
+    d_r = torch.from_numpy(w.pr.view(np.int32)).cuda()
+    d_s = torch.from_numpy(w.ps.view(np.int32)).cuda()
+    out = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    scratch = torch.empty(ctx.scratch_bytes(A.MODE_BATCHED, n), dtype=torch.uint8, device="cuda")
+    saved = ctx.get_tune()
+    want = _data.oracle_verdicts(1, 1.0)
+
+    def run():
+        out.fill_(0xEE)
+        ctx.april_filter_pairs(dR, dS, d_r, d_s, n, out, A.MODE_BATCHED, scratch)
+        ctx.april_sync_status()
+        assert np.array_equal(out.cpu().numpy(), want)
+        return ctx.april_ctx_graph_stats()
+
+    try:
+        steps = [A.april_tune(2048, 4, 16, 64, 0, 0.0, 0), A.april_tune(2048, 4, 16, 64, 0, 0.0, 0),
+                 A.april_tune(2048, 4, 16, 64, 0, 0.0, 1), A.april_tune(2048, 4, 16, 64, 0, 0.0, 1),
+                 A.april_tune(2048, 8, 16, 64, 0, 0.0, 1), A.april_tune(2048, 8, 16, 256, 0, 0.0, 1)]
+        ctx.set_tune(steps[0])
+        c0, l0 = run()
+        recaptured = []
+        for t in steps[1:]:
+            ctx.set_tune(t)
+            c, l = run()
+            assert l == l0 + 1
+            recaptured.append(c - c0)
+            c0, l0 = c, l
+        assert recaptured == [0, 1, 0, 1, 1]
+    finally:
+        ctx.set_tune(saved)
+
+
 def test_tune_validation(ctx):
     for bad in [(100, 6, 8, 256), (100, 8, 4, 256), (100, 8, 128, 256), (100, 8, 24, 256), (100, 32, 64, 4096),
                 (100, 8, 32, 16), (100, 8, 32, 96)]:

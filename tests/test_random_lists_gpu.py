@@ -98,7 +98,7 @@ def _run(torch, ctx, dR, dS, pr, ps, fn):
 
 
 @pytest.mark.parametrize("mode,tune", [("plain", None), ("warp", None), ("warp", (2048, 4, 16, 64, 1)),
-                                       ("batched", (2048, 4, 16, 64)), ("batched", (0, 8, 32, 64)),
+                                       ("batched", None), ("batched", (2048, 4, 16, 64)), ("batched", (0, 8, 32, 64)),
                                        ("batched", (64, 16, 32, 256)), ("batched", (0xFFFFFFFF, 32, 64, 256)),
                                        ("batched", (512, 4, 4, 2048)), ("batched", (2048, 4, 16, 64, 1)),
                                        ("batched", (0, 8, 32, 256, 1)), ("batched", (0xFFFFFFFF, 16, 32, 64, 1))])
