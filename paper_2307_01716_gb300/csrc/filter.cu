@@ -340,19 +340,27 @@ __device__ __forceinline__ bool join_lists(const SetsT &R, const SetsT &S, const
 // counts the probes below the key (a prefix, the keys being sorted), which
 // leaves one gap of the spacing; the keys themselves are loaded with the
 // first round's probes, whose positions do not depend on them.  Only lists
-// longer than a first window (w0) are searched.
+// longer than a first window (w0) are searched.  Over raw lists the search
+// stops once an open range holds at most kSearchSlack probe spacings of keys:
+// the join then starts at the range's lower end, which is a valid start too
+// (every interval before it ends before the other list's first start), and
+// the merge passes over the few intervals up to the exact start itself; that
+// costs less than the search rounds it saves.  Over compressed lists a key
+// stands for a 16-interval block, so their search runs to the end.
 constexpr uint32_t kSearchProbes = 1;
+constexpr uint32_t kSearchSlack = 2;
 template <uint32_t G, class ListT>
 __device__ __forceinline__ void dual_search(const ListT &X, const ListT &Y, bool need, uint32_t w0, uint32_t t,
                                             uint32_t gbits, uint32_t &i0, uint32_t &j0) {
     constexpr uint32_t P = kSearchProbes, F = G * P;
+    constexpr uint32_t SLACK = ListT::kRandomAccess ? kSearchSlack * F : 0u;
     const uint32_t nX = X.n, nY = Y.n;
     uint32_t loX = 0, hiX = (need && nX > w0) ? X.keys_n() : 0;
     uint32_t loY = 0, hiY = (need && nY > w0) ? Y.keys_n() : 0;
     uint32_t kx = 0, ky = 0;  // Y's first start (X's key), X's first start (Y's key)
     bool first = true;
-    while (__any_sync(kFull, loX < hiX || loY < hiY)) {
-        const bool ax = loX < hiX, ay = loY < hiY;
+    while (__any_sync(kFull, hiX - loX > SLACK || hiY - loY > SLACK)) {  // lo <= hi throughout
+        const bool ax = hiX - loX > SLACK, ay = hiY - loY > SLACK;
         const uint32_t sX = ax ? (hiX - loX + F - 1) / F : 1, sY = ay ? (hiY - loY + F - 1) / F : 1;
         uint32_t vX[P], vY[P];
 #pragma unroll
