@@ -596,7 +596,9 @@ april_status april_host_filter(const april_sets *R, const april_sets *S, const u
  * verdicts equal april_host_filter's.  consumed[k] counts, for every join
  * that ran, the intervals the merge reads from the start positions plus the
  * search's probes (the bit width of each list's length): the bytes model of
- * the kernels' reading, used for their roofline. */
+ * the kernels' reading, used for their roofline.  (The kernels' lane groups
+ * over raw lists end their search up to two probe spacings early and start
+ * that many intervals sooner; the verdicts are the same.) */
 april_status april_host_filter_searched(const april_sets *R, const april_sets *S, const uint32_t *pr,
                                         const uint32_t *ps, uint64_t n, uint32_t n_threads, uint8_t *verdict,
                                         uint64_t *consumed);

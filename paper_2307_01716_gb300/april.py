@@ -600,7 +600,7 @@ def april_host_filter_ex(R: Sets, S: Sets, pr: np.ndarray, ps: np.ndarray, predi
 
 def april_host_filter(R: Sets, S: Sets, pr: np.ndarray, ps: np.ndarray, n_threads: int = 0, searched: bool = False):
     """Host Algorithm 2 over built sets: (verdicts, consumed intervals).
-    searched=True starts every join where the GPU kernels start it
+    searched=True starts every join at the searched start the GPU kernels look for
     (april_host_filter_searched: same verdicts, the kernels' reading model)."""
     pr = np.ascontiguousarray(pr, dtype=np.uint32)
     ps = np.ascontiguousarray(ps, dtype=np.uint32)

@@ -763,11 +763,12 @@ bool host_join(const uint32_t *X, uint32_t nx, const uint32_t *Y, uint32_t ny, u
     return false;
 }
 
-// The same join started where the GPU kernels start it: each list at its
-// first interval whose last cell reaches the other list's first start (the
-// merge from the front would pass over the intervals before it without a
-// verdict).  *used counts the intervals the merge reads from there plus a
-// binary search per list (bit width of its length, in probed intervals).
+// The same join started at the searched start the GPU kernels look for: each
+// list at its first interval whose last cell reaches the other list's first
+// start (the merge from the front would pass over the intervals before it
+// without a verdict).  *used counts the intervals the merge reads from there
+// plus a binary search per list (bit width of its length, in probed
+// intervals).
 uint32_t lower_bound_last(const uint32_t *L, uint32_t n, uint32_t t) {
     uint32_t lo = 0, hi = n;
     while (lo < hi) {
