@@ -245,7 +245,10 @@ typedef struct april_ctx april_ctx;
 
 /* Creates a filter context on CUDA device `device`.  The context owns a
  * 256-byte device status block (allocated here with cudaMalloc) that kernels
- * use to report out-of-range ids and exhausted waits. */
+ * use to report out-of-range ids and exhausted waits.  A context is used by
+ * one host thread at a time: the filter calls update its captured graph and
+ * april_set_tune / april_autotune its tuning, without locks.  Threads that
+ * filter concurrently each create their own context. */
 april_status april_ctx_create(int device, april_ctx **out);
 void april_ctx_destroy(april_ctx *ctx);
 
@@ -403,7 +406,10 @@ typedef struct april_server_info {
 /* Creates a server for sets R and S (already uploaded; they stay resident).
  * d_arena/arena_bytes: caller-allocated device memory (256-byte aligned) that
  * bounds all request buffers: a request of n pairs needs about 21 n bytes.
- * max_inflight: 1..64 stream slots.  The context must outlive the server. */
+ * max_inflight: 1..64 stream slots.  The context must outlive the server,
+ * and while the server runs its worker thread reads the context's tuning:
+ * leave that context to the server (no april_set_tune, april_autotune or
+ * filter calls on it) and filter elsewhere through another context. */
 april_status april_server_create(april_ctx *ctx, const april_dev_sets *R, const april_dev_sets *S, void *d_arena,
                                  size_t arena_bytes, uint32_t max_inflight, april_server **out);
 

@@ -400,7 +400,8 @@ STATUS_OVER_BUDGET = -3
 
 
 class Context:
-    """april_ctx: device status block and kernel dispatch."""
+    """april_ctx: device status block and kernel dispatch.  One host thread
+    at a time (its captured graph and tuning are unguarded)."""
 
     def __init__(self, device: int = 0):
         h = _vp()
