@@ -74,14 +74,15 @@ def _cleanup(xy: np.ndarray, off: np.ndarray, cen: np.ndarray):
     """Drop duplicates and angular-order violations (vectorised over polygons).
 
     One pass over all polygons, then repeated passes over only the polygons
-    that still changed.
+    that still changed: a polygon's mask depends on its own vertices alone,
+    so one that had nothing to drop in a pass keeps its vertices for good.
     """
     drop, seg = _bad_mask(xy, off, cen)
     if not drop.any():
         return xy, off
     touched = np.unique(seg[drop])
     xy, off = _compact(xy, off, ~drop)
-    # iterate on the affected polygons only
+    # iterate on the affected polygons only, retiring each once it is stable
     counts = np.diff(off)
     sub_cnt = counts[touched]
     sub_off = np.zeros(len(touched) + 1, dtype=np.int64)
@@ -89,12 +90,40 @@ def _cleanup(xy: np.ndarray, off: np.ndarray, cen: np.ndarray):
     gather = np.repeat(off[touched] - sub_off[:-1], sub_cnt) + np.arange(int(sub_off[-1]))
     sub_xy = xy[gather]
     sub_cen = cen[touched]
+    ids = touched
+    done_ids, done_cnt, done_xy = [], [], []
     for _ in range(256):
-        d, _s = _bad_mask(sub_xy, sub_off, sub_cen)
+        d, s = _bad_mask(sub_xy, sub_off, sub_cen)
         if not d.any():
             break
-        sub_xy, sub_off = _compact(sub_xy, sub_off, ~d)
-    counts[touched] = np.diff(sub_off)
+        changing = np.zeros(len(ids), dtype=bool)
+        changing[np.unique(s[d])] = True
+        keep_v = changing[s]
+        cnt = np.diff(sub_off)
+        if not changing.all():
+            done_ids.append(ids[~changing])
+            done_cnt.append(cnt[~changing])
+            done_xy.append(sub_xy[~keep_v])
+        ch_off = np.zeros(int(changing.sum()) + 1, dtype=np.int64)
+        np.cumsum(cnt[changing], out=ch_off[1:])
+        sub_xy, sub_off = _compact(sub_xy[keep_v], ch_off, ~d[keep_v])
+        ids = ids[changing]
+        sub_cen = sub_cen[changing]
+    done_ids.append(ids)
+    done_cnt.append(np.diff(sub_off))
+    done_xy.append(sub_xy)
+    all_ids = np.concatenate(done_ids)
+    all_cnt = np.concatenate(done_cnt)
+    all_xy = np.concatenate(done_xy)
+    # the retired polygons back in id order
+    order = np.argsort(all_ids, kind="stable")
+    src_off = np.zeros(len(all_cnt) + 1, dtype=np.int64)
+    np.cumsum(all_cnt, out=src_off[1:])
+    dst_cnt = all_cnt[order]
+    dst_off = np.zeros(len(dst_cnt) + 1, dtype=np.int64)
+    np.cumsum(dst_cnt, out=dst_off[1:])
+    sub_xy = all_xy[np.repeat(src_off[:-1][order] - dst_off[:-1], dst_cnt) + np.arange(int(dst_off[-1]))]
+    counts[all_ids[order]] = dst_cnt
     new_off = np.zeros(len(off), dtype=np.int64)
     np.cumsum(counts, out=new_off[1:])
     new_xy = np.empty((int(new_off[-1]), 2), dtype=np.int64)
