@@ -15,8 +15,9 @@ CUDA path.  The product path must never import this package.
     partition each pair is evaluated in (Sec. 5.2), per the readings stated
     in the functions.
 
-Parity status: cell classes, verdicts, Hilbert order and intervalization are
-pinned by tests (closed forms, brute force, invariants).  The figure-based
+Parity status: cell classes, verdicts, Hilbert order, intervalization and the
+partition raster areas are pinned by tests (closed forms, brute force,
+invariants, hand-computed minimal squares).  The figure-based
 worked examples of Sec. 3.2 and Sec. 6.2 are parity unpinned: their polygons
 exist only in figures that are missing from the paper's text.
 """
@@ -141,20 +142,39 @@ def cells(poly: np.ndarray, grid: Grid):
     return A, F
 
 
-def verdicts(R_xy, R_off, S_xy, S_off, pr, ps, grid: Grid) -> np.ndarray:
-    """Per-pair verdicts (0 true negative, 1 true hit, 2 inconclusive)."""
-    rxy = np.ascontiguousarray(R_xy, dtype=np.int64).reshape(-1)
-    sxy = np.ascontiguousarray(S_xy, dtype=np.int64).reshape(-1)
-    roff = np.ascontiguousarray(R_off, dtype=np.int64)
-    soff = np.ascontiguousarray(S_off, dtype=np.int64)
-    pr = np.ascontiguousarray(pr, dtype=np.uint32)
-    ps = np.ascontiguousarray(ps, dtype=np.uint32)
+def _serial_verdicts(rxy, roff, sxy, soff, pr, ps, grid: Grid) -> np.ndarray:
     out = np.zeros(len(pr), dtype=np.uint8)
     rc = lib().oracle_verdicts(_p64(rxy), _p64(roff), _p64(sxy), _p64(soff), pr.ctypes.data, ps.ctypes.data,
                                len(pr), *grid.args(), out.ctypes.data)
     if rc != 0:
         raise RuntimeError(f"oracle_verdicts failed ({rc})")
     return out
+
+
+def _in_chunks(fn, pr, ps, threads: int, min_chunk: int = 16) -> np.ndarray:
+    """fn over contiguous chunks of the pairs on `threads` host threads (the
+    C calls release the GIL); every pair is still computed on its own by the
+    same plain code, so the result does not depend on the chunking."""
+    n = len(pr)
+    if threads <= 1 or n <= min_chunk:
+        return fn(pr, ps)
+    from concurrent.futures import ThreadPoolExecutor
+    bounds = np.linspace(0, n, min(4 * threads, n // min_chunk) + 1).astype(np.int64)
+    with ThreadPoolExecutor(threads) as ex:
+        parts = list(ex.map(lambda ab: fn(pr[ab[0]:ab[1]], ps[ab[0]:ab[1]]), zip(bounds[:-1], bounds[1:])))
+    return np.concatenate(parts)
+
+
+def verdicts(R_xy, R_off, S_xy, S_off, pr, ps, grid: Grid, threads: int = 1) -> np.ndarray:
+    """Per-pair verdicts (0 true negative, 1 true hit, 2 inconclusive);
+    `threads` > 1 evaluates contiguous chunks of the pairs concurrently."""
+    rxy = np.ascontiguousarray(R_xy, dtype=np.int64).reshape(-1)
+    sxy = np.ascontiguousarray(S_xy, dtype=np.int64).reshape(-1)
+    roff = np.ascontiguousarray(R_off, dtype=np.int64)
+    soff = np.ascontiguousarray(S_off, dtype=np.int64)
+    pr = np.ascontiguousarray(pr, dtype=np.uint32)
+    ps = np.ascontiguousarray(ps, dtype=np.uint32)
+    return _in_chunks(lambda a, b: _serial_verdicts(rxy, roff, sxy, soff, a, b, grid), pr, ps, threads)
 
 
 INTERSECTS = 0
@@ -298,7 +318,8 @@ def route_pairs(mbr_r: np.ndarray, mbr_s: np.ndarray, pr, ps, parts: int) -> np.
     return partition_of_point(np.maximum(mr[:, 0], ms[:, 0]), np.maximum(mr[:, 1], ms[:, 1]), parts)
 
 
-def partitioned_verdicts(R_xy, R_off, mbr_r, S_xy, S_off, mbr_s, pr, ps, parts: int, order: int):
+def partitioned_verdicts(R_xy, R_off, mbr_r, S_xy, S_off, mbr_s, pr, ps, parts: int, order: int,
+                         threads: int = 1):
     """Verdicts of the partitioned filter: each pair on its routed partition's grid."""
     grids = partition_areas(mbr_r, mbr_s, parts, order)
     part = route_pairs(mbr_r, mbr_s, pr, ps, parts)
@@ -307,5 +328,5 @@ def partitioned_verdicts(R_xy, R_off, mbr_r, S_xy, S_off, mbr_s, pr, ps, parts: 
     ps = np.asarray(ps)
     for p in np.unique(part):
         sel = np.nonzero(part == p)[0]
-        out[sel] = verdicts(R_xy, R_off, S_xy, S_off, pr[sel], ps[sel], grids[int(p)])
+        out[sel] = verdicts(R_xy, R_off, S_xy, S_off, pr[sel], ps[sel], grids[int(p)], threads)
     return out

@@ -330,3 +330,58 @@ def test_partition_areas_cover_members():
     met_s = oracle.partitions_met(w.S.mbr, 16)
     for k in range(len(w.pr)):
         assert part[k] in met_r[w.pr[k]] and part[k] in met_s[w.ps[k]]
+
+
+def _smallest_area_brute(lo, hi, order):
+    """Reading C11 enumerated: the smallest power-of-two side 2^k (cell side
+    2^k >> order of at least 2) such that SOME origin that is a multiple of
+    the cell side, at or below the MBR's lower corner, covers the closed MBR;
+    among the origins that work at that side, the largest (the snap of the
+    lower corner down to the cell lattice)."""
+    for k in range(order + 1, 26):
+        size = 1 << k
+        h = size >> order
+        ok = []
+        for ox in range(0, lo[0] + 1, h):
+            for oy in range(0, lo[1] + 1, h):
+                if ox + size >= hi[0] and oy + size >= hi[1]:
+                    ok.append((ox, oy))
+        if ok:
+            return size, max(o[0] for o in ok), max(o[1] for o in ok)
+    raise AssertionError("no area")
+
+
+@pytest.mark.parametrize("lo,hi,order,size,origin", [
+    # a 4x4 grid (order 2): cell side 2 at side 8
+    ((0, 0), (8, 8), 2, 8, (0, 0)),      # exactly 2^3 lattice units: side 8
+    ((0, 0), (9, 8), 2, 16, (0, 0)),     # one unit wider: must step to 2^4
+    ((5, 5), (12, 12), 2, 8, (4, 4)),    # origin snaps down to the cell lattice (4), 4 + 8 reaches 12
+    ((5, 5), (13, 12), 2, 16, (4, 4)),   # 4 + 8 misses 13: side 16 with cell side 4, origin 4
+    ((7, 3), (14, 10), 2, 8, (6, 2)),    # snaps to (6, 2) at cell side 2; 6 + 8 and 2 + 8 just reach
+    ((7, 3), (15, 10), 2, 16, (4, 0)),   # one unit wider: side 16, cell side 4, origin (4, 0)
+    ((100, 36), (224, 160), 3, 128, (96, 32)),  # order 3: cell side 16 at side 128
+    ((100, 36), (225, 160), 3, 256, (96, 32)),  # one unit wider in x: side 256, cell side 32
+])
+def test_partition_areas_minimal_square(lo, hi, order, size, origin):
+    """partition_areas picks the smallest admissible square (reading C11),
+    pinned by hand-computed cases and by brute force over all origins."""
+    mbr_r = np.array([[lo[0], lo[1], hi[0], hi[1]]], dtype=np.int64)
+    mbr_s = np.array([[lo[0], lo[1], lo[0], lo[1]]], dtype=np.int64)  # a point inside: does not grow the MBR
+    g = oracle.partition_areas(mbr_r, mbr_s, 1, order)[0]
+    assert (g.h * g.G, g.ox, g.oy) == (size, origin[0], origin[1])
+    assert (size, origin[0], origin[1]) == _smallest_area_brute(lo, hi, order)
+
+
+def test_partition_areas_minimal_square_random():
+    """Brute force on random small MBRs of two objects (one partition)."""
+    rng = np.random.default_rng(5)
+    for _ in range(300):
+        order = int(rng.integers(1, 4))
+        a = rng.integers(0, 300, 4)
+        b = rng.integers(0, 300, 4)
+        ma = [min(a[0], a[2]), min(a[1], a[3]), max(a[0], a[2]), max(a[1], a[3])]
+        mb = [min(b[0], b[2]), min(b[1], b[3]), max(b[0], b[2]), max(b[1], b[3])]
+        g = oracle.partition_areas(np.array([ma]), np.array([mb]), 1, order)[0]
+        lo = (min(ma[0], mb[0]), min(ma[1], mb[1]))
+        hi = (max(ma[2], mb[2]), max(ma[3], mb[3]))
+        assert (g.h * g.G, g.ox, g.oy) == _smallest_area_brute(lo, hi, order)
