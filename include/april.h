@@ -450,23 +450,55 @@ void april_server_destroy(april_server *server);
  * serving loop, a plugin whose host owns all allocations).  It runs the same
  * computation as april_filter_pairs(..., APRIL_MODE_BATCHED, ...) with the
  * default tuning, but without a context and without caller scratch: its
- * scratch is a static device array inside libapril (16 MiB + 256 bytes),
+ * scratch is a static device array inside libapril (16 MiB + 512 bytes),
  * which every GPU that loads the library holds until the process exits.
  *
  *   R, S, d_r, d_s, n, d_verdict, stream: as for april_filter_pairs.
  *
  * It allocates nothing: no cudaMalloc, no cudaFree, no allocating library
- * call.  The first call on a device (with that device current) looks up the
- * array's device address and the launch shape; make that first call before
- * any stream capture.  All calls share the one array and each call clears
- * its counters first: calls whose work overlaps on the GPU (several streams
- * or host threads) race and must be serialized by the caller.
- * Out-of-range ids give APRIL_VERDICT_ERROR verdicts (there is no context to
- * report them to).  n larger than APRIL_NOALLOC_MAX_PAIRS is rejected with
- * APRIL_ERR_INVALID_ARG.  Asynchronous on `stream`. */
+ * call.  The first call on a device (with that device current) loads the
+ * library's kernel module if nothing else has, which commits the array's
+ * device memory, and queries the launch shape: make that first call as a
+ * warm-up, outside the latency-bound path and before any stream capture.
+ * The array's device address is looked up on every call (cudaGetSymbolAddress,
+ * which does not allocate).  All calls share the one array and each call
+ * clears its counters first: calls whose work overlaps on the GPU (several
+ * streams or host threads) race and must be serialized by the caller.
+ * Out-of-range ids give APRIL_VERDICT_ERROR verdicts.  Device errors (bad
+ * ids, a bounded wait that ran out) are recorded in the array's status word,
+ * which keeps them across calls until april_noalloc_sync_status reads it.
+ * After a timeout the verdicts of the pairs the stopped warps held read
+ * APRIL_VERDICT_ERROR and pairs no warp reached keep their old contents:
+ * treat every verdict of the calls since the last status query as invalid.
+ * n larger than APRIL_NOALLOC_MAX_PAIRS is rejected with APRIL_ERR_INVALID_ARG.
+ * Asynchronous on `stream`. */
 #define APRIL_NOALLOC_MAX_PAIRS 4194304u
 april_status april_filter_pairs_noalloc(const april_dev_sets *R, const april_dev_sets *S, const uint32_t *d_r,
                                         const uint32_t *d_s, uint64_t n, uint8_t *d_verdict, void *stream);
+
+/* The paper has no counterpart; the status query of april_filter_pairs_noalloc
+ * on the current device, for the same callers (it allocates nothing either).
+ * Synchronizes `stream`, reads the status word of the static array and
+ * clears it.  Returns APRIL_OK, APRIL_ERR_DEVICE_TIMEOUT (a bounded device
+ * wait ran out in one of the calls since the last query) or
+ * APRIL_ERR_OUT_OF_RANGE_ID (a pair named an out-of-range id), or
+ * APRIL_ERR_CUDA. */
+april_status april_noalloc_sync_status(void *stream);
+
+/* ------------------------------------------------- diagnostics */
+
+/* The paper has no counterpart; a diagnostic for the error path of the
+ * filter kernels.  Every wait of a filter kernel for its window copies gives
+ * up after `spins` polls of its mbarrier (default APRIL_WAIT_LIMIT_DEFAULT);
+ * the kernel then waits (with the default limit) for the copies in flight,
+ * marks the pairs it held as APRIL_VERDICT_ERROR, records
+ * APRIL_ERR_DEVICE_TIMEOUT in the status word and stops.  spins = 0 makes
+ * every such wait give up at once, so the timeout path can be run without
+ * any fault.  Applies to the current device, to every context and to the
+ * allocation-free entry point, until set again; set it only while no filter
+ * kernel runs.  Synchronous.  Returns APRIL_OK or APRIL_ERR_CUDA. */
+#define APRIL_WAIT_LIMIT_DEFAULT 16777216u
+april_status april_debug_set_wait_limit(uint32_t spins);
 
 /* ------------------------------------------------- construction on the GPU */
 

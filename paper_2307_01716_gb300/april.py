@@ -152,6 +152,8 @@ SIGNATURES = {
                                      ctypes.POINTER(ctypes.POINTER(ctypes.c_uint8)), ctypes.POINTER(_u32)]),
     "april_filter_pairs_noalloc": (_st, [ctypes.POINTER(april_dev_sets), ctypes.POINTER(april_dev_sets), _vp, _vp,
                                          _u64, _vp, _vp]),
+    "april_noalloc_sync_status": (_st, [_vp]),
+    "april_debug_set_wait_limit": (_st, [_u32]),
     "april_set_tune": (_st, [_vp, ctypes.POINTER(april_tune)]),
     "april_get_tune": (_st, [_vp, ctypes.POINTER(april_tune)]),
     "april_autotune": (_st, [_vp, ctypes.POINTER(april_dev_sets), ctypes.POINTER(april_dev_sets), _vp, _vp, _u64,
@@ -586,6 +588,23 @@ def april_filter_pairs_noalloc(R: DevSets, S: DevSets, d_r, d_s, n: int, d_verdi
     st = stream if stream is not None else torch.cuda.current_stream()
     check(load().april_filter_pairs_noalloc(ctypes.byref(R.c), ctypes.byref(S.c), _ptr(d_r), _ptr(d_s), n,
                                             _ptr(d_verdict), st.cuda_stream))
+
+
+def april_noalloc_sync_status(stream=None) -> None:
+    """Reads and clears the allocation-free entry point's status word on the
+    current device; raises AprilError for a timeout or an out-of-range id."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    check(load().april_noalloc_sync_status(st.cuda_stream))
+
+
+WAIT_LIMIT_DEFAULT = 16777216
+
+
+def april_debug_set_wait_limit(spins: int) -> None:
+    """Diagnostic: the poll limit of the filter kernels' bounded waits on the
+    current device (0: every wait gives up at once)."""
+    check(load().april_debug_set_wait_limit(spins))
 
 
 def april_host_filter_ex(R: Sets, S: Sets, pr: np.ndarray, ps: np.ndarray, predicate: int, n_threads: int = 0):

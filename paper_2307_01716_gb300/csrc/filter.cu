@@ -42,6 +42,7 @@ namespace {
 // status bits in the context's device status block
 constexpr uint32_t ST_BAD_ID = 1u;
 constexpr uint32_t ST_TIMEOUT = 2u;
+static_assert(kMbarSpinLimit == APRIL_WAIT_LIMIT_DEFAULT, "the documented default wait limit");
 
 constexpr uint32_t kBlock = 256;                 // threads per CTA for K1/K3
 constexpr uint32_t kWarpsPerBlock = kBlock / 32;
@@ -228,8 +229,9 @@ __device__ __forceinline__ bool warp_chunk(const SetsT &R, const SetsT &S, const
         const typename SetsT::Desc a = SetsT::shfl(dr, t), b = SetsT::shfl(ds, t);
         const uint8_t v = warp_verdict(R, S, a, b, xs, ys, lane, w0, js, jo);
         if (lane == t) mine = v;
-        if (js.timeout) {
+        if (js.timeout) {  // the pairs of the chunk not decided yet read as errors
             if (lane == 0) atomicOr(status, ST_TIMEOUT);
+            if (take) out[k] = (lane == t || ((todo >> lane) & 1u)) ? (uint8_t)APRIL_VERDICT_ERROR : mine;
             return false;
         }
     }
@@ -518,7 +520,13 @@ __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, con
             ya = Y.window(yb, j0);
         }
         if constexpr (!ListT::kBulk) __syncwarp();  // the decoded windows are visible to the group
-        if (!__all_sync(kFull, ok)) {  // a bounded wait ran out: report and stop this warp
+        if (!__all_sync(kFull, ok)) {
+            // a bounded wait ran out: once the copies in flight have landed
+            // (bounded), mark the pairs this warp holds as errors, report
+            // and stop this warp
+            if (!ok) mbar_drain(bar, phase ^ 1u);
+            if (active && t == 0) out[k] = APRIL_VERDICT_ERROR;
+            if (lane < left) out[base + chunk_lane[cur + lane]] = APRIL_VERDICT_ERROR;
             if (lane == 0) atomicOr(status, ST_TIMEOUT);
             return;
         }
@@ -753,8 +761,9 @@ __global__ void __launch_bounds__(kBlock) k_general(Plan P, DevSet Rd, DevSet Sd
             const uint8_t v = plan_verdict<WarpScope, 32, kWarpWMax>(P, R, S, shfl4(dr, t), shfl4(ds, t), xs, ys,
                                                                       nullptr, lane, 64u, js);
             if (lane == t) mine = v;
-            if (js.timeout) {
+            if (js.timeout) {  // the pairs of the chunk not decided yet read as errors
                 if (lane == 0) atomicOr(status, ST_TIMEOUT);
+                if (take) out[k] = (lane == t || ((todo >> lane) & 1u)) ? (uint8_t)APRIL_VERDICT_ERROR : mine;
                 return;
             }
         }
@@ -1397,18 +1406,19 @@ extern "C" april_status april_sync_status(april_ctx *ctx, void *stream) {
 // every allocation) -- the batched filter can run with its scratch in this
 // file-scope device array instead of caller memory.  The array is part of
 // the loaded module, so every GPU that loads libapril holds it (16 MiB +
-// 256 bytes) until the process exits.  Layout: the batched pipeline's
-// 256-byte counter block (word kNoAllocStatusWord holds the device status),
-// then the list of long pairs, one uint32 per pair.
+// 512 bytes) until the process exits.  Layout: the batched pipeline's
+// 256-byte counter block (cleared by every call), a 256-byte status block
+// (word 0: the ST_* bits of every call since the last status query), then
+// the list of long pairs, one uint32 per pair.
 constexpr uint64_t kNoAllocMaxPairs = 4ull << 20;
-constexpr uint32_t kNoAllocStatusWord = 8;
-static __device__ __align__(256) uint32_t g_noalloc_scratch[kCounterBytes / 4 + kNoAllocMaxPairs];
+constexpr uint32_t kNoAllocStatusWord = kCounterBytes / 4;
+constexpr uint32_t kNoAllocListWord = 2 * kCounterBytes / 4;
+static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocListWord + kNoAllocMaxPairs];
 
 namespace {
 
 struct NoAllocDevice {
     bool ready = false;
-    uint32_t *scratch = nullptr;  // device address of g_noalloc_scratch on this device
     int num_sms = 0;
     int blocks_per_sm = 1;
 };
@@ -1430,6 +1440,16 @@ static PersistentRaw noalloc_kernel(uint32_t group_lanes) {
     }
 }
 
+// Device address of g_noalloc_scratch on the current device.  Host code
+// cannot use the array's name as an address (it names a host-side stand-in),
+// so the address is looked up on every call (no allocation; after the first
+// call on a device the module is loaded and the lookup is cheap).
+static april_status noalloc_scratch(uint32_t **ptr) {
+    cudaError_t e = cudaGetSymbolAddress((void **)ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    return APRIL_OK;
+}
+
 extern "C" april_status april_filter_pairs_noalloc(const april_dev_sets *R, const april_dev_sets *S,
                                                    const uint32_t *d_r, const uint32_t *d_s, uint64_t n,
                                                    uint8_t *d_verdict, void *stream) {
@@ -1446,22 +1466,21 @@ extern "C" april_status april_filter_pairs_noalloc(const april_dev_sets *R, cons
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(APRIL_ERR_INVALID_ARG, "device index out of range");
     const april_tune t = default_tune();
+    uint32_t *scratch = nullptr;
+    april_status rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
     NoAllocDevice nd;
     {
-        // first call on this device: resolve the array's device address and
-        // the launch shape (the current device is the one being set up)
+        // first call on this device: the launch shape (the current device is
+        // the one being set up)
         std::lock_guard<std::mutex> lock(g_noalloc_mu);
         NoAllocDevice &slot = g_noalloc_dev[dev];
         if (!slot.ready) {
-            uint32_t *ptr = nullptr;
-            e = cudaGetSymbolAddress((void **)&ptr, g_noalloc_scratch);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
             int sms = 0, bps = 0;
             e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             if (e == cudaSuccess)
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, noalloc_kernel(t.group_lanes), kBlock, 0);
             if (e != cudaSuccess) return cuda_fail(e, "april_filter_pairs_noalloc set-up");
-            slot.scratch = ptr;
             slot.num_sms = sms;
             slot.blocks_per_sm = bps < 1 ? 1 : bps;
             slot.ready = true;
@@ -1469,10 +1488,11 @@ extern "C" april_status april_filter_pairs_noalloc(const april_dev_sets *R, cons
         nd = slot;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    uint32_t *counters = nd.scratch;
-    uint32_t *status = counters + kNoAllocStatusWord;
-    uint32_t *big_list = counters + kCounterBytes / 4;
-    // the array keeps the previous call's contents: reset counters and status
+    uint32_t *counters = scratch;
+    uint32_t *status = scratch + kNoAllocStatusWord;
+    uint32_t *big_list = scratch + kNoAllocListWord;
+    // the array keeps the previous call's contents: reset the counters (the
+    // status block keeps its bits until april_noalloc_sync_status reads them)
     e = cudaMemsetAsync(counters, 0, kCounterBytes, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(no-alloc counters)");
     const RawSets dR{dev_set(R)}, dS{dev_set(S)};
@@ -1484,5 +1504,32 @@ extern "C" april_status april_filter_pairs_noalloc(const april_dev_sets *R, cons
                                                                 t.cta_window, t.join_order);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "april_filter_pairs_noalloc launch");
+    return APRIL_OK;
+}
+
+extern "C" april_status april_noalloc_sync_status(void *stream) {
+    uint32_t *scratch = nullptr;
+    april_status rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t h = 0;  // pageable: the copy has completed when the call returns
+    cudaError_t e = cudaMemcpyAsync(&h, scratch + kNoAllocStatusWord, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "april_noalloc_sync_status");
+    if (h) {
+        e = cudaMemsetAsync(scratch + kNoAllocStatusWord, 0, 4, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "april_noalloc_sync_status(clear)");
+    }
+    if (h & ST_TIMEOUT) return fail(APRIL_ERR_DEVICE_TIMEOUT, "a bounded device wait ran out");
+    if (h & ST_BAD_ID) return fail(APRIL_ERR_OUT_OF_RANGE_ID, "a pair named an out-of-range object id");
+    return APRIL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostic: the iteration limit of the filter kernels' bounded waits.
+extern "C" april_status april_debug_set_wait_limit(uint32_t spins) {
+    cudaError_t e = cudaMemcpyToSymbol(c_wait_limit, &spins, sizeof(spins));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyToSymbol(c_wait_limit)");
     return APRIL_OK;
 }

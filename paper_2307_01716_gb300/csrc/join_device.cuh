@@ -268,11 +268,24 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
 }
 
 // Spins on the mbarrier phase with an iteration limit; false if it ran out.
+// The limit of the waits for window copies is c_wait_limit (default
+// kMbarSpinLimit; a diagnostic setter lowers it, down to 0 = give up at once,
+// so that the timeout path can run without any fault).  After a wait gave
+// up, the copies it waited for may still be in flight: mbar_drain waits for
+// them with the fixed limit kMbarDrainLimit before the join returns, so that
+// no copy lands in shared memory the block no longer owns.
 constexpr uint32_t kMbarSpinLimit = 1u << 24;
+constexpr uint32_t kMbarDrainLimit = 1u << 24;
+__constant__ uint32_t c_wait_limit = kMbarSpinLimit;
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
-    for (uint32_t k = 0; k < kMbarSpinLimit; ++k)
+    const uint32_t lim = c_wait_limit;
+    for (uint32_t k = 0; k < lim; ++k)
         if (mbar_try_wait(bar, phase)) return true;
     return false;
+}
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t phase) {
+    for (uint32_t k = 0; k < kMbarDrainLimit; ++k)
+        if (mbar_try_wait(bar, phase)) return;
 }
 
 // Window staging by bulk copy: the 16-byte aligned span around src[0..cnt)
@@ -472,11 +485,13 @@ __device__ __noinline__ bool tile_join(const ListT X, const ListT Y, uint2 *xb, 
                 Y.issue(yb, j0, ny, bar);
             }
             const bool ok = Scope::all(mbar_wait(bar, *phase));
-            *phase ^= 1u;
-            if (!ok) {
+            if (!ok) {  // give up, once this window's copies have landed (bounded)
+                mbar_drain(bar, *phase);
+                *phase ^= 1u;
                 *timeout = true;
                 return false;
             }
+            *phase ^= 1u;
             xa = X.window(xb, i0);
             ya = Y.window(yb, j0);
         } else {
