@@ -177,6 +177,15 @@ april_status april_sets_object_entries(const april_sets *sets, uint32_t obj, uin
 /* Partition id and grid of an entry of partitioned sets. */
 april_status april_sets_entry_grid(const april_sets *sets, uint32_t entry, uint32_t *pid, april_grid *grid);
 
+/* The entries each candidate pair is evaluated on (host call; Sec. 5.2): for
+ * sets on one global grid the objects themselves; for partitioned sets the
+ * two objects' entries for the partition that holds the lower-left corner of
+ * MBR(r) n MBR(s), the partition april_filter_pairs routes the pair to.
+ * er[k], es[k] receive the entries of pair k (caller-owned host arrays of n),
+ * or UINT32_MAX for an out-of-range id.  R and S must be on the same grid. */
+april_status april_route_pairs(const april_sets *R, const april_sets *S, const uint32_t *pr, const uint32_t *ps,
+                               uint64_t n, uint32_t *er, uint32_t *es);
+
 /* Builds partitioned sets for both join inputs (Sec. 5.2, "Partitioning").
  * The data space [0, 2^24]^2 is split into parts x parts equal partitions
  * (parts a power of two, 1..4096).  Each polygon gets one approximation (an
@@ -288,8 +297,10 @@ april_status april_ctx_graph_stats(const april_ctx *ctx, uint64_t *captures, uin
  * {2048, 4096, 8192, 16384, none} x (group_lanes, group_window) in
  * {(4,8), (4,16), (8,16), (8,32), (16,32), (16,64), (32,64)} x long pairs by a
  * warp (cta_window 64) or by the CTA (the context's cta_window if >= 256, else
- * 256) x join_order in {0, 1}).  Arguments as for april_filter_pairs;
- * synchronizes `stream`. */
+ * 256) x join_order in {0, 1}).  The context's current tuning is timed
+ * first and is kept unless a candidate is more than 2% faster, so that
+ * repeated runs settle on the same tuning.  Arguments as for
+ * april_filter_pairs; synchronizes `stream`. */
 april_status april_autotune(april_ctx *ctx, const april_dev_sets *R, const april_dev_sets *S,
                             const uint32_t *d_r, const uint32_t *d_s, uint64_t n, uint8_t *d_verdict,
                             void *d_scratch, size_t scratch_bytes, void *stream, april_tune *out);

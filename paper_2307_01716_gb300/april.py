@@ -121,6 +121,7 @@ SIGNATURES = {
                                     _u64, _vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
     "april_host_filter_ex": (_st, [_vp, _vp, _vp, _vp, _u64, ctypes.c_int, _u32, _vp, _vp]),
     "april_sets_lengths": (_st, [_vp, _vp, _vp]),
+    "april_route_pairs": (_st, [_vp, _vp, _vp, _vp, _u64, _vp, _vp]),
     "april_quantize_polygons": (_st, [_vp, _vp, _u32, _vp, _vp]),
     "april_build_sets_device": (_st, [_vp, _vp, _vp, _u32, ctypes.POINTER(april_grid), _vp, ctypes.c_size_t, _vp,
                                       ctypes.c_size_t, ctypes.POINTER(april_dev_sets),
@@ -605,6 +606,17 @@ def april_debug_set_wait_limit(spins: int) -> None:
     """Diagnostic: the poll limit of the filter kernels' bounded waits on the
     current device (0: every wait gives up at once)."""
     check(load().april_debug_set_wait_limit(spins))
+
+
+def april_route_pairs(R: Sets, S: Sets, pr: np.ndarray, ps: np.ndarray):
+    """The entries each pair is evaluated on (partitioned sets: the partition
+    of the lower-left corner of MBR(r) n MBR(s)); two uint32 arrays."""
+    pr = np.ascontiguousarray(pr, dtype=np.uint32)
+    ps = np.ascontiguousarray(ps, dtype=np.uint32)
+    er = np.zeros(len(pr), dtype=np.uint32)
+    es = np.zeros(len(pr), dtype=np.uint32)
+    check(load().april_route_pairs(R.handle, S.handle, _ptr(pr), _ptr(ps), len(pr), _ptr(er), _ptr(es)))
+    return er, es
 
 
 def april_host_filter_ex(R: Sets, S: Sets, pr: np.ndarray, ps: np.ndarray, predicate: int, n_threads: int = 0):

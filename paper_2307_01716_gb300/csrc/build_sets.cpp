@@ -808,26 +808,49 @@ static uint32_t find_entry(const april_sets *S, uint32_t obj, uint32_t pid) {
     return 0xffffffffu;
 }
 
+// The entries a pair (r, s) is evaluated on: the objects themselves on one
+// global grid; for partitioned sets (Sec. 5.2) their entries for the
+// partition of the lower-left corner of MBR(r) n MBR(s).  An out-of-range id
+// or a missing entry gives UINT32_MAX.
+static void route_pair(const april_sets *R, const april_sets *S, uint32_t &r, uint32_t &s) {
+    if (r >= R->n || s >= S->n) {
+        r = s = 0xffffffffu;
+        return;
+    }
+    if (!R->parts) return;
+    const int64_t side = ((int64_t)1 << 24) / R->parts;
+    const int64_t x = std::max(R->obj_ll[2 * (size_t)r], S->obj_ll[2 * (size_t)s]);
+    const int64_t y = std::max(R->obj_ll[2 * (size_t)r + 1], S->obj_ll[2 * (size_t)s + 1]);
+    const int64_t P = R->parts;
+    const uint32_t pid = (uint32_t)(std::min(y / side, P - 1) * P + std::min(x / side, P - 1));
+    r = find_entry(R, r, pid);
+    s = find_entry(S, s, pid);
+}
+
+extern "C" april_status april_route_pairs(const april_sets *R, const april_sets *S, const uint32_t *pr,
+                                          const uint32_t *ps, uint64_t n, uint32_t *er, uint32_t *es) {
+    if (!R || !S || (n && (!pr || !ps || !er || !es))) return fail(APRIL_ERR_INVALID_ARG, "NULL argument");
+    if (R->parts != S->parts || R->order != S->order) return fail(APRIL_ERR_INVALID_ARG, "R and S use different grids");
+    for (uint64_t k = 0; k < n; ++k) {
+        uint32_t r = pr[k], s = ps[k];
+        route_pair(R, S, r, s);
+        er[k] = r;
+        es[k] = s;
+    }
+    return APRIL_OK;
+}
+
 static april_status host_filter(const april_sets *R, const april_sets *S, const uint32_t *pr, const uint32_t *ps,
                                 uint64_t n, uint32_t n_threads, uint8_t *verdict, uint64_t *consumed, bool searched) {
     auto join = searched ? host_join_searched : host_join;
     if (!R || !S || (n && (!pr || !ps || !verdict))) return fail(APRIL_ERR_INVALID_ARG, "NULL argument");
     if (R->parts != S->parts || R->order != S->order) return fail(APRIL_ERR_INVALID_ARG, "R and S use different grids");
-    const int64_t side = R->parts ? ((int64_t)1 << 24) / R->parts : 0;
     parallel_for(n, resolve_threads(n_threads), 4096, [&](uint32_t, uint64_t b, uint64_t e) {
         for (uint64_t k = b; k < e; ++k) {
             uint32_t r = pr[k], s = ps[k];
             uint64_t used = 0;
             uint8_t v;
-            if (r < R->n && s < S->n && R->parts) {
-                // evaluate the pair in the partition of the lower-left corner of MBR(r) n MBR(s)
-                const int64_t x = std::max(R->obj_ll[2 * (size_t)r], S->obj_ll[2 * (size_t)s]);
-                const int64_t y = std::max(R->obj_ll[2 * (size_t)r + 1], S->obj_ll[2 * (size_t)s + 1]);
-                const int64_t P = R->parts;
-                const uint32_t pid = (uint32_t)(std::min(y / side, P - 1) * P + std::min(x / side, P - 1));
-                r = find_entry(R, r, pid);
-                s = find_entry(S, s, pid);
-            }
+            route_pair(R, S, r, s);
             if (r >= R->n_entries || s >= S->n_entries) {
                 v = APRIL_VERDICT_ERROR;
             } else {

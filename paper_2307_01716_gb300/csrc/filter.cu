@@ -1294,9 +1294,33 @@ extern "C" april_status april_autotune(april_ctx *ctx, const april_dev_sets *R, 
     if (e == cudaSuccess) e = cudaEventCreate(&b);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
     april_status rc = APRIL_OK;
+    // times tuning t on the sample (best of three replays after the capture)
+    auto time_tune = [&](const april_tune &t, float &best_here) -> april_status {
+        ctx->tune = t;
+        best_here = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+            cudaError_t e2 = cudaEventRecord(a, st);
+            if (e2 != cudaSuccess) return cuda_fail(e2, "cudaEventRecord");
+            april_status r2 = april_filter_pairs(ctx, R, S, d_r, d_s, n, d_verdict, APRIL_MODE_BATCHED, d_scratch,
+                                                 scratch_bytes, stream);
+            if (r2) return r2;
+            e2 = cudaEventRecord(b, st);
+            if (e2 == cudaSuccess) e2 = cudaEventSynchronize(b);
+            float ms = 0.f;
+            if (e2 == cudaSuccess) e2 = cudaEventElapsedTime(&ms, a, b);
+            if (e2 != cudaSuccess) return cuda_fail(e2, "timing an autotune candidate");
+            if (rep > 0) best_here = std::min(best_here, ms);  // rep 0 captures the graph
+        }
+        return APRIL_OK;
+    };
+    // the context's tuning first: a candidate replaces it only if it is more
+    // than 2% faster, so that the pick does not flip between shapes whose
+    // times differ by noise
+    float saved_ms = 1e30f;
+    rc = time_tune(saved, saved_ms);
     // long pairs joined by one warp (first window 64) or by the whole CTA
     const uint32_t long_windows[] = {64u, saved.cta_window >= kBlock ? saved.cta_window : kBlock};
-    for (uint32_t jo = 0; jo < 2; ++jo)
+    for (uint32_t jo = 0; jo < 2 && rc == APRIL_OK; ++jo)
     for (uint32_t T : thresholds) {
         for (const auto &gw : groups)
         for (const uint32_t lw : long_windows) {
@@ -1307,21 +1331,8 @@ extern "C" april_status april_autotune(april_ctx *ctx, const april_dev_sets *R, 
             t.group_window = gw[1];
             t.cta_window = lw;
             t.join_order = jo;
-            ctx->tune = t;
             float best_here = 1e30f;
-            for (int rep = 0; rep < 3 && rc == APRIL_OK; ++rep) {
-                e = cudaEventRecord(a, st);
-                if (e != cudaSuccess) { rc = cuda_fail(e, "cudaEventRecord"); break; }
-                rc = april_filter_pairs(ctx, R, S, d_r, d_s, n, d_verdict, APRIL_MODE_BATCHED, d_scratch,
-                                        scratch_bytes, stream);
-                if (rc) break;
-                e = cudaEventRecord(b, st);
-                if (e == cudaSuccess) e = cudaEventSynchronize(b);
-                float ms = 0.f;
-                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-                if (e != cudaSuccess) { rc = cuda_fail(e, "timing an autotune candidate"); break; }
-                if (rep > 0) best_here = std::min(best_here, ms);  // rep 0 captures the graph
-            }
+            rc = time_tune(t, best_here);
             if (rc) break;
             if (best_here < best_ms) {
                 best_ms = best_here;
@@ -1329,6 +1340,10 @@ extern "C" april_status april_autotune(april_ctx *ctx, const april_dev_sets *R, 
             }
         }
         if (rc) break;
+    }
+    if (rc == APRIL_OK && saved_ms <= 1.02f * best_ms) {
+        best = saved;
+        best_ms = saved_ms;
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);

@@ -55,6 +55,20 @@ def gather_verdicts(local: np.ndarray, shards: list[tuple[int, int]], rank: int,
     return None
 
 
+def sharded_filter(cost: np.ndarray, world: int, rank: int, run_shard, group=None):
+    """The multi-rank filter of one pair list: split the pairs into `world`
+    contiguous shards of about equal cost, run run_shard(lo, hi) -> this
+    rank's verdicts of pairs [lo, hi), and gather every rank's verdicts to
+    rank 0.  Returns (shards, all verdicts on rank 0 / None elsewhere); with
+    one rank, (the one shard, its verdicts)."""
+    shards = balanced_shards(cost, world)
+    lo, hi = shards[rank]
+    local = np.asarray(run_shard(lo, hi), dtype=np.uint8)
+    if len(local) != hi - lo:
+        raise ValueError("run_shard returned the wrong number of verdicts")
+    return shards, gather_verdicts(local, shards, rank, world, group)
+
+
 def max_over_ranks(x: float, world: int, device=None, group=None) -> float:
     """The maximum of a scalar over ranks (step times: the job is as slow as its slowest rank)."""
     import torch

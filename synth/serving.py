@@ -23,6 +23,7 @@ GRID_BITS = 11  # reference points are counted on a 2048 x 2048 histogram
 class Request:
     pr: np.ndarray    # uint32 object ids into R
     ps: np.ndarray    # uint32 object ids into S
+    idx: np.ndarray   # positions of these pairs in the workload's candidate list
     arrival: float    # seconds after the start of the stream
     window: tuple     # (cx0, cy0, cx1, cy1) histogram cells, inclusive
 
@@ -64,7 +65,7 @@ class RequestMaker:
     def pairs_in(self, w):
         m = (self.cx >= w[0]) & (self.cx <= w[2]) & (self.cy >= w[1]) & (self.cy <= w[3])
         idx = np.nonzero(m)[0]
-        return self.pr[idx], self.ps[idx]
+        return self.pr[idx], self.ps[idx], idx
 
     def requests(self, seed: int, count: int, rate: float, lo: int = 1_000, hi: int = 2_000_000):
         """`count` requests with log-uniform size targets in [lo, hi] (capped
@@ -78,6 +79,6 @@ class RequestMaker:
         for t, at in zip(targets, arrivals):
             k = int(rng.integers(0, len(self.pr)))
             w = self.window_for(k, int(t))
-            pr, ps = self.pairs_in(w)
-            out.append(Request(pr=pr, ps=ps, arrival=float(at), window=w))
+            pr, ps, idx = self.pairs_in(w)
+            out.append(Request(pr=pr, ps=ps, idx=idx, arrival=float(at), window=w))
         return out

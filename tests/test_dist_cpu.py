@@ -1,7 +1,10 @@
-"""The multi-rank path on CPU: two gloo ranks shard the candidate pairs by
-estimated cost, each runs Algorithm 2 on its shard (host execution over the
-same built sets), and rank 0's gathered verdicts equal the single-process
-result; the max-over-ranks reduction returns the slowest rank's time."""
+"""The multi-rank path on CPU: two gloo ranks run dist.sharded_filter, the
+function bench.py's multi-rank run uses -- the candidate pairs split by
+estimated cost, each rank's shard filtered (here by Algorithm 2 on the host
+over the same built sets, where the bench runs the GPU filter), the verdicts
+gathered to rank 0 -- and rank 0's gathered verdicts equal the
+single-process result; the max-over-ranks reduction returns the slowest
+rank's time."""
 import os
 import socket
 
@@ -46,14 +49,17 @@ def _rank(rank, world, port, q):
         a_r, _ = R.lengths()
         a_s, _ = S.lengths()
         assert a_r.tolist() == [R.list(i, 0).shape[0] for i in range(w.R.n)]
-        shards = D.balanced_shards(D.pair_cost(a_r, a_s, w.pr, w.ps), world)
-        lo, hi = shards[rank]
-        v, _ = A.april_host_filter(R, S, w.pr[lo:hi], w.ps[lo:hi], n_threads=1)
-        allv = D.gather_verdicts(v, shards, rank, world)
+        def run_shard(lo, hi):
+            return A.april_host_filter(R, S, w.pr[lo:hi], w.ps[lo:hi], n_threads=1)[0]
+
+        shards, allv = D.sharded_filter(D.pair_cost(a_r, a_s, w.pr, w.ps), world, rank, run_shard)
+        assert shards[0][0] == 0 and shards[-1][1] == len(w.pr) and shards[0][1] == shards[1][0]
         t = D.max_over_ranks(float(rank + 1), world)
         if rank == 0:
             full, _ = A.april_host_filter(R, S, w.pr, w.ps, n_threads=1)
             q.put((bool(np.array_equal(allv, full)), t, len(allv)))
+        else:
+            assert allv is None
     finally:
         dist.destroy_process_group()
 

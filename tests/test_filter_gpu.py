@@ -3,9 +3,10 @@
 Verdicts are integers, so the bar is bit-exact equality with the oracle's
 cell-set verdicts.  Sizes: config 1 in full; configs 2 and 3 at reduced
 polygon counts (lists span many 32-interval windows and end in ragged
-tails); config 2 at full size in the benchmark's launch configuration,
-checked on a seeded sample of pairs the oracle computes one by one; and edge
-cases (no pairs, one pair, out-of-range ids, the last Hilbert cell)."""
+tails); configs 2 and 3 at full size in the benchmark's launch
+configuration, checked on seeded samples of pairs the oracle computes one by
+one (for config 3, long pairs included); and edge cases (no pairs, one pair,
+out-of-range ids, the last Hilbert cell)."""
 import numpy as np
 import pytest
 
@@ -131,6 +132,29 @@ def test_full_size_config2_sampled(torch_cuda, ctx, full_config2, mode):
     # every verdict agrees with the host execution of Algorithm 2 on the same lists
     hv, _ = A.april_host_filter(R, S, w.pr, w.ps)
     assert np.array_equal(got, hv)
+
+
+def test_full_size_config3_sampled(torch_cuda, ctx):
+    """The skewed workload at full size (340k + 340k polygons, 10M pairs,
+    lists up to ~10^5 intervals) in the batched mode with the default tuning,
+    as the benchmark runs it: every verdict equals host Algorithm 2, and a
+    seeded oracle sample of 1,000 pairs -- 200 of them long pairs
+    (|A(r)| + |A(s)| above the long-pair threshold, joined by whole warps) --
+    equals the oracle."""
+    w = _data.workload(3, 1.0)
+    R, S, dR, dS = _device_sets(w)
+    t = ctx.get_tune()
+    got = run_filter(torch_cuda, ctx, dR, dS, w.pr, w.ps, "batched")
+    hv, _ = A.april_host_filter(R, S, w.pr, w.ps)
+    assert np.array_equal(got, hv), np.nonzero(got != hv)[0][:10]
+    a_r, _ = R.lengths()
+    a_s, _ = S.lengths()
+    cost = a_r[w.pr].astype(np.int64) + a_s[w.ps]
+    rng = np.random.default_rng(31)
+    long_idx = rng.choice(np.nonzero(cost > t.cta_threshold)[0], 200, replace=False)
+    short_idx = rng.choice(np.nonzero(cost <= t.cta_threshold)[0], 800, replace=False)
+    idx = np.sort(np.concatenate([long_idx, short_idx]))
+    assert np.array_equal(got[idx], _data.oracle_sample(w, idx))
 
 
 @pytest.mark.parametrize("long_window", [32, 128, 256, 2048])

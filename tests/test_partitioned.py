@@ -116,3 +116,24 @@ def test_codec_round_trip_global_grid_with_wide_gaps_and_last_cell():
 def test_partitioned_errors():
     with pytest.raises(A.AprilError):
         A.april_build_partitioned_sets(np.zeros((3, 2)), [0, 3], np.zeros((3, 2)), [0, 3], 3, 14)
+
+
+def test_route_pairs_equals_oracle_routing(cfg4):
+    """april_route_pairs names, for every pair, each object's entry for the
+    partition the oracle routes the pair to; on one global grid the objects
+    themselves; out-of-range ids give UINT32_MAX."""
+    w, R, S = cfg4
+    er, es = A.april_route_pairs(R, S, w.pr, w.ps)
+    part = oracle.route_pairs(w.R.mbr, w.S.mbr, w.pr, w.ps, 16)
+    for k in range(len(w.pr)):
+        assert R.entry_grid(int(er[k]))[0] == part[k] and S.entry_grid(int(es[k]))[0] == part[k]
+        fr, cr = R.entries(int(w.pr[k]))
+        fs, cs = S.entries(int(w.ps[k]))
+        assert fr <= er[k] < fr + cr and fs <= es[k] < fs + cs
+    g = A.global_grid(w.order)
+    Rg = A.april_build_sets(w.R.xy, w.R.off, g)
+    Sg = A.april_build_sets(w.S.xy, w.S.off, g)
+    pr = np.array([0, 1, w.R.n], dtype=np.uint32)
+    ps = np.array([2, 3, 0], dtype=np.uint32)
+    er, es = A.april_route_pairs(Rg, Sg, pr, ps)
+    assert er.tolist() == [0, 1, 0xFFFFFFFF] and es.tolist() == [2, 3, 0xFFFFFFFF]
