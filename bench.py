@@ -724,12 +724,14 @@ def parse_tune(A, spec):
     return A.april_tune(T, G, W, CW, 0, 0.0, vals[4] if len(vals) > 4 else 0)
 
 
-def run_leg(A, torch, ctx, dev, stream, flush, cfg, args, mode, peak, peak_kind, ws=1, rank=0, barrier=None,
-            gloo=None):
+def run_leg(A, torch, ctx, dev, stream, flush, cfg, args, mode, peak, peak_kind, default_tune, ws=1, rank=0,
+            barrier=None, gloo=None):
     """One workload: the timed mode, the modes it is compared with, the
-    autotuner's pick, end to end, the roofline and the parity checks."""
+    autotuner's pick, end to end, the roofline and the parity checks; the
+    context starts from default_tune (the library default)."""
     from paper_2307_01716_gb300 import dist as D
     L = Leg(A, torch, ctx, dev, stream, flush, cfg, pack=(mode == "packed"))
+    ctx.set_tune(default_tune)  # earlier legs may have autotuned the context
     if args.tune:
         ctx.set_tune(parse_tune(A, args.tune))
     res = {"workload": L.w.name, "pairs": int(L.n_all), "polygons_per_side": int(L.w.R.n), "grid_order": L.w.order,
@@ -815,6 +817,7 @@ def main():
     if args.selection_build:
         return selection_build_only(A, torch, dev)
     ctx = A.Context(local)
+    default_tune = ctx.get_tune()
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     mode = args.mode
@@ -834,8 +837,8 @@ def main():
     barrier = dist.barrier if ws > 1 else None
     clocks = Clocks()
     clocks.start()
-    L, head, _ = run_leg(A, torch, ctx, dev, stream, flush, args.config, args, mode, peak, peak_kind, ws, rank,
-                         barrier, gloo)
+    L, head, _ = run_leg(A, torch, ctx, dev, stream, flush, args.config, args, mode, peak, peak_kind, default_tune,
+                         ws, rank, barrier, gloo)
     clk = clocks.stop(local)
     roof = head["roofline"]
     line = {
@@ -880,7 +883,8 @@ def main():
         line["workloads"] = {}
         for cfg in EXTRA_WORKLOADS:
             torch.cuda.empty_cache()
-            Lx, res, _ = run_leg(A, torch, ctx, dev, stream, flush, cfg, args, "batched", peak, peak_kind)
+            Lx, res, _ = run_leg(A, torch, ctx, dev, stream, flush, cfg, args, "batched", peak, peak_kind,
+                                 default_tune)
             if not args.no_cpu_baseline:
                 res["cpu_baseline"] = cpu_baseline(Lx.w, Lx.cost, ctx.get_tune().cta_threshold,
                                                    Lx.out[:Lx.n].cpu().numpy(), *ORACLE_SAMPLE[cfg])

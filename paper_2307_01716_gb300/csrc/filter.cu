@@ -349,16 +349,24 @@ __device__ __forceinline__ bool join_lists(const SetsT &R, const SetsT &S, const
 // the merge passes over the few intervals up to the exact start itself; that
 // costs less than the search rounds it saves.  Over compressed lists a key
 // stands for a 16-interval block, so their search runs to the end.
+#ifndef APRIL_SEARCH_SLACK
+#define APRIL_SEARCH_SLACK 2
+#endif
+#ifndef APRIL_SEARCH_MIN
+#define APRIL_SEARCH_MIN 0
+#endif
 constexpr uint32_t kSearchProbes = 1;
-constexpr uint32_t kSearchSlack = 2;
+constexpr uint32_t kSearchSlack = APRIL_SEARCH_SLACK;
+constexpr uint32_t kSearchMin = APRIL_SEARCH_MIN;  // lists up to this long are not searched
 template <uint32_t G, class ListT>
 __device__ __forceinline__ void dual_search(const ListT &X, const ListT &Y, bool need, uint32_t w0, uint32_t t,
                                             uint32_t gbits, uint32_t &i0, uint32_t &j0) {
     constexpr uint32_t P = kSearchProbes, F = G * P;
     constexpr uint32_t SLACK = ListT::kRandomAccess ? kSearchSlack * F : 0u;
     const uint32_t nX = X.n, nY = Y.n;
-    uint32_t loX = 0, hiX = (need && nX > w0) ? X.keys_n() : 0;
-    uint32_t loY = 0, hiY = (need && nY > w0) ? Y.keys_n() : 0;
+    const uint32_t smin = max(w0, kSearchMin);
+    uint32_t loX = 0, hiX = (need && nX > smin) ? X.keys_n() : 0;
+    uint32_t loY = 0, hiY = (need && nY > smin) ? Y.keys_n() : 0;
     uint32_t kx = 0, ky = 0;  // Y's first start (X's key), X's first start (Y's key)
     bool first = true;
     while (__any_sync(kFull, hiX - loX > SLACK || hiY - loY > SLACK)) {  // lo <= hi throughout
@@ -394,8 +402,8 @@ __device__ __forceinline__ void dual_search(const ListT &X, const ListT &Y, bool
             loY += cY * sY;
         }
     }
-    if (need && nX > w0) i0 = X.start_of(loX);
-    if (need && nY > w0) j0 = Y.start_of(loY);
+    if (need && nX > smin) i0 = X.start_of(loX);
+    if (need && nY > smin) j0 = Y.start_of(loY);
 }
 
 template <uint32_t G, class SetsT>
