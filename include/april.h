@@ -240,11 +240,16 @@ typedef struct april_dev_sets {
     const uint32_t *anchors;    /* compressed: block table, per block {anchor, gap_off64 | wide << 31} */
     const uint8_t *gaps;        /* compressed: gap blocks (64 or 128 bytes each) */
     const int32_t *mbr;         /* per object {x0, y0, x1, y1}: closed MBR in lattice units */
+    const uint32_t *posts;      /* skip index: the last cell of interval slot 16 q + 15, per q */
 } april_dev_sets;
 
 /* Copies the sets into a caller-allocated device buffer of at least
  * info.device_bytes bytes (256-byte aligned), asynchronously on stream, and
- * fills *out.  The host sets must stay alive until the copy completed. */
+ * fills *out; a small kernel on the same stream then derives the interval
+ * slots' skip index (posts) that the filter's start searches read.  The host
+ * sets must stay alive until the copy completed.  The filter entry points
+ * need the sets as these calls (or april_build_sets_device) lay them out:
+ * interval slots starting 256-byte aligned, with their skip index. */
 april_status april_upload(const april_sets *sets, void *dev_buf, size_t dev_bytes, void *stream,
                           april_dev_sets *out);
 
@@ -528,9 +533,10 @@ april_status april_debug_set_wait_limit(uint32_t spins);
  *                     to what counting needs, and the next call with that
  *                     much reports the full sizes.
  *   d_image           device image buffer (256-byte aligned) of at least
- *                     info->image_bytes: descriptors, MBRs and interval
+ *                     info->image_bytes: descriptors, MBRs, interval
  *                     slots (each polygon's lists in a slot range sized from
- *                     its cell count; unused slots are never read).
+ *                     its cell count; unused slots are never read) and the
+ *                     slots' skip index.
  *   out               receives the device sets (no partitions, no packed
  *                     lists); pointers into d_image.
  * The call counts cells on the device and synchronizes the stream once to

@@ -88,7 +88,7 @@ class april_dev_sets(ctypes.Structure):
                 ("order", ctypes.c_uint32), ("iv_slots", ctypes.c_uint64), ("n_entries", ctypes.c_uint32),
                 ("parts", ctypes.c_uint32), ("obj_ll", ctypes.c_void_p), ("obj_entry", ctypes.c_void_p),
                 ("entry_pid", ctypes.c_void_p), ("pdesc", ctypes.c_void_p), ("anchors", ctypes.c_void_p),
-                ("gaps", ctypes.c_void_p), ("mbr", ctypes.c_void_p)]
+                ("gaps", ctypes.c_void_p), ("mbr", ctypes.c_void_p), ("posts", ctypes.c_void_p)]
 
 
 _vp = ctypes.c_void_p

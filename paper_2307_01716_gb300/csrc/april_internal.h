@@ -54,11 +54,21 @@ struct april_sets {
 
 inline uint64_t april_round256(uint64_t b) { return (b + 255) / 256 * 256; }
 
+// Skip index of a set's interval array ("posts"): posts[q] is the last cell
+// (end - 1, in uint32) of interval slot 16 q + 15, one word per 16 slots; the
+// filter's start searches read it instead of the intervals (see
+// join_device.cuh).  Padded to whole 16-byte words for vector loads.
+inline uint64_t april_posts_words(uint64_t iv_slots) { return (iv_slots / 16 + 3) / 4 * 4; }
+// Fills posts from the device intervals iv (slots of {st, end}) on the CUDA
+// stream `stream`; returns the launch's cudaError_t as an int.
+int april_launch_posts(const uint32_t *iv, uint64_t iv_slots, uint32_t *posts, void *stream);
+
 // Device image layout (each section starts 256-byte aligned):
-//   desc (16 B/entry) | iv (8 B/slot, then a 16-byte pad) | obj_ll (8 B/object) | obj_entry (4 B x (n+1))
-//   | entry_pid (4 B/entry) | pdesc (16 B/entry) | block table (8 B/block) | gaps | mbr (16 B/object)
+//   desc (16 B/entry) | iv (8 B/slot, then a 16-byte pad) | posts (4 B per 16 slots) | obj_ll (8 B/object)
+//   | obj_entry (4 B x (n+1)) | entry_pid (4 B/entry) | pdesc (16 B/entry) | block table (8 B/block) | gaps
+//   | mbr (16 B/object)
 struct april_image_layout {
-    uint64_t desc, iv, obj_ll, obj_entry, entry_pid, pdesc, anchors, gaps, mbr, total;
+    uint64_t desc, iv, posts, obj_ll, obj_entry, entry_pid, pdesc, anchors, gaps, mbr, total;
 };
 
 inline april_image_layout april_layout(const april_sets &S) {
@@ -68,6 +78,8 @@ inline april_image_layout april_layout(const april_sets &S) {
     o += april_round256((uint64_t)S.n_entries * 16);
     L.iv = o;
     o += april_round256((uint64_t)S.iv.size() * 4 + 16);  // 16-byte pad: bulk copies round spans up to 16 bytes
+    L.posts = o;
+    o += april_round256(april_posts_words(S.iv.size() / 2) * 4);
     L.obj_ll = o;
     o += april_round256((uint64_t)S.obj_ll.size() * 4);
     L.obj_entry = o;

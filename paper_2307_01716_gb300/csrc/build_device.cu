@@ -816,7 +816,8 @@ extern "C" april_status april_build_sets_device(april_ctx *ctx, const int32_t *d
     }
     const WorkLayout L = work_layout(n_polys, h.keys, h.rb, h.cross);
     const uint64_t desc_b = r256((uint64_t)n_polys * 16), mbr_b = r256((uint64_t)n_polys * 16);
-    const uint64_t img = desc_b + mbr_b + r256(h.slots * 8 + 16);
+    const uint64_t iv_b = r256(h.slots * 8 + 16), posts_b = r256(april_posts_words(h.slots) * 4);
+    const uint64_t img = desc_b + mbr_b + iv_b + posts_b;
     info->touched_cells = h.keys;
     info->work_bytes = L.total;
     info->image_bytes = img;
@@ -869,11 +870,15 @@ extern "C" april_status april_build_sets_device(april_ctx *ctx, const int32_t *d
                                             &tot->ctr_build);
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess)  // the skip index of the interval array
+        e = (cudaError_t)april_launch_posts((const uint32_t *)(image + desc_b + mbr_b), h.slots,
+                                            (uint32_t *)(image + desc_b + mbr_b + iv_b), s);
     if (e != cudaSuccess) return cuda_fail(e, "building lists on the device");
     *out = april_dev_sets{};
     out->desc = (const uint32_t *)image;
     out->iv = (const uint32_t *)(image + desc_b + mbr_b);
     out->mbr = (const int32_t *)(image + desc_b);
+    out->posts = (const uint32_t *)(image + desc_b + mbr_b + iv_b);
     out->n_objects = n_polys;
     out->order = g.order;
     out->iv_slots = h.slots;

@@ -93,7 +93,8 @@ struct RawSets {
     static __device__ __forceinline__ uint32_t a_len(const Desc &d) { return d.y; }
     static __device__ __forceinline__ Desc shfl(const Desc &d, uint32_t src) { return shfl4(d, src); }
     __device__ __forceinline__ RawList list(const Desc &d, bool f) const {
-        return f ? RawList{s.iv + d.z, d.w} : RawList{s.iv + d.x, d.y};
+        const uint32_t off = f ? d.z : d.x;
+        return RawList{s.iv + off, f ? d.w : d.y, s.posts + off / 16};
     }
 };
 
@@ -332,45 +333,40 @@ __device__ __forceinline__ bool join_lists(const SetsT &R, const SetsT &S, const
     return X.n != 0 && Y.n != 0;
 }
 
-// (The keys are the lists' search keys: interval last cells, or block
-// anchors for compressed lists, whose start is then the block boundary.)
 // The start search of a fresh join for every group of a warp at once
 // (warp-collective; a group with need == false takes no part): X is searched
 // for its first interval whose last cell reaches Y's first start, and Y for
-// X's first start, both lists in the same rounds.  Each round every lane
-// probes P evenly spaced positions per list (fan-out G*P) and the group
-// counts the probes below the key (a prefix, the keys being sorted), which
-// leaves one gap of the spacing; the keys themselves are loaded with the
-// first round's probes, whose positions do not depend on them.  Only lists
-// longer than a first window (w0) are searched.  Over raw lists the search
-// stops once an open range holds at most kSearchSlack probe spacings of keys:
-// the join then starts at the range's lower end, which is a valid start too
-// (every interval before it ends before the other list's first start), and
-// the merge passes over the few intervals up to the exact start itself; that
-// costs less than the search rounds it saves.  Over compressed lists a key
-// stands for a 16-interval block, so their search runs to the end.
-#ifndef APRIL_SEARCH_SLACK
-#define APRIL_SEARCH_SLACK 2
-#endif
+// X's first start, both lists in the same rounds, over the lists' search
+// keys (the skip index's posts for raw lists, block anchors for compressed
+// lists; see RawList / PackedList).  Each probing round every lane probes P
+// evenly spaced keys per list (fan-out G*P) and the group counts the probes
+// below the target (a prefix, the keys being sorted), which leaves one gap
+// of the spacing.  Over a skip index the probing stops once both ranges fit
+// one vector round of 4 G kPostVec posts, and that round ends the search; a
+// list of up to about 16 * 4 G kPostVec intervals takes that round alone.
+// Only lists longer than a first window (w0) are searched.
 #ifndef APRIL_SEARCH_MIN
 #define APRIL_SEARCH_MIN 0
 #endif
 constexpr uint32_t kSearchProbes = 1;
-constexpr uint32_t kSearchSlack = APRIL_SEARCH_SLACK;
 constexpr uint32_t kSearchMin = APRIL_SEARCH_MIN;  // lists up to this long are not searched
 template <uint32_t G, class ListT>
 __device__ __forceinline__ void dual_search(const ListT &X, const ListT &Y, bool need, uint32_t w0, uint32_t t,
                                             uint32_t gbits, uint32_t &i0, uint32_t &j0) {
     constexpr uint32_t P = kSearchProbes, F = G * P;
-    constexpr uint32_t SLACK = ListT::kRandomAccess ? kSearchSlack * F : 0u;
+    // raw lists search their skip index: probing stops once a range fits one
+    // vector round (post_count); compressed lists probe to the end
+    constexpr uint32_t LIMIT = ListT::kPosts ? 4 * G * kPostVec - 3 : 0u;
     const uint32_t nX = X.n, nY = Y.n;
     const uint32_t smin = max(w0, kSearchMin);
-    uint32_t loX = 0, hiX = (need && nX > smin) ? X.keys_n() : 0;
-    uint32_t loY = 0, hiY = (need && nY > smin) ? Y.keys_n() : 0;
-    uint32_t kx = 0, ky = 0;  // Y's first start (X's key), X's first start (Y's key)
-    bool first = true;
-    while (__any_sync(kFull, hiX - loX > SLACK || hiY - loY > SLACK)) {  // lo <= hi throughout
-        const bool ax = hiX - loX > SLACK, ay = hiY - loY > SLACK;
+    const bool sx = need && nX > smin, sy = need && nY > smin;
+    uint32_t loX = 0, hiX = sx ? X.keys_n() : 0;
+    uint32_t loY = 0, hiY = sy ? Y.keys_n() : 0;
+    // Y's first start (X's key), X's first start (Y's key), loaded with the
+    // first round's probes, whose positions do not depend on them
+    const uint32_t kx = sx ? Y.first_start() : 0u, ky = sy ? X.first_start() : 0u;
+    while (__any_sync(kFull, hiX - loX > LIMIT || hiY - loY > LIMIT)) {  // lo <= hi throughout
+        const bool ax = hiX - loX > LIMIT, ay = hiY - loY > LIMIT;
         const uint32_t sX = ax ? (hiX - loX + F - 1) / F : 1, sY = ay ? (hiY - loY + F - 1) / F : 1;
         uint32_t vX[P], vY[P];
 #pragma unroll
@@ -379,11 +375,6 @@ __device__ __forceinline__ void dual_search(const ListT &X, const ListT &Y, bool
             vX[q] = (ax && px < hiX) ? X.key(px) : 0u;
             vY[q] = (ay && py < hiY) ? Y.key(py) : 0u;
         }
-        if (first && need) {
-            kx = Y.first_start();
-            ky = X.first_start();
-        }
-        first = false;
         uint32_t cX = 0, cY = 0;
 #pragma unroll
         for (uint32_t q = 0; q < P; ++q) {
@@ -402,8 +393,19 @@ __device__ __forceinline__ void dual_search(const ListT &X, const ListT &Y, bool
             loY += cY * sY;
         }
     }
-    if (need && nX > smin) i0 = X.start_of(loX);
-    if (need && nY > smin) j0 = Y.start_of(loY);
+    if constexpr (ListT::kPosts) {
+        if (__any_sync(kFull, hiX > loX || hiY > loY)) {
+            // the last round: each lane counts its vectors of posts of both
+            // lists; the group sums (X in the low half, Y in the high half)
+            uint32_t v = post_count(X.keys(), loX, hiX, 0, kx, t, G) | (post_count(Y.keys(), loY, hiY, 0, ky, t, G) << 16);
+#pragma unroll
+            for (uint32_t m = 1; m < G; m <<= 1) v += __shfl_xor_sync(kFull, v, m);
+            loX += v & 0xFFFFu;
+            loY += v >> 16;
+        }
+    }
+    if (sx) i0 = X.start_of(loX);
+    if (sy) j0 = Y.start_of(loY);
 }
 
 template <uint32_t G, class SetsT>
@@ -779,6 +781,15 @@ __global__ void __launch_bounds__(kBlock) k_general(Plan P, DevSet Rd, DevSet Sd
     }
 }
 
+// ----------------------------------------------- skip index of a set
+// posts[q] = last cell of interval slot 16 q + 15 (see RawList::key).
+__global__ void __launch_bounds__(256) k_posts(const uint2 *__restrict__ iv, uint64_t nposts,
+                                               uint32_t *__restrict__ posts) {
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nposts;
+         q += (uint64_t)gridDim.x * blockDim.x)
+        posts[q] = __ldg(&iv[16 * q + 15].y) - 1u;
+}
+
 // ------------------------------------------- K6: partition routing (a-8)
 // Sec. 5.2: a candidate pair is evaluated in the one partition that holds the
 // lower-left corner of MBR(r) n MBR(s).  Writes the two entries (object
@@ -821,6 +832,14 @@ __global__ void __launch_bounds__(256) k_route(PartView R, PartView S, uint32_t 
 int g_num_sms = 0;
 
 }  // namespace
+
+int april_launch_posts(const uint32_t *iv, uint64_t iv_slots, uint32_t *posts, void *stream) {
+    const uint64_t nposts = iv_slots / 16;
+    if (nposts == 0) return (int)cudaSuccess;
+    const unsigned grid = (unsigned)std::min<uint64_t>((nposts + 255) / 256, 152ull * 8);
+    k_posts<<<grid, 256, 0, (cudaStream_t)stream>>>((const uint2 *)iv, nposts, posts);
+    return (int)cudaGetLastError();
+}
 
 struct GraphKey {
     const void *r_desc, *r_iv, *s_desc, *s_iv;
@@ -985,6 +1004,9 @@ extern "C" april_status april_upload(const april_sets *S, void *dev_buf, size_t 
     put(L.gaps, S->gaps.data(), S->gaps.size());
     put(L.mbr, S->mbr.data(), S->mbr.size() * 4);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(upload)");
+    e = (cudaError_t)april_launch_posts((const uint32_t *)(base + L.iv), S->iv.size() / 2,
+                                        (uint32_t *)(base + L.posts), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "building the skip index (upload)");
     *out = april_dev_sets{};
     out->desc = (const uint32_t *)(base + L.desc);
     out->iv = (const uint32_t *)(base + L.iv);
@@ -994,6 +1016,7 @@ extern "C" april_status april_upload(const april_sets *S, void *dev_buf, size_t 
     out->n_entries = S->n_entries;
     out->parts = S->parts;
     out->mbr = S->mbr.empty() ? nullptr : (const int32_t *)(base + L.mbr);
+    out->posts = (const uint32_t *)(base + L.posts);
     if (S->parts) {
         out->obj_ll = (const int32_t *)(base + L.obj_ll);
         out->obj_entry = (const uint32_t *)(base + L.obj_entry);
@@ -1020,8 +1043,18 @@ extern "C" april_status april_filter_scratch_bytes(int mode, uint64_t n, size_t 
     }
 }
 
+// The filter reads sets as april_upload / april_build_sets_device lay them
+// out: interval slots 256-byte aligned (a list's place among the skip
+// index's 16-slot groups follows from its address) and the skip index.
+static april_status check_layout(const april_dev_sets *d) {
+    if (!d->desc || !d->iv || !d->posts || (((uintptr_t)d->iv) & 255u))
+        return fail(APRIL_ERR_INVALID_ARG, "device sets not laid out by april_upload or april_build_sets_device");
+    return APRIL_OK;
+}
+
 static inline DevSet dev_set(const april_dev_sets *d) {
-    return DevSet{(const uint4 *)d->desc, (const uint2 *)d->iv, d->n_entries ? d->n_entries : d->n_objects};
+    return DevSet{(const uint4 *)d->desc, (const uint2 *)d->iv, d->n_entries ? d->n_entries : d->n_objects,
+                  d->posts};
 }
 
 static inline PackedSets packed_set(const april_dev_sets *d) {
@@ -1135,6 +1168,7 @@ april_status april_enqueue_request(april_ctx *ctx, const april_dev_sets *R, cons
                                    const uint32_t *d_r, const uint32_t *d_s, uint64_t n, uint8_t *d_verdict,
                                    void *d_scratch, uint32_t *d_status, unsigned max_ctas, void *stream) {
     if (n == 0) return APRIL_OK;
+    if (check_layout(R) || check_layout(S)) return APRIL_ERR_INVALID_ARG;
     const bool packed = false;  // serving reads the raw lists
     const unsigned grid_bin = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx->num_sms * 8));
     const uint32_t gl = ctx->tune.group_lanes;
@@ -1160,6 +1194,7 @@ extern "C" april_status april_filter_pairs(april_ctx *ctx, const april_dev_sets 
     if (!d_r || !d_s || !d_verdict) return fail(APRIL_ERR_INVALID_ARG, "NULL pair or verdict array");
     if (R->order != S->order || R->parts != S->parts)
         return fail(APRIL_ERR_INVALID_ARG, "R and S are on different grids");
+    if (check_layout(R) || check_layout(S)) return APRIL_ERR_INVALID_ARG;
     if (n > 0xFFFFFFFFull) return fail(APRIL_ERR_INVALID_ARG, "at most 2^32-1 pairs per call");
     if (R->parts && mode != APRIL_MODE_BATCHED && mode != APRIL_MODE_BATCHED_PACKED)
         return fail(APRIL_ERR_INVALID_ARG, "partitioned sets need APRIL_MODE_BATCHED or APRIL_MODE_BATCHED_PACKED");
@@ -1256,6 +1291,7 @@ extern "C" april_status april_filter_pairs_ex(april_ctx *ctx, const april_dev_se
     if (predicate != APRIL_PREDICATE_INTERSECTS && predicate != APRIL_PREDICATE_WITHIN)
         return fail(APRIL_ERR_INVALID_ARG, "unknown predicate");
     if (R->parts || S->parts) return fail(APRIL_ERR_INVALID_ARG, "april_filter_pairs_ex takes sets on one global grid");
+    if (check_layout(R) || check_layout(S)) return APRIL_ERR_INVALID_ARG;
     if (predicate == APRIL_PREDICATE_WITHIN && R->order != S->order)
         return fail(APRIL_ERR_INVALID_ARG, "the within filter needs both sets on the same grid");
     if (n > 0xFFFFFFFFull) return fail(APRIL_ERR_INVALID_ARG, "at most 2^32-1 pairs per call");
@@ -1481,6 +1517,7 @@ extern "C" april_status april_filter_pairs_noalloc(const april_dev_sets *R, cons
     if (!d_r || !d_s || !d_verdict) return fail(APRIL_ERR_INVALID_ARG, "NULL pair or verdict array");
     if (R->order != S->order) return fail(APRIL_ERR_INVALID_ARG, "R and S are on different grids");
     if (R->parts || S->parts) return fail(APRIL_ERR_INVALID_ARG, "april_filter_pairs_noalloc takes unpartitioned sets");
+    if (check_layout(R) || check_layout(S)) return APRIL_ERR_INVALID_ARG;
     if (n > kNoAllocMaxPairs)
         return fail(APRIL_ERR_INVALID_ARG, "april_filter_pairs_noalloc: n exceeds APRIL_NOALLOC_MAX_PAIRS (4194304); "
                                            "split the pairs or use april_filter_pairs with caller scratch");

@@ -28,9 +28,10 @@ namespace april_dev {
 constexpr unsigned kFull = 0xffffffffu;
 
 struct DevSet {
-    const uint4 *desc;  // per object {a_off, a_len, f_off, f_len}
-    const uint2 *iv;    // intervals {st, end}
+    const uint4 *desc;      // per object {a_off, a_len, f_off, f_len}
+    const uint2 *iv;        // intervals {st, end}
     uint32_t n;
+    const uint32_t *posts;  // skip index: last cell of interval slot 16 q + 15
 };
 
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
@@ -210,6 +211,7 @@ __device__ __forceinline__ void coarsen_window(uint32_t a, uint32_t cnt, uint32_
 
 struct WarpScope {
     static __device__ __forceinline__ void sync() { __syncwarp(); }
+    static __device__ __forceinline__ uint32_t sum(uint32_t v) { return __reduce_add_sync(kFull, v); }
     static __device__ __forceinline__ bool all(bool b) { return __all_sync(kFull, b) != 0; }
     static __device__ __forceinline__ uint32_t count(bool b) { return __popc(__ballot_sync(kFull, b)); }
     // OR of `b` over the group; `v` from thread `src` is returned to all.
@@ -222,6 +224,11 @@ struct WarpScope {
 
 struct CtaScope {
     static __device__ __forceinline__ void sync() { __syncthreads(); }
+    // sum of per-thread counts below 16 (bit by bit)
+    static __device__ __forceinline__ uint32_t sum(uint32_t v) {
+        return (uint32_t)__syncthreads_count(v & 1u) + 2u * (uint32_t)__syncthreads_count(v & 2u) +
+               4u * (uint32_t)__syncthreads_count(v & 4u) + 8u * (uint32_t)__syncthreads_count(v & 8u);
+    }
     static __device__ __forceinline__ bool all(bool b) { return __syncthreads_and(b) != 0; }
     static __device__ __forceinline__ uint32_t count(bool b) { return (uint32_t)__syncthreads_count(b); }
     static __device__ __forceinline__ bool vote(bool b, uint32_t &v, uint32_t src, uint32_t *slot) {
@@ -328,8 +335,10 @@ __device__ __forceinline__ uint2 *stage_window(uint2 *buf, const uint2 *src, uin
 struct RawList {
     static constexpr bool kBulk = true;
     static constexpr bool kRandomAccess = true;
+    static constexpr bool kPosts = true;
     const uint2 *p;
     uint32_t n;
+    const uint32_t *pk;  // the set's posts from the one that closes a slot of this list on
     template <uint32_t NT>
     __device__ __forceinline__ uint32_t stage(uint2 *buf, uint32_t i0, uint32_t cnt, uint32_t tid) const {
         return smem_addr(stage_window<NT>(buf, p + i0, cnt, tid));
@@ -346,16 +355,27 @@ struct RawList {
         return smem_addr(buf) + 8u * (uint32_t)(((uintptr_t)(p + i0) >> 3) & 1u);
     }
     __device__ __forceinline__ uint32_t first_start() const { return __ldg(&p->x); }
-    // Start search: the keys are the intervals' last cells; a count c of keys
-    // below the target makes interval c the first that can meet.
-    __device__ __forceinline__ uint32_t keys_n() const { return n; }
-    __device__ __forceinline__ uint32_t key(uint32_t q) const { return __ldg(&p[q].y) - 1u; }
-    __device__ __forceinline__ uint32_t start_of(uint32_t c) const { return c; }
+    // Start search over the skip index.  The set's post q is the last cell of
+    // interval slot 16 q + 15; interval arrays start 256-byte aligned, so this
+    // list's first post closes its interval pb = 15 - (slot % 16) and post k
+    // closes interval pb + 16 k.  With c posts below the target, every
+    // interval up to pb + 16 (c - 1) ends below it, and the join may start
+    // right after that one: at most 16 intervals before the first that can
+    // meet, all of which the merge passes over without a verdict.
+    __device__ __forceinline__ uint32_t pb() const { return 15u - (uint32_t)(((uintptr_t)p >> 3) & 15u); }
+    __device__ __forceinline__ uint32_t keys_n() const {
+        const uint32_t b = pb();
+        return n > b ? (n - 1 - b) / 16 + 1 : 0u;
+    }
+    __device__ __forceinline__ uint32_t key(uint32_t q) const { return __ldg(pk + q); }
+    __device__ __forceinline__ const uint32_t *keys() const { return pk; }
+    __device__ __forceinline__ uint32_t start_of(uint32_t c) const { return c ? pb() + 16u * (c - 1) + 1u : 0u; }
 };
 
 struct PackedList {
     static constexpr bool kBulk = false;
     static constexpr bool kRandomAccess = false;
+    static constexpr bool kPosts = false;
     const uint2 *blocks;  // per block {anchor, gap_off64 | wide << 31}
     const uint8_t *gaps;  // the set's gap stream
     uint32_t n;
@@ -412,19 +432,50 @@ struct PackedList {
     // that block boundary, at or before the first interval that can meet.
     __device__ __forceinline__ uint32_t keys_n() const { return (2 * n + 31) / 32; }
     __device__ __forceinline__ uint32_t key(uint32_t q) const { return __ldg(&blocks[q].x); }
+    __device__ __forceinline__ const uint32_t *keys() const { return nullptr; }
     __device__ __forceinline__ uint32_t start_of(uint32_t c) const { return c ? 16u * (c - 1) : 0u; }
 };
 
-// Count of a list's search keys (interval last cells, or block anchors for
-// compressed lists; sorted) that lie below t after a right shift by sh: an
-// NT-ary search by the group.  Each round the NT threads probe evenly spaced
-// keys and count those below t (a prefix, the keys being sorted), which
-// leaves one gap of the spacing; with NT = 32 a list of 10^4 intervals takes
-// three rounds.  Every thread of the group gets the same answer.
+// The final round of a search over a skip index (lists with kPosts): the
+// count of keys below t (after a right shift by sh) among keys [lo, hi) of
+// `keys`, where hi - lo <= 4 * NT * kPostVec - 3.  Each thread loads
+// kPostVec 16-byte words of keys (contiguous per thread, the group's loads
+// cover one aligned run that holds [lo, hi)) and counts; the group sums.
+constexpr uint32_t kPostVec = 2;
+__device__ __forceinline__ uint32_t post_count(const uint32_t *keys, uint32_t lo, uint32_t hi, uint32_t sh,
+                                               uint32_t t, uint32_t tid, uint32_t nt) {
+    uint32_t c = 0;
+    if (lo < hi) {
+        const int mis = (int)(((uintptr_t)(keys + lo) >> 2) & 3u);
+        const uint4 *base = (const uint4 *)(keys + lo - mis);  // aligned down: still inside the posts array
+        const int ilo = (int)lo, ihi = (int)hi;
+#pragma unroll
+        for (uint32_t j = 0; j < kPostVec; ++j) {
+            const int v = (int)(tid + nt * j);  // 16-byte word of the run
+            const int k0 = ilo - mis + 4 * v;   // its first key (may lie before lo)
+            if (k0 < ihi) {
+                const uint4 q = __ldg(base + v);
+                c += (k0 >= ilo && (q.x >> sh) < t) + (k0 + 1 >= ilo && k0 + 1 < ihi && (q.y >> sh) < t) +
+                     (k0 + 2 >= ilo && k0 + 2 < ihi && (q.z >> sh) < t) + (k0 + 3 < ihi && (q.w >> sh) < t);
+            }
+        }
+    }
+    return c;
+}
+
+// Count of a list's search keys (the skip index's posts for raw lists, block
+// anchors for compressed lists; sorted) that lie below t after a right shift
+// by sh: an NT-ary search by the group.  Each round the NT threads probe
+// evenly spaced keys and count those below t (a prefix, the keys being
+// sorted), which leaves one gap of the spacing; with NT = 32 a list of 10^4
+// keys takes three rounds.  Over a skip index the probing stops once the
+// range fits one vector round (post_count), which ends the search.  Every
+// thread of the group gets the same answer.
 template <class Scope, uint32_t NT, class ListT>
 __device__ __forceinline__ uint32_t start_search(const ListT &L, uint32_t sh, uint32_t t, uint32_t tid) {
+    constexpr uint32_t LIMIT = ListT::kPosts ? 4 * NT * kPostVec - 3 : 0u;
     uint32_t lo = 0, hi = L.keys_n();  // the answer lies in [lo, hi]
-    while (lo < hi) {
+    while (hi - lo > LIMIT) {
         const uint32_t step = (hi - lo + NT - 1) / NT;
         const uint32_t q = lo + (tid + 1) * step - 1;
         const bool below = q < hi && (L.key(q) >> sh) < t;
@@ -434,6 +485,7 @@ __device__ __forceinline__ uint32_t start_search(const ListT &L, uint32_t sh, ui
         if (lo + (c + 1) * step <= hi) hi = lo + (c + 1) * step - 1;
         lo += c * step;
     }
+    if constexpr (ListT::kPosts) lo += Scope::sum(post_count(L.keys(), lo, hi, sh, t, tid, NT));
     return lo;
 }
 

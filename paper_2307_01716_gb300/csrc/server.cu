@@ -222,6 +222,8 @@ extern "C" april_status april_server_create(april_ctx *ctx, const april_dev_sets
     if (((uintptr_t)d_arena) & 255u) return fail(APRIL_ERR_INVALID_ARG, "arena must be 256-byte aligned");
     if (max_inflight < 1 || max_inflight > 64) return fail(APRIL_ERR_INVALID_ARG, "max_inflight must be 1..64");
     if (R->order != S->order || R->parts != S->parts) return fail(APRIL_ERR_INVALID_ARG, "R and S use different grids");
+    if (!R->posts || !S->posts || (((uintptr_t)R->iv | (uintptr_t)S->iv) & 255u))
+        return fail(APRIL_ERR_INVALID_ARG, "device sets not laid out by april_upload or april_build_sets_device");
     auto *sv = new april_server();
     sv->ctx = ctx;
     sv->R = *R;
