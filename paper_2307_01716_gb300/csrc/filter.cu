@@ -66,11 +66,10 @@ constexpr uint32_t kCtaBuf = kCtaWMax + 2;
 #define APRIL_GROUP_PER 8
 #endif
 constexpr uint32_t kGroupPer = APRIL_GROUP_PER;
-// intervals of shared staging per warp: the largest of 2 lists x (32/G groups)
-// x (kGroupPer*G + 2) over the group sizes, and 2 x kWarpBuf for whole warps
-constexpr uint32_t kWarpShare = 64 * kGroupPer + 32 > 2 * (kWarpWMax + 2) ? 64 * kGroupPer + 32 : 2 * (kWarpWMax + 2);
-constexpr uint32_t kSharedIv = kWarpsPerBlock * kWarpShare;  // one buffer serves both phases
-static_assert(2 * kCtaBuf <= kSharedIv, "CTA windows must fit in the warps' buffers");
+// intervals of shared staging per warp for kernels with whole-warp joins only
+// (K1, K7): two windows of a warp, and a CTA's two windows across its warps
+constexpr uint32_t kWarpShare = 2 * (kWarpWMax + 2);
+constexpr uint32_t kSharedIv = kWarpsPerBlock * kWarpShare > 2 * kCtaBuf ? kWarpsPerBlock * kWarpShare : 2 * kCtaBuf;
 static_assert(kWarpBuf % 2 == 0 && kCtaBuf % 2 == 0, "buffers must stay 16-byte aligned");
 
 // scratch of the batched mode: counters, then the list of long pairs
@@ -317,11 +316,18 @@ struct GroupCfg {
     static constexpr uint32_t WMAX = kGroupPer * G;
     static constexpr uint32_t BUF = WMAX + 2;
     static constexpr uint32_t LEADS = G == 32 ? 1u : G == 16 ? 0x00010001u : G == 8 ? 0x01010101u : 0x11111111u;
+    // intervals of shared staging per warp: the groups' buffers, or two warp
+    // windows for the long pairs joined by the warp
+    static constexpr uint32_t SHARE = NG * 2 * BUF > 2 * kWarpBuf ? NG * 2 * BUF : 2 * kWarpBuf;
+    // mbarriers: [0] the CTA phase, [1 + warp * NG + group] the group engine,
+    // [1 + kWarpsPerBlock * NG + warp] long pairs joined by warps
+    static constexpr uint32_t BARS = 1 + kWarpsPerBlock * (NG + 1);
+    static __device__ __forceinline__ uint32_t group_bar(uint32_t warp, uint32_t g) { return 1 + warp * NG + g; }
+    static __device__ __forceinline__ uint32_t warp_bar(uint32_t warp) { return 1 + kWarpsPerBlock * NG + warp; }
 };
-static_assert(GroupCfg<4>::NG * 2 * GroupCfg<4>::BUF <= kWarpShare, "group buffers fit in a warp's share");
-static_assert(GroupCfg<8>::NG * 2 * GroupCfg<8>::BUF <= kWarpShare, "group buffers fit in a warp's share");
-static_assert(GroupCfg<16>::NG * 2 * GroupCfg<16>::BUF <= kWarpShare, "group buffers fit in a warp's share");
-static_assert(2 * kWarpBuf <= kWarpShare, "warp buffers fit in a warp's share");
+static_assert(2 * kCtaBuf <= kWarpsPerBlock * GroupCfg<32>::SHARE, "CTA windows must fit in the warps' buffers");
+static_assert(GroupCfg<4>::SHARE % 2 == 0 && GroupCfg<8>::SHARE % 2 == 0 && GroupCfg<16>::SHARE % 2 == 0,
+              "warp shares keep 16-byte alignment");
 
 // Lists of join step `stage` of a pair (in join order jo, see step_outcome);
 // false when one of them is empty (the join then has no overlap).
@@ -354,9 +360,10 @@ template <uint32_t G, class ListT>
 __device__ __forceinline__ void dual_search(const ListT &X, const ListT &Y, bool need, uint32_t w0, uint32_t t,
                                             uint32_t gbits, uint32_t &i0, uint32_t &j0) {
     constexpr uint32_t P = kSearchProbes, F = G * P;
-    // raw lists search their skip index: probing stops once a range fits one
-    // vector round (post_count); compressed lists probe to the end
-    constexpr uint32_t LIMIT = ListT::kPosts ? 4 * G * kPostVec - 3 : 0u;
+    // probing stops once a range fits one vector round (post_count) over the
+    // skip index (raw lists) or the block anchors (compressed lists)
+    constexpr uint32_t PER = 4 / ListT::kKeyStride;  // keys per 16-byte load
+    constexpr uint32_t LIMIT = PER * G * kPostVec - (PER - 1);
     const uint32_t nX = X.n, nY = Y.n;
     const uint32_t smin = max(w0, kSearchMin);
     const bool sx = need && nX > smin, sy = need && nY > smin;
@@ -393,16 +400,15 @@ __device__ __forceinline__ void dual_search(const ListT &X, const ListT &Y, bool
             loY += cY * sY;
         }
     }
-    if constexpr (ListT::kPosts) {
-        if (__any_sync(kFull, hiX > loX || hiY > loY)) {
-            // the last round: each lane counts its vectors of posts of both
-            // lists; the group sums (X in the low half, Y in the high half)
-            uint32_t v = post_count(X.keys(), loX, hiX, 0, kx, t, G) | (post_count(Y.keys(), loY, hiY, 0, ky, t, G) << 16);
+    if (__any_sync(kFull, hiX > loX || hiY > loY)) {
+        // the last round: each lane counts its vectors of keys of both lists;
+        // the group sums (X in the low half, Y in the high half)
+        constexpr uint32_t KS = ListT::kKeyStride;
+        uint32_t v = post_count<KS>(X.keys(), loX, hiX, 0, kx, t, G) | (post_count<KS>(Y.keys(), loY, hiY, 0, ky, t, G) << 16);
 #pragma unroll
-            for (uint32_t m = 1; m < G; m <<= 1) v += __shfl_xor_sync(kFull, v, m);
-            loX += v & 0xFFFFu;
-            loY += v >> 16;
-        }
+        for (uint32_t m = 1; m < G; m <<= 1) v += __shfl_xor_sync(kFull, v, m);
+        loX += v & 0xFFFFu;
+        loY += v >> 16;
     }
     if (sx) i0 = X.start_of(loX);
     if (sy) j0 = Y.start_of(loY);
@@ -523,8 +529,8 @@ __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, con
                 ok = mbar_wait(bar, phase);
                 phase ^= 1u;
             } else {
-                X.template stage<G>(xb, i0, nx, t);
-                Y.template stage<G>(yb, j0, ny, t);
+                X.template stage<G>(xb, i0, nx, t, gbits);
+                Y.template stage<G>(yb, j0, ny, t, gbits);
             }
             xa = X.window(xb, i0);
             ya = Y.window(yb, j0);
@@ -590,21 +596,20 @@ __global__ void APRIL_PERSISTENT_BOUNDS k_persistent(SetsT R, SetsT S,
                                                        uint32_t cta_threshold, const uint32_t *__restrict__ big_list,
                                                        uint32_t *counters, uint32_t w0_group, uint32_t w0_cta,
                                                        uint32_t jo) {
-    __shared__ __align__(16) uint2 sm[kSharedIv];
+    using C = GroupCfg<G>;
+    __shared__ __align__(16) uint2 sm[kWarpsPerBlock * C::SHARE];
     __shared__ uint32_t s_item, s_slot;
-    // mbarriers: [0] the CTA phase, [1 + warp * 8 + group] the group engine,
-    // [1 + 8 * 8 + warp] long pairs joined by warps
-    __shared__ uint64_t bars[1 + kWarpsPerBlock * 9];
+    __shared__ uint64_t bars[C::BARS];  // see GroupCfg
     __shared__ uint4 s_chunk[kWarpsPerBlock][64];     // group engine: each warp's chunk descriptors
     __shared__ uint8_t s_chunk_lane[kWarpsPerBlock][32];  // and the chunk lanes they came from
-    init_barriers(bars, 1 + kWarpsPerBlock * 9);
+    init_barriers(bars, C::BARS);
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const uint32_t nbig = *((volatile uint32_t *)&counters[C_BIG_COUNT]);
-    uint2 *wbuf = sm + warp * kWarpShare;
+    uint2 *wbuf = sm + warp * C::SHARE;
     if (w0_cta < kBlock) {
         // long pairs one per warp (first window w0_cta): the CTA's warps work
         // on eight long pairs at once
-        JoinSync ws{smem_addr(&bars[1 + kWarpsPerBlock * 8 + warp]), 0u, false};
+        JoinSync ws{smem_addr(&bars[C::warp_bar(warp)]), 0u, false};
         for (;;) {
             uint32_t it = 0;
             if (lane == 0) it = atomicAdd(&counters[C_BIG_HEAD], 1u);
@@ -642,7 +647,7 @@ __global__ void APRIL_PERSISTENT_BOUNDS k_persistent(SetsT R, SetsT S,
         __syncthreads();
     }
     if constexpr (G == 32) {
-        JoinSync js{smem_addr(&bars[1 + warp * 8]), 0u, false};
+        JoinSync js{smem_addr(&bars[C::group_bar(warp, 0)]), 0u, false};
         const uint64_t nchunks = (n + 31) / 32;
         for (;;) {
             uint32_t c = 0;
@@ -655,7 +660,7 @@ __global__ void APRIL_PERSISTENT_BOUNDS k_persistent(SetsT R, SetsT S,
         }
     } else {
         group_engine<G>(R, S, pr, ps, n, out, status, counters, cta_threshold, wbuf, s_chunk[warp],
-                        s_chunk_lane[warp], smem_addr(&bars[1 + warp * 8]), lane, w0_group, jo);
+                        s_chunk_lane[warp], smem_addr(&bars[C::group_bar(warp, 0)]), lane, w0_group, jo);
     }
 }
 
@@ -842,7 +847,7 @@ int april_launch_posts(const uint32_t *iv, uint64_t iv_slots, uint32_t *posts, v
 }
 
 struct GraphKey {
-    const void *r_desc, *r_iv, *s_desc, *s_iv;
+    const void *r_desc, *r_iv, *s_desc, *s_iv, *r_posts, *s_posts;
     uint32_t rn, sn;
     const void *d_r, *d_s, *out, *scratch;
     uint64_t n;
@@ -853,7 +858,8 @@ struct GraphKey {
     const void *r_pdesc, *s_pdesc;
     bool operator==(const GraphKey &o) const {
         return packed == o.packed && parts == o.parts && r_pdesc == o.r_pdesc && s_pdesc == o.s_pdesc &&
-               r_desc == o.r_desc && r_iv == o.r_iv && s_desc == o.s_desc && s_iv == o.s_iv && rn == o.rn &&
+               r_desc == o.r_desc && r_iv == o.r_iv && s_desc == o.s_desc && s_iv == o.s_iv &&
+               r_posts == o.r_posts && s_posts == o.s_posts && rn == o.rn &&
                sn == o.sn && d_r == o.d_r && d_s == o.d_s && out == o.out && scratch == o.scratch && n == o.n &&
                tune.cta_threshold == o.tune.cta_threshold && tune.group_lanes == o.tune.group_lanes &&
                tune.group_window == o.tune.group_window && tune.cta_window == o.tune.cta_window &&
@@ -880,6 +886,9 @@ using april::fail;
 static april_status cuda_fail(cudaError_t e, const char *what) {
     return fail(APRIL_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
+
+// index of a group size 4, 8, 16, 32 in the context's occupancy table
+static int group_index(uint32_t g) { return g == 4 ? 0 : g == 8 ? 1 : g == 16 ? 2 : 3; }
 
 static april_tune default_tune() {
     april_tune t{};
@@ -914,30 +923,19 @@ extern "C" april_status april_ctx_create(int device, april_ctx **out) {
     c->device = device;
     c->tune = default_tune();
     e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->persistent_blocks_per_sm[0], k_persistent<4, RawSets>,
-                                                          kBlock, 0);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->persistent_blocks_per_sm[1], k_persistent<8, RawSets>,
-                                                          kBlock, 0);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->persistent_blocks_per_sm[2], k_persistent<16, RawSets>,
-                                                          kBlock, 0);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->persistent_blocks_per_sm[3], k_persistent<32, RawSets>,
-                                                          kBlock, 0);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->persistent_blocks_per_sm[4],
-                                                          k_persistent<4, PackedSets>, kBlock, 0);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->persistent_blocks_per_sm[5],
-                                                          k_persistent<8, PackedSets>, kBlock, 0);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->persistent_blocks_per_sm[6],
-                                                          k_persistent<16, PackedSets>, kBlock, 0);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->persistent_blocks_per_sm[7],
-                                                          k_persistent<32, PackedSets>, kBlock, 0);
+#define APRIL_OCC(I, G, SETS)                                                                                \
+    if (e == cudaSuccess)                                                                                      \
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->persistent_blocks_per_sm[I], k_persistent<G, SETS>, \
+                                                          kBlock, 0)
+    APRIL_OCC(0, 4, RawSets);
+    APRIL_OCC(1, 8, RawSets);
+    APRIL_OCC(2, 16, RawSets);
+    APRIL_OCC(3, 32, RawSets);
+    APRIL_OCC(4, 4, PackedSets);
+    APRIL_OCC(5, 8, PackedSets);
+    APRIL_OCC(6, 16, PackedSets);
+    APRIL_OCC(7, 32, PackedSets);
+#undef APRIL_OCC
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_status, 256);
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, 256);
@@ -1127,11 +1125,11 @@ static april_status launch_batched(april_ctx *ctx, const april_dev_sets *R, cons
                                    void *scratch, bool packed, cudaStream_t st) {
     const unsigned grid_bin = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx->num_sms * 8);
     const uint32_t gl = ctx->tune.group_lanes;
-    const int occ = ctx->persistent_blocks_per_sm[(packed ? 4 : 0) + (gl == 4 ? 0 : gl == 8 ? 1 : gl == 16 ? 2 : 3)];
+    const int occ = ctx->persistent_blocks_per_sm[(packed ? 4 : 0) + group_index(gl)];
     const int bps = ctx->tune.blocks_per_sm ? (int)std::min<uint32_t>(ctx->tune.blocks_per_sm, (uint32_t)occ) : occ;
     const unsigned grid_main = (unsigned)std::max(1, ctx->num_sms * bps);
-    GraphKey key{R->desc, R->iv, S->desc, S->iv, R->n_objects, S->n_objects, d_r, d_s, out, scratch, n,
-                 ctx->tune, grid_bin, grid_main, packed, R->parts, R->pdesc, S->pdesc};
+    GraphKey key{R->desc, R->iv, S->desc, S->iv, R->posts, S->posts, R->n_objects, S->n_objects, d_r, d_s, out,
+                 scratch, n, ctx->tune, grid_bin, grid_main, packed, R->parts, R->pdesc, S->pdesc};
     cudaError_t e;
     if (!ctx->graph || !(key == ctx->key)) {
         if (ctx->graph) {
@@ -1172,7 +1170,7 @@ april_status april_enqueue_request(april_ctx *ctx, const april_dev_sets *R, cons
     const bool packed = false;  // serving reads the raw lists
     const unsigned grid_bin = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx->num_sms * 8));
     const uint32_t gl = ctx->tune.group_lanes;
-    const int occ = ctx->persistent_blocks_per_sm[(packed ? 4 : 0) + (gl == 4 ? 0 : gl == 8 ? 1 : gl == 16 ? 2 : 3)];
+    const int occ = ctx->persistent_blocks_per_sm[(packed ? 4 : 0) + group_index(gl)];
     unsigned grid_main = (unsigned)std::max(1, ctx->num_sms * occ);
     grid_main = std::min<unsigned>(grid_main, std::max<unsigned>(1, max_ctas));
     cudaError_t e = enqueue_batched(ctx, R, S, d_r, d_s, n, d_verdict, d_scratch, packed, grid_bin, grid_main,

@@ -335,12 +335,12 @@ __device__ __forceinline__ uint2 *stage_window(uint2 *buf, const uint2 *src, uin
 struct RawList {
     static constexpr bool kBulk = true;
     static constexpr bool kRandomAccess = true;
-    static constexpr bool kPosts = true;
+    static constexpr uint32_t kKeyStride = 1;  // words per search key in keys()
     const uint2 *p;
     uint32_t n;
     const uint32_t *pk;  // the set's posts from the one that closes a slot of this list on
     template <uint32_t NT>
-    __device__ __forceinline__ uint32_t stage(uint2 *buf, uint32_t i0, uint32_t cnt, uint32_t tid) const {
+    __device__ __forceinline__ uint32_t stage(uint2 *buf, uint32_t i0, uint32_t cnt, uint32_t tid, uint32_t) const {
         return smem_addr(stage_window<NT>(buf, p + i0, cnt, tid));
     }
     // Bulk-copy form: called by the one issuing thread; returns bytes in flight.
@@ -375,50 +375,62 @@ struct RawList {
 struct PackedList {
     static constexpr bool kBulk = false;
     static constexpr bool kRandomAccess = false;
-    static constexpr bool kPosts = false;
+    static constexpr uint32_t kKeyStride = 2;  // words per search key: the anchors of the block table
     const uint2 *blocks;  // per block {anchor, gap_off64 | wide << 31}
     const uint8_t *gaps;  // the set's gap stream
     uint32_t n;
+    // Decodes the window [i0, i0 + cnt) into shared memory as intervals.  The
+    // window's endpoints are split into slices of 8 (a quarter of a block),
+    // one slice per thread per round: the thread loads its slice's gaps with
+    // one 16-byte load (two for 32-bit gaps), sums them in registers, the 4
+    // threads of a block add the totals of the slices before theirs (two
+    // shuffle steps) and the block anchor, and every endpoint inside the
+    // window is stored.  A block's slot 0 holds no gap (the anchor is its
+    // endpoint 0) and reads as 0.  `mask` names the threads of this warp that
+    // call stage together (whole groups of 4 consecutive lanes).
     template <uint32_t NT>
-    __device__ __forceinline__ uint32_t stage(uint2 *buf, uint32_t i0, uint32_t cnt, uint32_t tid) const {
+    __device__ __forceinline__ uint32_t stage(uint2 *buf, uint32_t i0, uint32_t cnt, uint32_t tid,
+                                              uint32_t mask) const {
+        static_assert(NT >= 4, "a block's four slices are decoded by four threads at once");
         const uint32_t base = smem_addr(buf);
         const uint32_t e0 = 2 * i0, e1 = 2 * (i0 + cnt);  // endpoint range of the window
-        const uint32_t b0 = e0 >> 5, b1 = (e1 - 1) >> 5;
-        for (uint32_t b = b0 + tid; b <= b1; b += NT) {
-            const uint2 meta = __ldg(blocks + b);
-            uint32_t v = meta.x;
-            const uint8_t *gb = gaps + 64ull * (meta.y & 0x7FFFFFFFu);
-            uint32_t g[32];
-            if (meta.y >> 31) {
-                const uint4 *q = (const uint4 *)gb;
+        const uint32_t b0 = e0 >> 5, nsl = ((((e1 - 1) >> 5) - b0) + 1) * 4;
+        for (uint32_t s0 = 0; s0 < nsl; s0 += NT) {
+            const uint32_t sl = s0 + tid, q = sl & 3u;
+            const bool on = sl < nsl;
+            uint32_t g[8], anchor = 0;
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const uint4 u = __ldg(q + c);
-                    g[4 * c] = u.x;
-                    g[4 * c + 1] = u.y;
-                    g[4 * c + 2] = u.z;
-                    g[4 * c + 3] = u.w;
-                }
-            } else {
-                const uint4 *q = (const uint4 *)gb;
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const uint4 u = __ldg(q + c);
-                    g[8 * c] = u.x & 0xFFFFu;
-                    g[8 * c + 1] = u.x >> 16;
-                    g[8 * c + 2] = u.y & 0xFFFFu;
-                    g[8 * c + 3] = u.y >> 16;
-                    g[8 * c + 4] = u.z & 0xFFFFu;
-                    g[8 * c + 5] = u.z >> 16;
-                    g[8 * c + 6] = u.w & 0xFFFFu;
-                    g[8 * c + 7] = u.w >> 16;
+            for (int k = 0; k < 8; ++k) g[k] = 0;
+            if (on) {
+                const uint2 meta = __ldg(blocks + b0 + (sl >> 2));
+                anchor = meta.x;
+                const uint8_t *gb = gaps + 64ull * (meta.y & 0x7FFFFFFFu);
+                if (meta.y >> 31) {
+                    const uint4 *p4 = (const uint4 *)(gb + 32u * q);
+                    const uint4 u = __ldg(p4), v = __ldg(p4 + 1);
+                    g[0] = u.x; g[1] = u.y; g[2] = u.z; g[3] = u.w;
+                    g[4] = v.x; g[5] = v.y; g[6] = v.z; g[7] = v.w;
+                } else {
+                    const uint4 u = __ldg((const uint4 *)(gb + 16u * q));
+                    g[0] = u.x & 0xFFFFu; g[1] = u.x >> 16; g[2] = u.y & 0xFFFFu; g[3] = u.y >> 16;
+                    g[4] = u.z & 0xFFFFu; g[5] = u.z >> 16; g[6] = u.w & 0xFFFFu; g[7] = u.w >> 16;
                 }
             }
 #pragma unroll
-            for (uint32_t k = 0; k < 32; ++k) {
-                if (k) v += g[k];
-                const uint32_t e = 32 * b + k;
-                if (e >= e0 && e < e1) asm volatile("st.shared.u32 [%0], %1;\n" ::"r"(base + 4 * (e - e0)), "r"(v));
+            for (int k = 1; k < 8; ++k) g[k] += g[k - 1];
+            // inclusive scan of the slice totals over the block's 4 threads
+            uint32_t x = g[7];
+            uint32_t y = __shfl_up_sync(mask, x, 1, 4);
+            if (q >= 1) x += y;
+            y = __shfl_up_sync(mask, x, 2, 4);
+            if (q >= 2) x += y;
+            const uint32_t v0 = anchor + x - g[7];
+            const uint32_t ebase = 32u * (b0 + (sl >> 2)) + 8u * q;
+#pragma unroll
+            for (uint32_t k = 0; k < 8; ++k) {
+                const uint32_t e = ebase + k;
+                if (on && e >= e0 && e < e1)
+                    asm volatile("st.shared.u32 [%0], %1;\n" ::"r"(base + 4 * (e - e0)), "r"(v0 + g[k]));
             }
         }
         return base;
@@ -432,31 +444,38 @@ struct PackedList {
     // that block boundary, at or before the first interval that can meet.
     __device__ __forceinline__ uint32_t keys_n() const { return (2 * n + 31) / 32; }
     __device__ __forceinline__ uint32_t key(uint32_t q) const { return __ldg(&blocks[q].x); }
-    __device__ __forceinline__ const uint32_t *keys() const { return nullptr; }
+    __device__ __forceinline__ const uint32_t *keys() const { return (const uint32_t *)blocks; }
     __device__ __forceinline__ uint32_t start_of(uint32_t c) const { return c ? 16u * (c - 1) : 0u; }
 };
 
-// The final round of a search over a skip index (lists with kPosts): the
-// count of keys below t (after a right shift by sh) among keys [lo, hi) of
-// `keys`, where hi - lo <= 4 * NT * kPostVec - 3.  Each thread loads
-// kPostVec 16-byte words of keys (contiguous per thread, the group's loads
-// cover one aligned run that holds [lo, hi)) and counts; the group sums.
+// The final round of a start search over sorted keys (a skip index, or block
+// anchors at a stride of two words): the count of keys below t (after a
+// right shift by sh) among keys [lo, hi) of `keys`, where hi - lo is at most
+// P NT kPostVec - (P - 1) with P = 4 / STRIDE keys per 16-byte word.  Each
+// thread loads kPostVec 16-byte words of keys (the group's loads cover one
+// aligned run that holds [lo, hi)) and counts; the group sums.
 constexpr uint32_t kPostVec = 2;
+template <uint32_t STRIDE>  // words per key: 1 (posts) or 2 (block anchors, the first word of each pair)
 __device__ __forceinline__ uint32_t post_count(const uint32_t *keys, uint32_t lo, uint32_t hi, uint32_t sh,
                                                uint32_t t, uint32_t tid, uint32_t nt) {
+    constexpr int PER = 4 / STRIDE;  // keys per 16-byte word
     uint32_t c = 0;
     if (lo < hi) {
-        const int mis = (int)(((uintptr_t)(keys + lo) >> 2) & 3u);
-        const uint4 *base = (const uint4 *)(keys + lo - mis);  // aligned down: still inside the posts array
+        const int mis = (int)(((uintptr_t)(keys + STRIDE * lo) >> 2) & 3u) / (int)STRIDE;
+        // aligned down (signed: lo may be below mis), still inside the array
+        const uint4 *base = (const uint4 *)(keys + (ptrdiff_t)STRIDE * ((ptrdiff_t)lo - mis));
         const int ilo = (int)lo, ihi = (int)hi;
 #pragma unroll
         for (uint32_t j = 0; j < kPostVec; ++j) {
             const int v = (int)(tid + nt * j);  // 16-byte word of the run
-            const int k0 = ilo - mis + 4 * v;   // its first key (may lie before lo)
+            const int k0 = ilo - mis + PER * v;  // its first key (may lie before lo)
             if (k0 < ihi) {
                 const uint4 q = __ldg(base + v);
-                c += (k0 >= ilo && (q.x >> sh) < t) + (k0 + 1 >= ilo && k0 + 1 < ihi && (q.y >> sh) < t) +
-                     (k0 + 2 >= ilo && k0 + 2 < ihi && (q.z >> sh) < t) + (k0 + 3 < ihi && (q.w >> sh) < t);
+                if (STRIDE == 1)
+                    c += (k0 >= ilo && (q.x >> sh) < t) + (k0 + 1 >= ilo && k0 + 1 < ihi && (q.y >> sh) < t) +
+                         (k0 + 2 >= ilo && k0 + 2 < ihi && (q.z >> sh) < t) + (k0 + 3 < ihi && (q.w >> sh) < t);
+                else
+                    c += (k0 >= ilo && (q.x >> sh) < t) + (k0 + 1 < ihi && (q.z >> sh) < t);
             }
         }
     }
@@ -473,7 +492,8 @@ __device__ __forceinline__ uint32_t post_count(const uint32_t *keys, uint32_t lo
 // thread of the group gets the same answer.
 template <class Scope, uint32_t NT, class ListT>
 __device__ __forceinline__ uint32_t start_search(const ListT &L, uint32_t sh, uint32_t t, uint32_t tid) {
-    constexpr uint32_t LIMIT = ListT::kPosts ? 4 * NT * kPostVec - 3 : 0u;
+    constexpr uint32_t PER = 4 / ListT::kKeyStride;  // keys per 16-byte load
+    constexpr uint32_t LIMIT = PER * NT * kPostVec - (PER - 1);
     uint32_t lo = 0, hi = L.keys_n();  // the answer lies in [lo, hi]
     while (hi - lo > LIMIT) {
         const uint32_t step = (hi - lo + NT - 1) / NT;
@@ -485,7 +505,7 @@ __device__ __forceinline__ uint32_t start_search(const ListT &L, uint32_t sh, ui
         if (lo + (c + 1) * step <= hi) hi = lo + (c + 1) * step - 1;
         lo += c * step;
     }
-    if constexpr (ListT::kPosts) lo += Scope::sum(post_count(L.keys(), lo, hi, sh, t, tid, NT));
+    lo += Scope::sum(post_count<ListT::kKeyStride>(L.keys(), lo, hi, sh, t, tid, NT));
     return lo;
 }
 
@@ -547,8 +567,8 @@ __device__ __noinline__ bool tile_join(const ListT X, const ListT Y, uint2 *xb, 
             xa = X.window(xb, i0);
             ya = Y.window(yb, j0);
         } else {
-            xa = X.template stage<NT>(xb, i0, nx, tid);
-            ya = Y.template stage<NT>(yb, j0, ny, tid);
+            xa = X.template stage<NT>(xb, i0, nx, tid, kFull);
+            ya = Y.template stage<NT>(yb, j0, ny, tid, kFull);
             cp_async_wait_all();
             Scope::sync();
         }
