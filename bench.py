@@ -73,7 +73,8 @@ def parse():
     ap.add_argument("--autotuned", action="store_true",
                     help="time the headline with the autotuner's pick instead of the default tuning")
     ap.add_argument("--tune", default=None,
-                    help="T,G,W,CW[,JO]: fixed batched tuning instead of the default (JO: join order 0 or 1)")
+                    help="T,G,W,CW[,JO[,ESC]]: fixed batched tuning instead of the default (JO: join order 0 or 1; "
+                         "ESC: escalate_windows)")
     ap.add_argument("--no-workloads", action="store_true", help="skip the skewed and partitioned workloads")
     ap.add_argument("--no-oracle-sample", action="store_true", help="skip the oracle parity samples")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
@@ -105,7 +106,8 @@ def kernel_source_sha() -> str:
 
 
 def tune_key(t):
-    return [t["cta_threshold"], t["group_lanes"], t["group_window"], t["cta_window"], t.get("join_order", 0)]
+    return [t["cta_threshold"], t["group_lanes"], t["group_window"], t["cta_window"], t.get("join_order", 0),
+            t.get("escalate_windows", 0)]
 
 
 def kernel_traffic(kernel: str, workload: str, mode: str, tune):
@@ -625,7 +627,7 @@ def serving_bench(A, torch, dev, n_requests: int, threads: int):
            "request_pairs_max": int(sizes.max()), "slots": 8, "budgets": {}}
     rng = np.random.default_rng(77)
     gaps = rng.exponential(1.0, len(reqs))
-    big = int(1.5 * 21 * sizes.max()) + (1 << 20)  # a request of n pairs takes about 21 n bytes of arena
+    big = int(1.5 * 25 * sizes.max()) + (1 << 20)  # a request of n pairs takes about 25 n bytes of arena
     capacity = None
     for label, nbytes in (("40GB", 40 << 30), ("binding", big)):
         arena = torch.empty(nbytes, dtype=torch.uint8, device=dev)
@@ -721,7 +723,7 @@ def selection_build_only(A, torch, dev):
 def parse_tune(A, spec):
     vals = [int(x) for x in spec.split(",")]
     T, G, W, CW = vals[:4]
-    return A.april_tune(T, G, W, CW, 0, 0.0, vals[4] if len(vals) > 4 else 0)
+    return A.april_tune(T, G, W, CW, 0, 0.0, vals[4] if len(vals) > 4 else 0, vals[5] if len(vals) > 5 else 0)
 
 
 def run_leg(A, torch, ctx, dev, stream, flush, cfg, args, mode, peak, peak_kind, default_tune, ws=1, rank=0,

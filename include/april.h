@@ -269,7 +269,7 @@ void april_ctx_destroy(april_ctx *ctx);
 /* ------------------------------------------------------------------ tuning */
 
 /* Knobs of APRIL_MODE_BATCHED (a build-side addition; the paper's CPU
- * filter has none).  Defaults: {2048, 4, 16, 64, 0, -, 0}. */
+ * filter has none).  Defaults: {2048, 4, 16, 64, 0, -, 0, 0}. */
 typedef struct april_tune {
     uint32_t cta_threshold;  /* pairs with |A(r)| + |A(s)| above this ("long pairs") are joined
                                 first, each by one warp or by a whole CTA (see cta_window) */
@@ -285,6 +285,10 @@ typedef struct april_tune {
                                 the same, Sec. 4.2): 0 = AF, AA, FA (a true hit from AF takes
                                 one join); 1 = AA, AF, FA, Algorithm 2's (a true negative takes
                                 one join) */
+    uint32_t escalate_windows; /* 0, or 1..64: a join of the lane groups that still runs after
+                                this many windows is handed, at the position it reached, to a
+                                second kernel that joins it by a whole warp (first window
+                                2 * cta_window when that is below 256, else 128) */
 } april_tune;
 
 april_status april_set_tune(april_ctx *ctx, const april_tune *tune);
@@ -314,9 +318,10 @@ april_status april_autotune(april_ctx *ctx, const april_dev_sets *R, const april
 
 /* Device scratch (bytes) april_filter_pairs needs for `mode` and n pairs.
  * PLAIN and WARP need none; BATCHED and BATCHED_PACKED need 256 bytes of
- * work counters plus 12 bytes per pair (the list of long pairs and, for
- * partitioned sets, each pair's two routed entries), each part rounded up to
- * 256 bytes. */
+ * work counters plus 16 bytes per pair (the list of long pairs, for
+ * partitioned sets each pair's two routed entries, and a queue of joins
+ * handed from the lane groups to whole warps with room for a quarter of the
+ * pairs), each part rounded up to 256 bytes. */
 april_status april_filter_scratch_bytes(int mode, uint64_t n, size_t *bytes);
 
 /* Runs the APRIL intermediate filter (Algorithm 2) on n candidate pairs.
@@ -421,7 +426,7 @@ typedef struct april_server_info {
 
 /* Creates a server for sets R and S (already uploaded; they stay resident).
  * d_arena/arena_bytes: caller-allocated device memory (256-byte aligned) that
- * bounds all request buffers: a request of n pairs needs about 21 n bytes.
+ * bounds all request buffers: a request of n pairs needs about 25 n bytes.
  * max_inflight: 1..64 stream slots.  The context must outlive the server,
  * and while the server runs its worker thread reads the context's tuning:
  * leave that context to the server (no april_set_tune, april_autotune or

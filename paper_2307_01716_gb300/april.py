@@ -51,7 +51,8 @@ class april_sets_info(ctypes.Structure):
 class april_tune(ctypes.Structure):
     _fields_ = [("cta_threshold", ctypes.c_uint32), ("group_lanes", ctypes.c_uint32),
                 ("group_window", ctypes.c_uint32), ("cta_window", ctypes.c_uint32),
-                ("blocks_per_sm", ctypes.c_uint32), ("ms", ctypes.c_float), ("join_order", ctypes.c_uint32)]
+                ("blocks_per_sm", ctypes.c_uint32), ("ms", ctypes.c_float), ("join_order", ctypes.c_uint32),
+                ("escalate_windows", ctypes.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

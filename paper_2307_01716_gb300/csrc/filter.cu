@@ -72,8 +72,13 @@ constexpr uint32_t kWarpShare = 2 * (kWarpWMax + 2);
 constexpr uint32_t kSharedIv = kWarpsPerBlock * kWarpShare > 2 * kCtaBuf ? kWarpsPerBlock * kWarpShare : 2 * kCtaBuf;
 static_assert(kWarpBuf % 2 == 0 && kCtaBuf % 2 == 0, "buffers must stay 16-byte aligned");
 
-// scratch of the batched mode: counters, then the list of long pairs
-constexpr uint32_t C_BIG_COUNT = 0, C_BIG_HEAD = 1, C_CHUNK_HEAD = 2;
+// scratch of the batched mode: counters, the list of long pairs, the routed
+// entries of partitioned sets, then the queue of joins handed from the lane
+// groups to whole warps (one uint4 {pair, step, i0, j0} each, room for a
+// quarter of the pairs; when it is full a group finishes its join itself)
+constexpr uint32_t C_BIG_COUNT = 0, C_BIG_HEAD = 1, C_CHUNK_HEAD = 2, C_ESC_COUNT = 3, C_ESC_HEAD = 4;
+static inline uint64_t esc_capacity(uint64_t n) { return (n + 3) / 4; }
+constexpr uint32_t kMaxEscalateWindows = 64;
 constexpr size_t kCounterBytes = 256;
 
 __device__ __forceinline__ uint4 shfl4(const uint4 &v, uint32_t src) {
@@ -167,15 +172,20 @@ struct JoinSync {
     bool timeout;
 };
 
+// With resume, the pair's join step st0 continues from merge position
+// (ri, rj), where the lane groups left it (see k_long).
 template <class SetsT>
 __device__ __forceinline__ uint8_t warp_verdict(const SetsT &R, const SetsT &S, const typename SetsT::Desc &dr,
                                                 const typename SetsT::Desc &ds, uint2 *xs, uint2 *ys, uint32_t lane,
-                                                uint32_t w0, JoinSync &js, uint32_t jo) {
-    uint32_t st = 0;
+                                                uint32_t w0, JoinSync &js, uint32_t jo, uint32_t st0 = 0,
+                                                bool resume = false, uint32_t ri = 0, uint32_t rj = 0) {
+    uint32_t st = st0;
     for (;;) {
         const bool ov = tile_join<WarpScope, 32, kWarpWMax>(R.list(dr, step_x_f(st, jo)), S.list(ds, step_y_f(st, jo)),
-                                                            xs, ys, nullptr, lane, w0, js.bar, &js.phase, &js.timeout);
+                                                            xs, ys, nullptr, lane, w0, js.bar, &js.phase, &js.timeout,
+                                                            0, 0, resume, ri, rj);
         if (js.timeout) return APRIL_VERDICT_ERROR;
+        resume = false;
         const int v = step_outcome(st, ov, jo);
         if (v >= 0) return (uint8_t)v;
     }
@@ -419,7 +429,8 @@ __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, con
                                              const uint32_t *__restrict__ ps, uint64_t n, uint8_t *__restrict__ out,
                                              uint32_t *status, uint32_t *counters, uint32_t cta_threshold, uint2 *wbuf,
                                              uint4 *chunk_desc, uint8_t *chunk_lane, uint32_t bars, uint32_t lane,
-                                             uint32_t w0, uint32_t jo) {
+                                             uint32_t w0, uint32_t jo, uint32_t esc_windows, uint4 *esc,
+                                             uint32_t esc_cap) {
     using C = GroupCfg<G>;
     const uint32_t g = lane / G, t = lane % G, glead = g * G;
     const uint32_t gbits = (G == 32 ? kFull : ((1u << G) - 1u)) << glead;
@@ -439,6 +450,7 @@ __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, con
     uint32_t k = 0;
     uint4 dr = make_uint4(0, 0, 0, 0), ds = make_uint4(0, 0, 0, 0);
     uint32_t stage = 0, i0 = 0, j0 = 0, w = w0;
+    uint32_t nwin = 0;   // windows of the current join so far
     bool fresh = false;  // the join has just started: its start has not been searched yet
     using ListT = decltype(R.list(dr, false));
     ListT X = R.list(dr, false), Y = S.list(ds, false);
@@ -486,6 +498,7 @@ __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, con
                 stage = 0;
                 i0 = j0 = 0;
                 w = w0;
+                nwin = 0;
                 fresh = true;
                 int verdict = -1;  // steps with an empty list have no overlap
                 while (!join_lists(R, S, dr, ds, stage, X, Y, jo))
@@ -565,12 +578,27 @@ __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, con
                 i0 += split;
                 j0 += D - split;
                 w = min(w * 2u, C::WMAX);
+                if (esc_windows && ++nwin >= esc_windows) {
+                    // a long join: hand it, at the position it reached, to a
+                    // whole warp (k_long) and take the next pair, unless the
+                    // queue is full
+                    uint32_t slot = 0;
+                    if (t == 0) slot = atomicAdd(&counters[C_ESC_COUNT], 1u);
+                    slot = __shfl_sync(gbits, slot, glead);
+                    if (slot < esc_cap) {
+                        if (t == 0) esc[slot] = make_uint4(k, stage, i0, j0);
+                        active = false;
+                    } else {
+                        nwin = 0;
+                    }
+                }
             }
             if (res >= 0) {
                 int verdict = step_outcome(stage, res != 0, jo);
                 while (verdict < 0) {
                     i0 = j0 = 0;
                     w = w0;
+                    nwin = 0;
                     fresh = true;
                     if (join_lists(R, S, dr, ds, stage, X, Y, jo)) break;
                     verdict = step_outcome(stage, false, jo);
@@ -595,7 +623,7 @@ __global__ void APRIL_PERSISTENT_BOUNDS k_persistent(SetsT R, SetsT S,
                                                        uint8_t *__restrict__ out, uint32_t *status,
                                                        uint32_t cta_threshold, const uint32_t *__restrict__ big_list,
                                                        uint32_t *counters, uint32_t w0_group, uint32_t w0_cta,
-                                                       uint32_t jo) {
+                                                       uint32_t jo, uint32_t esc_windows, uint4 *esc, uint32_t esc_cap) {
     using C = GroupCfg<G>;
     __shared__ __align__(16) uint2 sm[kWarpsPerBlock * C::SHARE];
     __shared__ uint32_t s_item, s_slot;
@@ -660,7 +688,40 @@ __global__ void APRIL_PERSISTENT_BOUNDS k_persistent(SetsT R, SetsT S,
         }
     } else {
         group_engine<G>(R, S, pr, ps, n, out, status, counters, cta_threshold, wbuf, s_chunk[warp],
-                        s_chunk_lane[warp], smem_addr(&bars[C::group_bar(warp, 0)]), lane, w0_group, jo);
+                        s_chunk_lane[warp], smem_addr(&bars[C::group_bar(warp, 0)]), lane, w0_group, jo,
+                        esc_windows, esc, esc_cap);
+    }
+}
+
+// ------------------------------ K3b: joins handed over by the lane groups
+// Each warp takes the next queued join {pair, step, i0, j0} and finishes the
+// pair by whole-warp joins: that step resumes at (i0, j0) with first window
+// w0, the later steps of the join order start fresh.
+template <class SetsT>
+__global__ void __launch_bounds__(kBlock) k_long(SetsT R, SetsT S, const uint32_t *__restrict__ pr,
+                                                 const uint32_t *__restrict__ ps, uint8_t *__restrict__ out,
+                                                 uint32_t *status, const uint4 *__restrict__ esc, uint32_t *counters,
+                                                 uint32_t esc_cap, uint32_t w0, uint32_t jo) {
+    __shared__ __align__(16) uint2 sm[kWarpsPerBlock][2][kWarpBuf];
+    __shared__ uint64_t bars[kWarpsPerBlock];
+    init_barriers(bars, kWarpsPerBlock);
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    JoinSync js{smem_addr(&bars[warp]), 0u, false};
+    const uint32_t nesc = min(*((volatile uint32_t *)&counters[C_ESC_COUNT]), esc_cap);
+    for (;;) {
+        uint32_t it = 0;
+        if (lane == 0) it = atomicAdd(&counters[C_ESC_HEAD], 1u);
+        it = __shfl_sync(kFull, it, 0);
+        if (it >= nesc) break;
+        const uint4 rec = esc[it];
+        const typename SetsT::Desc dr = R.load(__ldg(pr + rec.x)), ds = S.load(__ldg(ps + rec.x));
+        const uint8_t v = warp_verdict(R, S, dr, ds, sm[warp][0], sm[warp][1], lane, w0, js, jo, rec.y, true, rec.z,
+                                       rec.w);
+        if (lane == 0) out[rec.x] = v;
+        if (js.timeout) {  // a bounded wait ran out: report and stop this warp
+            if (lane == 0) atomicOr(status, ST_TIMEOUT);
+            return;
+        }
     }
 }
 
@@ -863,7 +924,8 @@ struct GraphKey {
                sn == o.sn && d_r == o.d_r && d_s == o.d_s && out == o.out && scratch == o.scratch && n == o.n &&
                tune.cta_threshold == o.tune.cta_threshold && tune.group_lanes == o.tune.group_lanes &&
                tune.group_window == o.tune.group_window && tune.cta_window == o.tune.cta_window &&
-               tune.join_order == o.tune.join_order && grid_bin == o.grid_bin && grid_main == o.grid_main;
+               tune.join_order == o.tune.join_order && tune.escalate_windows == o.tune.escalate_windows &&
+               grid_bin == o.grid_bin && grid_main == o.grid_main;
     }
 };
 
@@ -873,6 +935,7 @@ struct april_ctx {
     int num_sms = 0;
     // occupancy of k_persistent<4, 8, 16, 32> over raw lists, then over packed lists
     int persistent_blocks_per_sm[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+    int long_blocks_per_sm = 1;  // occupancy of k_long (the larger of its two instances' limits)
     april_tune tune{};
     cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
     cudaGraphExec_t graph = nullptr;    // the batched pipeline, captured once per argument set
@@ -897,6 +960,7 @@ static april_tune default_tune() {
     t.group_window = 16;
     t.cta_window = 64;       // long pairs one per warp
     t.join_order = 0;        // AF, AA, FA
+    t.escalate_windows = 0;  // lane groups finish every join they start
     t.blocks_per_sm = 0;
     t.ms = 0.f;
     return t;
@@ -911,6 +975,7 @@ static april_status check_tune(const april_tune &t) {
     if (t.cta_window < 32 || t.cta_window > kCtaWMax || (t.cta_window & (t.cta_window - 1)))
         return fail(APRIL_ERR_INVALID_ARG, "cta_window must be a power of two in [32, 2048]");
     if (t.join_order > 1) return fail(APRIL_ERR_INVALID_ARG, "join_order must be 0 (AF AA FA) or 1 (AA AF FA)");
+    if (t.escalate_windows > kMaxEscalateWindows) return fail(APRIL_ERR_INVALID_ARG, "escalate_windows must be 0..64");
     return APRIL_OK;
 }
 
@@ -936,6 +1001,11 @@ extern "C" april_status april_ctx_create(int device, april_ctx **out) {
     APRIL_OCC(6, 16, PackedSets);
     APRIL_OCC(7, 32, PackedSets);
 #undef APRIL_OCC
+    int occ_long_raw = 1, occ_long_packed = 1;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_long_raw, k_long<RawSets>, kBlock, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_long_packed, k_long<PackedSets>, kBlock, 0);
+    c->long_blocks_per_sm = std::max(1, std::min(occ_long_raw, occ_long_packed));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_status, 256);
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, 256);
@@ -1036,7 +1106,9 @@ extern "C" april_status april_filter_scratch_bytes(int mode, uint64_t n, size_t 
         case APRIL_MODE_PLAIN:
         case APRIL_MODE_WARP: *bytes = 0; return APRIL_OK;
         case APRIL_MODE_BATCHED:
-        case APRIL_MODE_BATCHED_PACKED: *bytes = (size_t)(kCounterBytes + 3 * round256(4 * n)); return APRIL_OK;
+        case APRIL_MODE_BATCHED_PACKED:
+            *bytes = (size_t)(kCounterBytes + 3 * round256(4 * n) + round256(16 * esc_capacity(n)));
+            return APRIL_OK;
         default: return fail(APRIL_ERR_INVALID_ARG, "unknown mode");
     }
 }
@@ -1065,7 +1137,10 @@ static inline PartView part_view(const april_dev_sets *d) {
 }
 
 // Enqueues the batched pipeline on `st`: counter reset, partition routing
-// (partitioned sets only), K4 binning, K3 persistent filter.
+// (partitioned sets only), K4 binning, K3 persistent filter, and, when the
+// tuning escalates long joins, K3b for the joins the lane groups handed over.
+// `esc_windows` overrides the tuning's escalate_windows (the allocation-free
+// entry point has no room for the queue and passes 0).
 static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, const april_dev_sets *Sd,
                                    const uint32_t *d_r, const uint32_t *d_s, uint64_t n, uint8_t *out, void *scratch,
                                    bool packed, unsigned grid_bin, unsigned grid_main, cudaStream_t st,
@@ -1073,7 +1148,12 @@ static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, con
     if (!status) status = ctx->d_status;
     uint32_t *counters = (uint32_t *)scratch;
     uint32_t *big_list = (uint32_t *)((char *)scratch + kCounterBytes);
+    uint4 *esc = (uint4 *)((char *)scratch + kCounterBytes + 3 * round256(4 * n));
     const april_tune &t = ctx->tune;
+    const uint32_t escw = t.group_lanes < 32 ? t.escalate_windows : 0u;
+    const uint32_t w0_long = t.cta_window < kBlock ? std::min<uint32_t>(2 * t.cta_window, kWarpWMax) : 128u;
+    const uint32_t esc_cap = (uint32_t)esc_capacity(n);
+    const unsigned grid_long = (unsigned)std::max(1, ctx->num_sms * ctx->long_blocks_per_sm);
     cudaError_t e = cudaMemsetAsync(counters, 0, kCounterBytes, st);
     if (e != cudaSuccess) return e;
     if (Rd->parts) {
@@ -1091,7 +1171,7 @@ static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, con
 #define APRIL_LAUNCH_PACKED(G)                                                                                  \
     k_persistent<G, PackedSets><<<grid_main, kBlock, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold,   \
                                                               big_list, counters, t.group_window, t.cta_window,   \
-                                                              t.join_order)
+                                                              t.join_order, escw, esc, esc_cap)
         switch (t.group_lanes) {
             case 4: APRIL_LAUNCH_PACKED(4); break;
             case 8: APRIL_LAUNCH_PACKED(8); break;
@@ -1099,6 +1179,9 @@ static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, con
             default: APRIL_LAUNCH_PACKED(32); break;
         }
 #undef APRIL_LAUNCH_PACKED
+        if (escw)
+            k_long<<<grid_long, kBlock, 0, st>>>(R, S, d_r, d_s, out, status, esc, counters, esc_cap, w0_long,
+                                                  t.join_order);
         return cudaGetLastError();
     }
     const RawSets R{dev_set(Rd)}, S{dev_set(Sd)};
@@ -1106,7 +1189,7 @@ static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, con
 #define APRIL_LAUNCH_PERSISTENT(G)                                                                            \
     k_persistent<G, RawSets><<<grid_main, kBlock, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold,       \
                                                            big_list, counters, t.group_window, t.cta_window,      \
-                                                           t.join_order)
+                                                           t.join_order, escw, esc, esc_cap)
     switch (t.group_lanes) {
         case 4: APRIL_LAUNCH_PERSISTENT(4); break;
         case 8: APRIL_LAUNCH_PERSISTENT(8); break;
@@ -1114,6 +1197,9 @@ static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, con
         default: APRIL_LAUNCH_PERSISTENT(32); break;
     }
 #undef APRIL_LAUNCH_PERSISTENT
+    if (escw)
+        k_long<<<grid_long, kBlock, 0, st>>>(R, S, d_r, d_s, out, status, esc, counters, esc_cap, w0_long,
+                                              t.join_order);
     return cudaGetLastError();
 }
 
@@ -1487,7 +1573,8 @@ NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
 
 // The persistent kernel instance for the default tuning's lane groups.
 using PersistentRaw = void (*)(RawSets, RawSets, const uint32_t *, const uint32_t *, uint64_t, uint8_t *,
-                               uint32_t *, uint32_t, const uint32_t *, uint32_t *, uint32_t, uint32_t, uint32_t);
+                               uint32_t *, uint32_t, const uint32_t *, uint32_t *, uint32_t, uint32_t, uint32_t,
+                               uint32_t, uint4 *, uint32_t);
 static PersistentRaw noalloc_kernel(uint32_t group_lanes) {
     switch (group_lanes) {
         case 4: return k_persistent<4, RawSets>;
@@ -1557,9 +1644,10 @@ extern "C" april_status april_filter_pairs_noalloc(const april_dev_sets *R, cons
     const unsigned grid_bin = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)nd.num_sms * 8);
     const unsigned grid_main = (unsigned)std::max(1, nd.num_sms * nd.blocks_per_sm);
     k_bin<<<grid_bin, 256, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, status, t.cta_threshold, big_list, counters);
+    // no escalation: the static array has no room for the queue of handed-over joins
     noalloc_kernel(t.group_lanes)<<<grid_main, kBlock, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, status,
                                                                 t.cta_threshold, big_list, counters, t.group_window,
-                                                                t.cta_window, t.join_order);
+                                                                t.cta_window, t.join_order, 0u, nullptr, 0u);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "april_filter_pairs_noalloc launch");
     return APRIL_OK;

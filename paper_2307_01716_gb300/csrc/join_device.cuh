@@ -516,14 +516,17 @@ __device__ __forceinline__ uint32_t start_search(const ListT &L, uint32_t sh, ui
 // WMAX.  Every thread of the group must call it with the same arguments.
 // For raw lists the window is staged by two bulk copies issued by thread 0
 // and completed on the mbarrier `bar` (phase bit in *phase, flipped per
-// window); a wait that runs out sets *timeout and ends the join.
+// window); a wait that runs out sets *timeout and ends the join.  A join
+// handed over at merge position (ri, rj) of an earlier run (resume) starts
+// there, without a search.
 template <class Scope, uint32_t NT, uint32_t WMAX, class ListT, int PRED = kOverlap>
 __device__ __noinline__ bool tile_join(const ListT X, const ListT Y, uint2 *xb, uint2 *yb, uint32_t *slot,
                                        uint32_t tid, uint32_t w0, uint32_t bar, uint32_t *phase, bool *timeout,
-                                       uint32_t sx = 0, uint32_t sy = 0) {
+                                       uint32_t sx = 0, uint32_t sy = 0, bool resume = false, uint32_t ri = 0,
+                                       uint32_t rj = 0) {
     const uint32_t n = X.n, m = Y.n;
     if (PRED == kContain && n > 0 && m == 0) return true;  // nothing can contain X
-    uint32_t i0 = 0, j0 = 0, w = w0;
+    uint32_t i0 = resume ? ri : 0u, j0 = resume ? rj : 0u, w = w0;
     // Start each list at (or, for compressed lists, at a block boundary
     // before) its first interval that can meet the other one: an interval of
     // Y ending before X's first start meets no interval of X (nor contains
@@ -531,7 +534,7 @@ __device__ __noinline__ bool tile_join(const ListT X, const ListT Y, uint2 *xb, 
     // (0, 0) would pass over those intervals, and a merge started anywhere
     // before the first interval that can meet finds the same overlaps, so the
     // verdict is unchanged; only lists longer than a window search.
-    if (n && m && (n > w0 || m > w0)) {
+    if (!resume && n && m && (n > w0 || m > w0)) {
         const uint32_t xs = X.first_start() >> sx, ys = Y.first_start() >> sy;
         if (PRED == kOverlap) {
             if (n > w0) i0 = X.start_of(start_search<Scope, NT>(X, sx, ys, tid));

@@ -157,19 +157,23 @@ def test_full_size_config3_sampled(torch_cuda, ctx):
     assert np.array_equal(got[idx], _data.oracle_sample(w, idx))
 
 
+@pytest.mark.parametrize("escalate", [0, 1, 3])
 @pytest.mark.parametrize("long_window", [32, 128, 256, 2048])
 @pytest.mark.parametrize("threshold", [0, 64, 0xFFFFFFFF])
 @pytest.mark.parametrize("group", [(4, 4), (4, 32), (8, 8), (8, 64), (16, 16), (16, 128), (32, 32), (32, 256)])
-def test_batched_tunings(torch_cuda, ctx, threshold, group, long_window):
+def test_batched_tunings(torch_cuda, ctx, threshold, group, long_window, escalate):
     """Every pair joined as a long pair (threshold 0), a mix, or none; long
     pairs by one warp (first window 32 or 128) or by the whole CTA (256 or
-    2048); every group size with its smallest and largest first window."""
+    2048); every group size with its smallest and largest first window; and
+    joins of the lane groups handed to whole warps after 1 or 3 windows."""
     if threshold == 0xFFFFFFFF and long_window != 256:
         pytest.skip("no long pairs: the long-pair scope is unused")
+    if escalate and (threshold == 0 or group[0] == 32 or long_window == 2048):
+        pytest.skip("no lane-group joins to hand over, or the case adds nothing")
     w = _data.workload(3, 0.01)
     _, _, dR, dS = _device_sets(w)
     saved = ctx.get_tune()
-    t = A.april_tune(threshold, group[0], group[1], long_window, 0, 0.0)
+    t = A.april_tune(threshold, group[0], group[1], long_window, 0, 0.0, 0, escalate)
     ctx.set_tune(t)
     try:
         got = run_filter(torch_cuda, ctx, dR, dS, w.pr, w.ps, "batched")

@@ -88,7 +88,10 @@ def test_alone_equals_mixed_equals_oracle(torch_cuda, env):
 def test_budget_limits_admission(torch_cuda, env):
     w, ctx, dR, dS, reqs = env
     sizes = sorted(len(q.pr) for q in reqs)
-    budget = max(24 * sizes[-1] + 8192, 3 * (24 * sizes[len(sizes) // 2] + 8192))
+
+    def need(n):  # a request's buffers: pairs, verdicts, the batched scratch, status (each 256-aligned)
+        return 9 * n + ctx.scratch_bytes(A.MODE_BATCHED, n) + 8192
+    budget = max(need(sizes[-1]), 3 * need(sizes[len(sizes) // 2]))
     budget = (budget + 255) // 256 * 256
     alone, _ = _serve(torch_cuda, ctx, dR, dS, reqs, 1, 1 << 28, alone=True)
     mixed, info = _serve(torch_cuda, ctx, dR, dS, reqs, 8, budget, alone=False)
