@@ -269,7 +269,7 @@ void april_ctx_destroy(april_ctx *ctx);
 /* ------------------------------------------------------------------ tuning */
 
 /* Knobs of APRIL_MODE_BATCHED (a build-side addition; the paper's CPU
- * filter has none).  Defaults: {2048, 4, 16, 64, 0, -, 0, 0}. */
+ * filter has none).  Defaults: {2048, 4, 16, 128, 0, -, 0, 0}. */
 typedef struct april_tune {
     uint32_t cta_threshold;  /* pairs with |A(r)| + |A(s)| above this ("long pairs") are joined
                                 first, each by one warp or by a whole CTA (see cta_window) */
@@ -305,8 +305,8 @@ april_status april_ctx_graph_stats(const april_ctx *ctx, uint64_t *captures, uin
  * fastest in the context, and returns it in *out (candidates: cta_threshold in
  * {2048, 4096, 8192, 16384, none} x (group_lanes, group_window) in
  * {(4,8), (4,16), (8,16), (8,32), (16,32), (16,64), (32,64)} x long pairs by a
- * warp (cta_window 64) or by the CTA (the context's cta_window if >= 256, else
- * 256) x join_order in {0, 1}).  The context's current tuning is timed
+ * warp (cta_window 64 or 128) or by the CTA (the context's cta_window if >= 256,
+ * else 256) x join_order in {0, 1}).  The context's current tuning is timed
  * first and is kept unless a candidate is more than 2% faster, so that
  * repeated runs settle on the same tuning.  Arguments as for
  * april_filter_pairs; synchronizes `stream`. */

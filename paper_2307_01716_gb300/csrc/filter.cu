@@ -958,7 +958,7 @@ static april_tune default_tune() {
     t.cta_threshold = 2048;  // the shape the autotuner picks on the paper-scale and skewed workloads
     t.group_lanes = 4;
     t.group_window = 16;
-    t.cta_window = 64;       // long pairs one per warp
+    t.cta_window = 128;      // long pairs one per warp, first window 128
     t.join_order = 0;        // AF, AA, FA
     t.escalate_windows = 0;  // lane groups finish every join they start
     t.blocks_per_sm = 0;
@@ -1446,8 +1446,8 @@ extern "C" april_status april_autotune(april_ctx *ctx, const april_dev_sets *R, 
     // times differ by noise
     float saved_ms = 1e30f;
     rc = time_tune(saved, saved_ms);
-    // long pairs joined by one warp (first window 64) or by the whole CTA
-    const uint32_t long_windows[] = {64u, saved.cta_window >= kBlock ? saved.cta_window : kBlock};
+    // long pairs joined by one warp (first window 64 or 128) or by the whole CTA
+    const uint32_t long_windows[] = {64u, 128u, saved.cta_window >= kBlock ? saved.cta_window : kBlock};
     for (uint32_t jo = 0; jo < 2 && rc == APRIL_OK; ++jo)
     for (uint32_t T : thresholds) {
         for (const auto &gw : groups)
