@@ -269,7 +269,10 @@ void april_ctx_destroy(april_ctx *ctx);
 /* ------------------------------------------------------------------ tuning */
 
 /* Knobs of APRIL_MODE_BATCHED (a build-side addition; the paper's CPU
- * filter has none).  Defaults: {2048, 4, 16, 128, 0, -, 0, 0}. */
+ * filter has none).  Defaults: {0xFFFFFFFF, 4, 32, 128, 0, -, 0, 0}: every
+ * pair joined by a group of 4 lanes with windows of 32 intervals per list,
+ * galloping (a window that advances one list only is followed by a search of
+ * that list); the long-pair scope (cta_threshold, cta_window) is off. */
 typedef struct april_tune {
     uint32_t cta_threshold;  /* pairs with |A(r)| + |A(s)| above this ("long pairs") are joined
                                 first, each by one warp or by a whole CTA (see cta_window) */
@@ -653,12 +656,15 @@ april_status april_host_filter(const april_sets *R, const april_sets *S, const u
  * join started at each list's first interval whose last cell reaches the
  * other list's first start (found by binary search; the sequential merge from
  * the front passes over the intervals before it without a verdict).  The
+ * merge gallops: after 16 consecutive advances of one list it jumps, by
+ * binary search, to that list's first interval whose last cell reaches the
+ * other list's current start (the intervals passed over meet nothing).  The
  * verdicts equal april_host_filter's.  consumed[k] counts, for every join
- * that ran, the intervals the merge reads from the start positions plus the
- * search's probes (the bit width of each list's length): the bytes model of
- * the kernels' reading, used for their roofline.  (The kernels' lane groups
- * over raw lists end their search up to two probe spacings early and start
- * that many intervals sooner; the verdicts are the same.) */
+ * that ran, the intervals the merge reads plus the probes of every search
+ * (the bit width of the searched length): the bytes model of the kernels'
+ * reading, used for their roofline.  (The kernels start up to 16 intervals
+ * before the exact start and gallop after a whole window that advanced one
+ * list only, so they read at least this much; the verdicts are the same.) */
 april_status april_host_filter_searched(const april_sets *R, const april_sets *S, const uint32_t *pr,
                                         const uint32_t *ps, uint64_t n, uint32_t n_threads, uint8_t *verdict,
                                         uint64_t *consumed);

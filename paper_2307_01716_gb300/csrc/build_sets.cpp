@@ -763,12 +763,18 @@ bool host_join(const uint32_t *X, uint32_t nx, const uint32_t *Y, uint32_t ny, u
     return false;
 }
 
-// The same join started at the searched start the GPU kernels look for: each
-// list at its first interval whose last cell reaches the other list's first
-// start (the merge from the front would pass over the intervals before it
-// without a verdict).  *used counts the intervals the merge reads from there
-// plus a binary search per list (bit width of its length, in probed
-// intervals).
+// The same join as the GPU kernels read it: each list starts at its first
+// interval whose last cell reaches the other list's first start (the merge
+// from the front would pass over the intervals before it without a verdict),
+// and the merge gallops: once one list has advanced kGallopRun times in a row
+// it jumps to its first interval whose last cell reaches the other list's
+// current start (the intervals it passes over meet nothing either).  The
+// kernels gallop after a window that advanced one list only, so they read at
+// least this much.  *used counts the intervals the merge reads plus a binary
+// search for every start and jump (bit width of the searched length, in
+// probed intervals).
+constexpr uint32_t kGallopRun = 16;  // one post of the skip index per 16 intervals
+
 uint32_t lower_bound_last(const uint32_t *L, uint32_t n, uint32_t t) {
     uint32_t lo = 0, hi = n;
     while (lo < hi) {
@@ -783,19 +789,41 @@ uint32_t bit_width(uint32_t v) { return v ? 32u - (uint32_t)__builtin_clz(v) : 0
 
 bool host_join_searched(const uint32_t *X, uint32_t nx, const uint32_t *Y, uint32_t ny, uint64_t *used) {
     if (!nx || !ny) return false;
-    const uint32_t i0 = lower_bound_last(X, nx, Y[0]), j0 = lower_bound_last(Y, ny, X[0]);
+    uint32_t i = lower_bound_last(X, nx, Y[0]), j = lower_bound_last(Y, ny, X[0]);
     *used += bit_width(nx) + bit_width(ny);
-    uint32_t i = i0, j = j0;
-    while (i < nx && j < ny) {
-        uint32_t xs = X[2 * i], xl = X[2 * i + 1] - 1u, ys = Y[2 * j], yl = Y[2 * j + 1] - 1u;
+    if (i >= nx || j >= ny) return false;
+    uint64_t read = 2;   // X[i] and Y[j]
+    uint32_t run = 0;    // consecutive advances of the same list
+    bool run_x = false;  // ... of X
+    for (;;) {
+        const uint32_t xs = X[2 * i], xl = X[2 * i + 1] - 1u, ys = Y[2 * j], yl = Y[2 * j + 1] - 1u;
         if (xs <= yl && ys <= xl) {
-            *used += (uint64_t)(i - i0) + 1 + (j - j0) + 1;
+            *used += read;
             return true;
         }
-        if (xl <= yl) ++i;
-        else ++j;
+        const bool adv_x = xl <= yl;
+        run = adv_x == run_x ? run + 1 : 1;
+        run_x = adv_x;
+        if (adv_x) {
+            if (++i >= nx) break;
+            if (run >= kGallopRun) {
+                *used += bit_width(nx - i);
+                i += lower_bound_last(X + 2 * (size_t)i, nx - i, ys);
+                run = 0;
+                if (i >= nx) break;
+            }
+        } else {
+            if (++j >= ny) break;
+            if (run >= kGallopRun) {
+                *used += bit_width(ny - j);
+                j += lower_bound_last(Y + 2 * (size_t)j, ny - j, xs);
+                run = 0;
+                if (j >= ny) break;
+            }
+        }
+        ++read;
     }
-    *used += (uint64_t)std::min(i + 1, nx) - i0 + std::min(j + 1, ny) - j0;
+    *used += read;
     return false;
 }
 

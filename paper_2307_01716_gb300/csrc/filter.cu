@@ -349,39 +349,38 @@ __device__ __forceinline__ bool join_lists(const SetsT &R, const SetsT &S, const
     return X.n != 0 && Y.n != 0;
 }
 
-// The start search of a fresh join for every group of a warp at once
-// (warp-collective; a group with need == false takes no part): X is searched
-// for its first interval whose last cell reaches Y's first start, and Y for
-// X's first start, both lists in the same rounds, over the lists' search
-// keys (the skip index's posts for raw lists, block anchors for compressed
-// lists; see RawList / PackedList).  Each probing round every lane probes P
-// evenly spaced keys per list (fan-out G*P) and the group counts the probes
-// below the target (a prefix, the keys being sorted), which leaves one gap
-// of the spacing.  Over a skip index the probing stops once both ranges fit
-// one vector round of 4 G kPostVec posts, and that round ends the search; a
-// list of up to about 16 * 4 G kPostVec intervals takes that round alone.
-// Only lists longer than a first window (w0) are searched.
+// The start searches of every group of a warp at once (warp-collective;
+// `need` names a group's lists to search, bit 0 X and bit 1 Y, 0 for none).
+// A fresh join searches each list longer than a first window for its first
+// interval whose last cell reaches the other list's first start; a galloping
+// search (a window advanced one list only) searches that list, from its
+// merge position, against the target `gt` (the other list's current start).
+// Both lists are searched in the same rounds over their search keys (the skip
+// index's posts for raw lists, block anchors for compressed lists; see
+// RawList / PackedList).  Each probing round every lane probes P evenly spaced
+// keys per list (fan-out G*P) and the group counts the probes below the
+// target (a prefix, the keys being sorted), which leaves one gap of the
+// spacing.  The probing stops once both ranges fit one vector round of
+// 4 G kPostVec keys, and that round ends the search.
 #ifndef APRIL_SEARCH_MIN
 #define APRIL_SEARCH_MIN 0
 #endif
 constexpr uint32_t kSearchProbes = 1;
-constexpr uint32_t kSearchMin = APRIL_SEARCH_MIN;  // lists up to this long are not searched
+constexpr uint32_t kSearchMin = APRIL_SEARCH_MIN;  // lists up to this long are not searched by fresh joins
 template <uint32_t G, class ListT>
-__device__ __forceinline__ void dual_search(const ListT &X, const ListT &Y, bool need, uint32_t w0, uint32_t t,
-                                            uint32_t gbits, uint32_t &i0, uint32_t &j0) {
+__device__ __forceinline__ void dual_search(const ListT &X, const ListT &Y, uint32_t need, bool fresh, uint32_t gt,
+                                            uint32_t t, uint32_t gbits, uint32_t &i0, uint32_t &j0) {
     constexpr uint32_t P = kSearchProbes, F = G * P;
     // probing stops once a range fits one vector round (post_count) over the
     // skip index (raw lists) or the block anchors (compressed lists)
     constexpr uint32_t PER = 4 / ListT::kKeyStride;  // keys per 16-byte load
     constexpr uint32_t LIMIT = PER * G * kPostVec - (PER - 1);
-    const uint32_t nX = X.n, nY = Y.n;
-    const uint32_t smin = max(w0, kSearchMin);
-    const bool sx = need && nX > smin, sy = need && nY > smin;
-    uint32_t loX = 0, hiX = sx ? X.keys_n() : 0;
-    uint32_t loY = 0, hiY = sy ? Y.keys_n() : 0;
-    // Y's first start (X's key), X's first start (Y's key), loaded with the
+    const bool sx = need & 1u, sy = need & 2u;
+    uint32_t loX = sx ? X.key_lo(i0) : 0, hiX = sx ? X.keys_n() : 0;
+    uint32_t loY = sy ? Y.key_lo(j0) : 0, hiY = sy ? Y.keys_n() : 0;
+    // the targets: a fresh join's other list's first start, loaded with the
     // first round's probes, whose positions do not depend on them
-    const uint32_t kx = sx ? Y.first_start() : 0u, ky = sy ? X.first_start() : 0u;
+    const uint32_t kx = sx ? (fresh ? Y.first_start() : gt) : 0u, ky = sy ? (fresh ? X.first_start() : gt) : 0u;
     while (__any_sync(kFull, hiX - loX > LIMIT || hiY - loY > LIMIT)) {  // lo <= hi throughout
         const bool ax = hiX - loX > LIMIT, ay = hiY - loY > LIMIT;
         const uint32_t sX = ax ? (hiX - loX + F - 1) / F : 1, sY = ay ? (hiY - loY + F - 1) / F : 1;
@@ -420,8 +419,8 @@ __device__ __forceinline__ void dual_search(const ListT &X, const ListT &Y, bool
         loX += v & 0xFFFFu;
         loY += v >> 16;
     }
-    if (sx) i0 = X.start_of(loX);
-    if (sy) j0 = Y.start_of(loY);
+    if (sx) i0 = max(i0, X.start_of(loX));
+    if (sy) j0 = max(j0, Y.start_of(loY));
 }
 
 template <uint32_t G, class SetsT>
@@ -452,6 +451,7 @@ __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, con
     uint32_t stage = 0, i0 = 0, j0 = 0, w = w0;
     uint32_t nwin = 0;   // windows of the current join so far
     bool fresh = false;  // the join has just started: its start has not been searched yet
+    uint32_t gal = 0, gt = 0;  // a galloping search due (bit 0: X, bit 1: Y) and its target
     using ListT = decltype(R.list(dr, false));
     ListT X = R.list(dr, false), Y = S.list(ds, false);
 
@@ -514,9 +514,16 @@ __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, con
 
         // -------- a join that has just started skips, in each list longer
         // than a window, the intervals ending before the other list's first
-        // start (they meet nothing; the merge would pass over them)
-        if (__any_sync(kFull, active && fresh)) dual_search<G>(X, Y, active && fresh, w0, t, gbits, i0, j0);
+        // start (they meet nothing; the merge would pass over them); a list
+        // that the last window advanced alone skips those ending before the
+        // other list's current start (galloping, see tile_join)
+        if (__any_sync(kFull, active && (fresh || gal))) {
+            const uint32_t smin = max(w0, kSearchMin);
+            const uint32_t nd = !active ? 0u : fresh ? (uint32_t)(X.n > smin) | ((uint32_t)(Y.n > smin) << 1) : gal;
+            dual_search<G>(X, Y, nd, fresh, gt, t, gbits, i0, j0);
+        }
         fresh = false;
+        gal = 0;
         const uint32_t nX = X.n, nY = Y.n;
         const bool ran_out = active && (i0 >= nX || j0 >= nY);  // the search passed a whole list
 
@@ -578,6 +585,15 @@ __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, con
                 i0 += split;
                 j0 += D - split;
                 w = min(w * 2u, C::WMAX);
+                // the windows stay intact until the next pass's staging,
+                // which follows that pass's first warp vote
+                if (split == 0 && nY - j0 > w) {
+                    gal = 2u;
+                    gt = lds1(xa);  // X's current start
+                } else if (split == D && nX - i0 > w) {
+                    gal = 1u;
+                    gt = lds1(ya);  // Y's current start
+                }
                 if (esc_windows && ++nwin >= esc_windows) {
                     // a long join: hand it, at the position it reached, to a
                     // whole warp (k_long) and take the next pair, unless the
@@ -955,10 +971,13 @@ static int group_index(uint32_t g) { return g == 4 ? 0 : g == 8 ? 1 : g == 16 ? 
 
 static april_tune default_tune() {
     april_tune t{};
-    t.cta_threshold = 2048;  // the shape the autotuner picks on the paper-scale and skewed workloads
+    // the shape the autotuner picks on the paper-scale, skewed and partitioned
+    // workloads: every pair in groups of 4 lanes with full windows from the
+    // start (with galloping, the lane groups also take the long pairs)
+    t.cta_threshold = 0xffffffffu;
     t.group_lanes = 4;
-    t.group_window = 16;
-    t.cta_window = 128;      // long pairs one per warp, first window 128
+    t.group_window = 32;
+    t.cta_window = 128;      // with a threshold set: long pairs one per warp, first window 128
     t.join_order = 0;        // AF, AA, FA
     t.escalate_windows = 0;  // lane groups finish every join they start
     t.blocks_per_sm = 0;
@@ -1413,7 +1432,8 @@ extern "C" april_status april_autotune(april_ctx *ctx, const april_dev_sets *R, 
     }
     cudaStream_t st = (cudaStream_t)stream;
     const uint32_t thresholds[] = {2048, 4096, 8192, 16384, 0xffffffffu};
-    const uint32_t groups[][2] = {{4, 8}, {4, 16}, {8, 16}, {8, 32}, {16, 32}, {16, 64}, {32, 64}};
+    const uint32_t groups[][2] = {{4, 8}, {4, 16}, {4, 32}, {8, 16}, {8, 32}, {8, 64}, {16, 32}, {16, 64}, {16, 128},
+                                  {32, 64}};
     const april_tune saved = ctx->tune;
     april_tune best = saved;
     float best_ms = 1e30f;

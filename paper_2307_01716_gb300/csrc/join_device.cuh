@@ -370,6 +370,12 @@ struct RawList {
     __device__ __forceinline__ uint32_t key(uint32_t q) const { return __ldg(pk + q); }
     __device__ __forceinline__ const uint32_t *keys() const { return pk; }
     __device__ __forceinline__ uint32_t start_of(uint32_t c) const { return c ? pb() + 16u * (c - 1) + 1u : 0u; }
+    // The largest post count c with start_of(c) <= j (j < n): a search from
+    // merge position j counts the posts from there on.
+    __device__ __forceinline__ uint32_t key_lo(uint32_t j) const {
+        const uint32_t b = pb();
+        return j > b ? (j - b - 1) / 16 + 1 : 0u;
+    }
 };
 
 struct PackedList {
@@ -446,6 +452,7 @@ struct PackedList {
     __device__ __forceinline__ uint32_t key(uint32_t q) const { return __ldg(&blocks[q].x); }
     __device__ __forceinline__ const uint32_t *keys() const { return (const uint32_t *)blocks; }
     __device__ __forceinline__ uint32_t start_of(uint32_t c) const { return c ? 16u * (c - 1) : 0u; }
+    __device__ __forceinline__ uint32_t key_lo(uint32_t j) const { return j / 16 + 1; }  // start_of(.) <= j < n
 };
 
 // The final round of a start search over sorted keys (a skip index, or block
@@ -489,12 +496,16 @@ __device__ __forceinline__ uint32_t post_count(const uint32_t *keys, uint32_t lo
 // sorted), which leaves one gap of the spacing; with NT = 32 a list of 10^4
 // keys takes three rounds.  Over a skip index the probing stops once the
 // range fits one vector round (post_count), which ends the search.  Every
-// thread of the group gets the same answer.
+// thread of the group gets the same answer.  A search from a merge position
+// j passes lo0 = L.key_lo(j) and counts the keys from there on (the keys
+// before lo0 lie before j); the merge then resumes at the larger of j and
+// L.start_of(answer).
 template <class Scope, uint32_t NT, class ListT>
-__device__ __forceinline__ uint32_t start_search(const ListT &L, uint32_t sh, uint32_t t, uint32_t tid) {
+__device__ __forceinline__ uint32_t start_search(const ListT &L, uint32_t sh, uint32_t t, uint32_t tid,
+                                                 uint32_t lo0 = 0) {
     constexpr uint32_t PER = 4 / ListT::kKeyStride;  // keys per 16-byte load
     constexpr uint32_t LIMIT = PER * NT * kPostVec - (PER - 1);
-    uint32_t lo = 0, hi = L.keys_n();  // the answer lies in [lo, hi]
+    uint32_t lo = lo0, hi = L.keys_n();  // the answer lies in [lo, hi]
     while (hi - lo > LIMIT) {
         const uint32_t step = (hi - lo + NT - 1) / NT;
         const uint32_t q = lo + (tid + 1) * step - 1;
@@ -533,19 +544,36 @@ __device__ __noinline__ bool tile_join(const ListT X, const ListT Y, uint2 *xb, 
     // one), and likewise for X against Y's first start.  The merge from
     // (0, 0) would pass over those intervals, and a merge started anywhere
     // before the first interval that can meet finds the same overlaps, so the
-    // verdict is unchanged; only lists longer than a window search.
+    // verdict is unchanged; only lists longer than a window search.  `need`
+    // names the lists to search before the next window (bit 0: X, against
+    // target tx; bit 1: Y, against ty).
+    uint32_t need = 0, tx = 0, ty = 0;
     if (!resume && n && m && (n > w0 || m > w0)) {
-        const uint32_t xs = X.first_start() >> sx, ys = Y.first_start() >> sy;
+        tx = Y.first_start() >> sy;
+        ty = X.first_start() >> sx;
         if (PRED == kOverlap) {
-            if (n > w0) i0 = X.start_of(start_search<Scope, NT>(X, sx, ys, tid));
+            need = n > w0 ? 1u : 0u;
         } else {
             static_assert(PRED == kOverlap || ListT::kRandomAccess, "containment joins read raw lists");
             if constexpr (ListT::kRandomAccess)
-                if (((__ldg(&X.p->y) - 1u) >> sx) < ys) return true;  // X's first interval ends before Y starts
+                if (((__ldg(&X.p->y) - 1u) >> sx) < tx) return true;  // X's first interval ends before Y starts
         }
-        if (m > w0) j0 = Y.start_of(start_search<Scope, NT>(Y, sy, xs, tid));
+        if (m > w0) need |= 2u;
     }
     while (i0 < n && j0 < m) {
+        // the searches, one call site for both lists (the group agrees on need)
+#pragma unroll 1
+        while (need) {
+            const bool sideY = !(need & 1u);
+            need &= need - 1u;
+            const ListT L = sideY ? Y : X;
+            const uint32_t pos = sideY ? j0 : i0;
+            const uint32_t c = start_search<Scope, NT>(L, sideY ? sy : sx, sideY ? ty : tx, tid, L.key_lo(pos));
+            const uint32_t at = max(pos, L.start_of(c));
+            if (sideY) j0 = at;
+            else i0 = at;
+        }
+        if (i0 >= n || j0 >= m) break;
         const uint32_t nx = min(w, n - i0), ny = min(w, m - j0);
         uint32_t xa, ya;
         if constexpr (ListT::kBulk) {
@@ -587,11 +615,31 @@ __device__ __noinline__ bool tile_join(const ListT X, const ListT Y, uint2 *xb, 
         const uint32_t owner = (D - 1) >> (__ffs(per) - 1);  // walks the window's last diagonal
         uint32_t state;
         const bool found = window_walk<WMAX / NT, PRED>(xa, nx, ya, ny, w, D, per, tid * per, state);
+        // the starts of the window's first intervals, read before the vote
+        // (after it the next window may overwrite the buffers)
+        const uint32_t xs0 = PRED == kOverlap ? lds1(xa) : 0u, ys0 = PRED == kOverlap ? lds1(ya) : 0u;
         if (Scope::vote(found, state, owner, slot)) return true;
         if (D == nx + ny || state == 0xffffffffu) return false;  // a list ran out (violations were seen in the walk)
         i0 += state;
         j0 += D - state;
         w = min(w * 2u, WMAX);
+        if constexpr (PRED == kOverlap) {
+            // Galloping: a window that advanced one list only (its every
+            // interval ended before the other list's current one starts) is
+            // likely followed by more of the same, as where a list of a few
+            // intervals meets one of 10^5.  The lagging list then searches
+            // from its merge position for its first interval that ends at or
+            // after the other's current start; the ones it skips meet nothing
+            // (the same argument as the start search), and a merge resumed
+            // before the first that can meet finds the same overlaps.
+            if (state == 0 && m - j0 > w) {
+                need = 2u;
+                ty = xs0;
+            } else if (state == D && n - i0 > w) {
+                need = 1u;
+                tx = ys0;
+            }
+        }
     }
     return PRED == kContain && i0 < n;  // Y ended before X: the rest of X has no container
 }

@@ -110,9 +110,10 @@ def test_empty_set():
 @pytest.mark.parametrize("cfg,scale", [(1, 1.0), (3, 0.01)])
 def test_searched_host_filter(cfg, scale):
     """The kernels' reading (joins in the order AF, AA, FA, each from its
-    searched start) keeps Algorithm 2's verdicts; per pair it reads no more
-    than a full scan of the three joins plus the probes, and in total less
-    than sequential Algorithm 2."""
+    searched start, galloping) keeps Algorithm 2's verdicts; per pair it
+    reads no more than a full scan of the three joins plus the probes of the
+    start searches and of at most one jump per 16 intervals read (each at
+    most 32 probes), and in total less than sequential Algorithm 2."""
     from tests import _data
     w = _data.workload(cfg, scale)
     g = A.global_grid(w.order)
@@ -126,7 +127,7 @@ def test_searched_host_filter(cfg, scale):
     bw = lambda v: np.floor(np.log2(np.maximum(v, 1))).astype(np.int64) + (v > 0)
     probes = 3 * (bw(np.maximum(a_r, f_r)[w.pr]) + bw(np.maximum(a_s, f_s)[w.ps]))
     full = 2 * a_r[w.pr].astype(np.int64) + 2 * a_s[w.ps] + f_r[w.pr] + f_s[w.ps]
-    assert np.all(c1.astype(np.int64) <= full + probes)
+    assert np.all(c1.astype(np.int64) <= full + probes + 2 * full)
     assert c1.sum() < c0.sum()
 
 

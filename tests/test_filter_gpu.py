@@ -139,11 +139,10 @@ def test_full_size_config3_sampled(torch_cuda, ctx):
     lists up to ~10^5 intervals) in the batched mode with the default tuning,
     as the benchmark runs it: every verdict equals host Algorithm 2, and a
     seeded oracle sample of 1,000 pairs -- 200 of them long pairs
-    (|A(r)| + |A(s)| above the long-pair threshold, joined by whole warps) --
-    equals the oracle."""
+    (|A(r)| + |A(s)| > 2048, where the joins gallop over lists of up to 10^5
+    intervals) -- equals the oracle."""
     w = _data.workload(3, 1.0)
     R, S, dR, dS = _device_sets(w)
-    t = ctx.get_tune()
     got = run_filter(torch_cuda, ctx, dR, dS, w.pr, w.ps, "batched")
     hv, _ = A.april_host_filter(R, S, w.pr, w.ps)
     assert np.array_equal(got, hv), np.nonzero(got != hv)[0][:10]
@@ -151,8 +150,8 @@ def test_full_size_config3_sampled(torch_cuda, ctx):
     a_s, _ = S.lengths()
     cost = a_r[w.pr].astype(np.int64) + a_s[w.ps]
     rng = np.random.default_rng(31)
-    long_idx = rng.choice(np.nonzero(cost > t.cta_threshold)[0], 200, replace=False)
-    short_idx = rng.choice(np.nonzero(cost <= t.cta_threshold)[0], 800, replace=False)
+    long_idx = rng.choice(np.nonzero(cost > 2048)[0], 200, replace=False)
+    short_idx = rng.choice(np.nonzero(cost <= 2048)[0], 800, replace=False)
     idx = np.sort(np.concatenate([long_idx, short_idx]))
     assert np.array_equal(got[idx], _data.oracle_sample(w, idx))
 

@@ -178,3 +178,97 @@ def test_random_lists_packed_equal_host(torch_cuda, ctx, data, tune):
     finally:
         ctx.set_tune(saved)
     assert np.array_equal(got, want), np.flatnonzero(got != want)[:10]
+
+
+_BAND = 1 << 20  # galloping lists hold cells of q in [0, _BAND): 8 q .. 8 q + 7
+_COMMON = np.linspace(1000, _BAND - 1000, 64).astype(np.int64)  # q's every dense list holds
+
+
+def _gallop_list(rng, k, dense, cross):
+    """A dense list: intervals [8 q, 8 q + 4) for k random q and every q of
+    _COMMON.  A sparse list: intervals [8 q + 5, 8 q + 7) for k random q (they
+    meet no dense interval), and, if cross, the one at a random q = c of
+    _COMMON replaced by [8 c + 2, 8 c + 6), which meets every dense list."""
+    q = np.sort(rng.choice(_BAND, k, replace=False)).astype(np.int64)
+    if dense:
+        q = np.union1d(q, _COMMON)
+        iv = np.stack([8 * q, 8 * q + 4], axis=1)
+    else:
+        iv = np.stack([8 * q + 5, 8 * q + 7], axis=1)
+        if cross:
+            c = int(rng.choice(_COMMON))
+            iv = np.concatenate([iv[q != c], [[8 * c + 2, 8 * c + 6]]])
+            iv = iv[np.argsort(iv[:, 0])]
+    return iv.astype(np.uint64)
+
+
+def _gallop_sets(rng, n, dense):
+    """Objects on order 16 whose A-lists are dense (500 to 20,000 intervals)
+    or sparse (1 to 40, a third of them crossing); F-lists are random
+    sub-intervals, as for _random_sets."""
+    A_, F_ = [], []
+    for _ in range(n):
+        if dense:
+            a = _gallop_list(rng, int(rng.integers(500, 20000)), True, False)
+        else:
+            a = _gallop_list(rng, int(rng.integers(1, 40)), False, rng.random() < 0.35)
+        A_.append(a)
+        F_.append(_inner_list(rng, a))
+    return A.april_sets_from_lists(16, A_, F_)
+
+
+@pytest.fixture(scope="module")
+def gallop_data():
+    """A set of objects with a few intervals each spread over the whole curve
+    and a set of objects with thousands, where a merge join spends nearly all
+    its steps on the long list and the kernels gallop over it; pairs in both
+    roles (the short list as X and as Y)."""
+    rng = np.random.default_rng(77)
+    Sp = _gallop_sets(rng, 300, False)
+    De = _gallop_sets(rng, 300, True)
+    n = 12_000
+    pr = rng.integers(0, 300, n).astype(np.uint32)
+    ps = rng.integers(0, 300, n).astype(np.uint32)
+    return Sp, De, pr, ps
+
+
+@pytest.mark.parametrize("mode,tune", [("batched", None), ("batched", (0, 4, 32, 128)), ("batched", (0, 4, 32, 256)),
+                                       ("batched", (2048, 8, 64, 64, 1)), ("batched", (0xFFFFFFFF, 16, 128, 256)),
+                                       ("batched", (0xFFFFFFFF, 32, 256, 256)), ("batched", (0xFFFFFFFF, 4, 8, 64, 1)),
+                                       ("warp", None), ("packed", None), ("packed", (0, 8, 64, 128))])
+@pytest.mark.parametrize("roles", ["sparse X", "sparse Y"])
+def test_galloping_equals_host(torch_cuda, ctx, gallop_data, mode, tune, roles):
+    """Joins of a few intervals against thousands, with and without one
+    planted overlap, in every scope that gallops (lane groups, warps, CTAs,
+    compressed lists), equal host Algorithm 2 verdict for verdict."""
+    torch = torch_cuda
+    Sp, De, pr, ps = gallop_data
+    R, S = (Sp, De) if roles == "sparse X" else (De, Sp)
+    want, _ = A.april_host_filter(R, S, pr, ps)
+    assert np.bincount(want, minlength=3)[:2].min() > 100  # true negatives and true hits both occur
+    m = A.MODE_BATCHED_PACKED if mode == "packed" else A.MODES[mode]
+    if mode == "packed":
+        R = A.april_sets_from_lists(16, *_lists_of(R))
+        S = A.april_sets_from_lists(16, *_lists_of(S))
+        R.compress()
+        S.compress()
+    dR, dS = A.april_upload(R), A.april_upload(S)
+    saved = ctx.get_tune()
+    if tune:
+        ctx.set_tune(A.april_tune(*tune[:4], 0, 0.0, tune[4] if len(tune) > 4 else 0))
+    try:
+        def fn(d_r, d_s, out, n):
+            sb = ctx.scratch_bytes(m, n)
+            scratch = torch.empty(max(sb, 256), dtype=torch.uint8, device="cuda") if sb else None
+            ctx.april_filter_pairs(dR, dS, d_r, d_s, n, out, m, scratch)
+        got = _run(torch, ctx, dR, dS, pr, ps, fn)
+    finally:
+        ctx.set_tune(saved)
+    bad = np.flatnonzero(got != want)
+    assert len(bad) == 0, (len(bad), bad[:10])
+
+
+def _lists_of(sets):
+    """The A- and F-lists of every object of `sets` (a fresh copy to compress)."""
+    n = sets.info().n_objects
+    return [sets.list(i, 0) for i in range(n)], [sets.list(i, 1) for i in range(n)]

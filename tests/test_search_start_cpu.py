@@ -8,7 +8,10 @@ position up to that exact one.  These tests check, on random sorted
 disjoint interval lists (half-open [st, end) of 32-bit cells, an end of 2^32
 included), that a merge started at any positions up to the exact starts
 returns the full merge's answer, and that starting past the exact start can
-miss an overlap (so the bound is tight)."""
+miss an overlap (so the bound is tight).  The kernels also gallop: at a
+merge state (i, j) a list that lags may jump ahead to its first interval whose
+last cell reaches the other list's current start; the last test checks that
+jumps up to that position, taken at any state, keep the answer."""
 import numpy as np
 import pytest
 
@@ -68,3 +71,42 @@ def test_exact_start_is_tight():
     Y = [(15, 16)]
     assert _exact_start(X, Y[0][0]) == 1
     assert _merge(X, Y, 1, 0) and not _merge(X, Y, 2, 0)
+
+
+def _galloping_merge(X, Y, rng):
+    """The merge of _merge from (0, 0), except that at random states the
+    list whose current interval ends first jumps to a random position up to
+    its first interval whose last cell reaches the other's current start."""
+    i = j = 0
+    while i < len(X) and j < len(Y):
+        (xs, xe), (ys, ye) = X[i], Y[j]
+        if xs < ye and ys < xe:
+            return True
+        if rng.random() < 0.3:
+            if xe <= ye:
+                e = i + _exact_start(X[i:], ys)
+                i = int(rng.integers(i, e + 1))
+            else:
+                e = j + _exact_start(Y[j:], xs)
+                j = int(rng.integers(j, e + 1))
+            continue
+        if xe <= ys:
+            i += 1
+        else:
+            j += 1
+    return False
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_galloping_jumps_keep_the_answer(seed):
+    rng = np.random.default_rng(100 + seed)
+    for _ in range(400):
+        span = int(rng.integers(256, 4000))
+        # lists of very different lengths, where galloping pays
+        X = _lists(rng, int(rng.integers(1, 6)), span)
+        Y = _lists(rng, int(rng.integers(1, 60)), span)
+        if rng.random() < 0.5:
+            X, Y = Y, X
+        want = _any_overlap(X, Y)
+        for _ in range(4):
+            assert _galloping_merge(X, Y, rng) == want, (X, Y)

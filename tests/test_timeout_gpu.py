@@ -56,6 +56,7 @@ def test_timeout_reported_then_recovers(setup, mode, long_scope):
     n = len(w.pr)
     ctx = A.Context(0)
     t = ctx.get_tune()
+    t.cta_threshold = 2048  # long pairs go to the warp or CTA scope under test
     t.cta_window = 64 if long_scope == "warp" else 256
     ctx.set_tune(t)
     m = A.MODES[mode]
