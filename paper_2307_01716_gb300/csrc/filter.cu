@@ -48,12 +48,16 @@ constexpr uint32_t kBlock = 256;                 // threads per CTA for K1/K3
 constexpr uint32_t kWarpsPerBlock = kBlock / 32;
 constexpr uint32_t kWarpWMax = 256;              // largest warp window per list
 constexpr uint32_t kCtaWMax = 2048;              // largest CTA window per list
+// cta_threshold value meaning "no long pairs": every pair goes to the lane
+// groups, whatever its length, and the binning kernel is not launched
+constexpr uint32_t kNoLongPairs = 0xffffffffu;
 constexpr uint32_t kWarpFirstWindow = 64;        // first window of a join in APRIL_MODE_WARP
 constexpr uint32_t kWarpBuf = kWarpWMax + 2;     // staging buffer per list (odd start + rounding)
 constexpr uint32_t kCtaBuf = kCtaWMax + 2;
 // Compile-time knobs (defaults are the shipped configuration):
 //   APRIL_MIN_BLOCKS  minimum resident CTAs per SM requested for k_persistent
 //   APRIL_GROUP_PER   diagonals each lane walks per window in the group engine
+//   APRIL_GENERAL_MIN_BLOCKS  minimum resident CTAs per SM requested for k_general
 #ifdef APRIL_MIN_BLOCKS
 #define APRIL_PERSISTENT_BOUNDS __launch_bounds__(256, APRIL_MIN_BLOCKS)
 #else
@@ -225,7 +229,8 @@ __device__ __forceinline__ bool warp_chunk(const SetsT &R, const SetsT &S, const
         if (r < R.n() && s < S.n()) {
             dr = R.load(r);
             ds = S.load(s);
-            take = (uint64_t)SetsT::a_len(dr) + SetsT::a_len(ds) <= (uint64_t)cta_threshold;
+            take = cta_threshold == kNoLongPairs ||
+                   (uint64_t)SetsT::a_len(dr) + SetsT::a_len(ds) <= (uint64_t)cta_threshold;
         } else if (flag_bad) {
             out[k] = APRIL_VERDICT_ERROR;
             atomicOr(status, ST_BAD_ID);
@@ -277,7 +282,8 @@ __global__ void __launch_bounds__(kBlock) k_warp(DevSet R, DevSet S, const uint3
 // --------------------------------------------- K4: length binning (batched)
 // Validates ids (error verdicts), and appends every pair whose cost
 // |A(r)| + |A(s)| exceeds the threshold to the long-pair list (warp-
-// aggregated atomics).
+// aggregated atomics).  Not launched when the threshold is kNoLongPairs: the
+// lane groups then take every pair and report bad ids themselves.
 template <class SetsT>
 __global__ void __launch_bounds__(256) k_bin(SetsT R, SetsT S, const uint32_t *__restrict__ pr,
                                              const uint32_t *__restrict__ ps, uint64_t n, uint8_t *__restrict__ out,
@@ -431,6 +437,7 @@ __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, con
                                              uint32_t w0, uint32_t jo, uint32_t esc_windows, uint4 *esc,
                                              uint32_t esc_cap) {
     using C = GroupCfg<G>;
+    const bool no_long = cta_threshold == kNoLongPairs;  // every pair is joined here; no binning kernel ran
     const uint32_t g = lane / G, t = lane % G, glead = g * G;
     const uint32_t gbits = (G == 32 ? kFull : ((1u << G) - 1u)) << glead;
     uint2 *xb = wbuf + g * 2 * C::BUF, *yb = xb + C::BUF;
@@ -473,11 +480,14 @@ __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, con
                 __syncwarp();  // every group has read its descriptors from the previous chunk
                 if (qk < n) {
                     const uint32_t r = __ldg(pr + qk), s2 = __ldg(ps + qk);
-                    if (r < R.n() && s2 < S.n()) {  // out-of-range ids were reported by the binning kernel
+                    if (r < R.n() && s2 < S.n()) {
                         const uint4 qdr = R.load(r), qds = S.load(s2);
                         chunk_desc[lane] = qdr;
                         chunk_desc[32 + lane] = qds;
-                        take = (uint64_t)qdr.y + qds.y <= (uint64_t)cta_threshold;
+                        take = no_long || (uint64_t)qdr.y + qds.y <= (uint64_t)cta_threshold;
+                    } else if (no_long) {  // no binning kernel ran to report them
+                        out[qk] = APRIL_VERDICT_ERROR;
+                        atomicOr(status, ST_BAD_ID);
                     }
                 }
                 const uint32_t tb = __ballot_sync(kFull, take);
@@ -699,7 +709,7 @@ __global__ void APRIL_PERSISTENT_BOUNDS k_persistent(SetsT R, SetsT S,
             c = __shfl_sync(kFull, c, 0);
             if (c >= nchunks) break;
             if (!warp_chunk(R, S, pr, ps, n, (uint64_t)c * 32, out, status, wbuf, wbuf + kWarpBuf, lane, w0_group,
-                            cta_threshold, false, js, jo))
+                            cta_threshold, cta_threshold == kNoLongPairs, js, jo))
                 return;
         }
     } else {
@@ -777,7 +787,11 @@ __device__ __forceinline__ uint8_t plan_verdict(const Plan &P, const RawSets &R,
 
 // Same shape as K3 with 32-lane groups: long pairs by whole CTAs, the rest by
 // warps taking 32-pair chunks.
-__global__ void __launch_bounds__(kBlock) k_general(Plan P, DevSet Rd, DevSet Sd, const uint32_t *__restrict__ pr,
+// the variant kernel at four CTAs per SM (at most 64 registers a thread)
+#ifndef APRIL_GENERAL_MIN_BLOCKS
+#define APRIL_GENERAL_MIN_BLOCKS 4
+#endif
+__global__ void __launch_bounds__(kBlock, APRIL_GENERAL_MIN_BLOCKS) k_general(Plan P, DevSet Rd, DevSet Sd, const uint32_t *__restrict__ pr,
                                                     const uint32_t *__restrict__ ps, uint64_t n,
                                                     uint8_t *__restrict__ out, uint32_t *status,
                                                     uint32_t cta_threshold, const uint32_t *__restrict__ big_list,
@@ -1186,7 +1200,8 @@ static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, con
     }
     if (packed) {
         const PackedSets R = packed_set(Rd), S = packed_set(Sd);
-        k_bin<<<grid_bin, 256, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold, big_list, counters);
+        if (t.cta_threshold != kNoLongPairs)
+            k_bin<<<grid_bin, 256, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold, big_list, counters);
 #define APRIL_LAUNCH_PACKED(G)                                                                                  \
     k_persistent<G, PackedSets><<<grid_main, kBlock, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold,   \
                                                               big_list, counters, t.group_window, t.cta_window,   \
@@ -1204,7 +1219,8 @@ static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, con
         return cudaGetLastError();
     }
     const RawSets R{dev_set(Rd)}, S{dev_set(Sd)};
-    k_bin<<<grid_bin, 256, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold, big_list, counters);
+    if (t.cta_threshold != kNoLongPairs)
+        k_bin<<<grid_bin, 256, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold, big_list, counters);
 #define APRIL_LAUNCH_PERSISTENT(G)                                                                            \
     k_persistent<G, RawSets><<<grid_main, kBlock, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold,       \
                                                            big_list, counters, t.group_window, t.cta_window,      \
@@ -1663,7 +1679,8 @@ extern "C" april_status april_filter_pairs_noalloc(const april_dev_sets *R, cons
     const RawSets dR{dev_set(R)}, dS{dev_set(S)};
     const unsigned grid_bin = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)nd.num_sms * 8);
     const unsigned grid_main = (unsigned)std::max(1, nd.num_sms * nd.blocks_per_sm);
-    k_bin<<<grid_bin, 256, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, status, t.cta_threshold, big_list, counters);
+    if (t.cta_threshold != kNoLongPairs)
+        k_bin<<<grid_bin, 256, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, status, t.cta_threshold, big_list, counters);
     // no escalation: the static array has no room for the queue of handed-over joins
     noalloc_kernel(t.group_lanes)<<<grid_main, kBlock, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, status,
                                                                 t.cta_threshold, big_list, counters, t.group_window,
