@@ -362,8 +362,14 @@ april_status april_filter_pairs(april_ctx *ctx, const april_dev_sets *R, const a
  * and waits for the stream.  h_r, h_s and h_verdict are host arrays (pinned
  * memory makes the copies asynchronous DMA); d_work is a caller-allocated
  * device buffer of april_filter_host_work_bytes() bytes (256-byte aligned)
- * that holds the staged pairs, the verdicts and the mode's scratch.
- * Returns the same codes as april_filter_pairs followed by april_sync_status. */
+ * that holds the staged pairs, the verdicts and the mode's scratch.  In the
+ * batched modes the pairs are pipelined in up to 8 chunks of at least 2^22
+ * pairs: a chunk's pairs are copied in while the previous chunk is filtered
+ * and its verdicts copied out while the next is, on streams of the context
+ * (created on first use) that follow the work queued on `stream` before the
+ * call and that `stream` waits for.  The verdicts are those of one
+ * april_filter_pairs call over all n pairs.  Returns the same codes as
+ * april_filter_pairs followed by april_sync_status. */
 april_status april_filter_host_work_bytes(int mode, uint64_t n, size_t *bytes);
 april_status april_filter_pairs_host(april_ctx *ctx, const april_dev_sets *R, const april_dev_sets *S,
                                      const uint32_t *h_r, const uint32_t *h_s, uint64_t n, uint8_t *h_verdict,

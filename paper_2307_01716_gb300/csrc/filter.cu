@@ -58,6 +58,7 @@ constexpr uint32_t kCtaBuf = kCtaWMax + 2;
 //   APRIL_MIN_BLOCKS  minimum resident CTAs per SM requested for k_persistent
 //   APRIL_GROUP_PER   diagonals each lane walks per window in the group engine
 //   APRIL_GENERAL_MIN_BLOCKS  minimum resident CTAs per SM requested for k_general
+//   APRIL_STAGE2      1: a lane group's two windows are copied by two lanes (mbarrier count 2)
 #ifdef APRIL_MIN_BLOCKS
 #define APRIL_PERSISTENT_BOUNDS __launch_bounds__(256, APRIL_MIN_BLOCKS)
 #else
@@ -66,6 +67,10 @@ constexpr uint32_t kCtaBuf = kCtaWMax + 2;
 // the others leave the register count to the compiler
 #define APRIL_PERSISTENT_BOUNDS __launch_bounds__(256, (G < 32 && !SetsT::kPacked) ? 5 : 0)
 #endif
+#ifndef APRIL_STAGE2
+#define APRIL_STAGE2 1
+#endif
+constexpr bool kStage2 = APRIL_STAGE2 != 0;  // lane groups stage their two windows from two lanes
 #ifndef APRIL_GROUP_PER
 #define APRIL_GROUP_PER 8
 #endif
@@ -546,7 +551,20 @@ __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, con
             nx = min(w, nX - i0);
             ny = min(w, nY - j0);
             if constexpr (ListT::kBulk) {
-                if (t == 0) {
+                if constexpr (kStage2) {
+                    // lane 0 copies X's window, lane 1 Y's; each arrives once
+                    // with its own bytes on the group's mbarrier (count 2)
+                    if (t < 2) {
+                        fence_proxy_async();
+                        const bool isy = t == 1;
+                        const uint2 *src = isy ? Y.p + j0 : X.p + i0;
+                        const uint2 *a;
+                        uint32_t b, o;
+                        bulk_span(src, isy ? ny : nx, a, b, o);
+                        mbar_arrive_expect_tx(bar, b);
+                        bulk_load(smem_addr(isy ? yb : xb), src - o, b, bar);
+                    }
+                } else if (t == 0) {
                     fence_proxy_async();
                     const uint2 *a;
                     uint32_t bx, by, ox, oy;
@@ -656,7 +674,17 @@ __global__ void APRIL_PERSISTENT_BOUNDS k_persistent(SetsT R, SetsT S,
     __shared__ uint64_t bars[C::BARS];  // see GroupCfg
     __shared__ uint4 s_chunk[kWarpsPerBlock][64];     // group engine: each warp's chunk descriptors
     __shared__ uint8_t s_chunk_lane[kWarpsPerBlock][32];  // and the chunk lanes they came from
-    init_barriers(bars, C::BARS);
+    if constexpr (kStage2 && G < 32 && !SetsT::kPacked) {
+        // the lane groups' mbarriers take two arrivals a window (see group_engine)
+        for (uint32_t i = threadIdx.x; i < C::BARS; i += blockDim.x) {
+            const bool grp = i >= 1 && i < 1 + kWarpsPerBlock * C::NG;
+            mbar_init(smem_addr(bars + i), grp ? 2u : 1u);
+        }
+        if (threadIdx.x == 0) mbar_init_fence();
+        __syncthreads();
+    } else {
+        init_barriers(bars, C::BARS);
+    }
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const uint32_t nbig = *((volatile uint32_t *)&counters[C_BIG_COUNT]);
     uint2 *wbuf = sm + warp * C::SHARE;
@@ -968,6 +996,11 @@ struct april_ctx {
     int long_blocks_per_sm = 1;  // occupancy of k_long (the larger of its two instances' limits)
     april_tune tune{};
     cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+    // april_filter_pairs_host's pipeline (created on first use): streams for
+    // the pair copies, two for the chunks' kernels, one for the verdict
+    // copies, and events ordering them (start, end, per chunk: in, kernel)
+    cudaStream_t pipe[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t pev[2 + 2 * 8] = {};
     cudaGraphExec_t graph = nullptr;    // the batched pipeline, captured once per argument set
     GraphKey key{};
     uint64_t graph_launches = 0;
@@ -1058,6 +1091,10 @@ extern "C" void april_ctx_destroy(april_ctx *ctx) {
     if (!ctx) return;
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    for (cudaStream_t &p : ctx->pipe)
+        if (p) cudaStreamDestroy(p);
+    for (cudaEvent_t &v : ctx->pev)
+        if (v) cudaEventDestroy(v);
     if (ctx->d_status) cudaFree(ctx->d_status);
     delete ctx;
 }
@@ -1152,6 +1189,19 @@ extern "C" april_status april_filter_scratch_bytes(int mode, uint64_t n, size_t 
 static april_status check_layout(const april_dev_sets *d) {
     if (!d->desc || !d->iv || !d->posts || (((uintptr_t)d->iv) & 255u))
         return fail(APRIL_ERR_INVALID_ARG, "device sets not laid out by april_upload or april_build_sets_device");
+    return APRIL_OK;
+}
+
+// The checks april_filter_pairs makes on its sets, size and mode.
+static april_status check_filter_args(const april_dev_sets *R, const april_dev_sets *S, uint64_t n, int mode) {
+    if (R->order != S->order || R->parts != S->parts)
+        return fail(APRIL_ERR_INVALID_ARG, "R and S are on different grids");
+    if (check_layout(R) || check_layout(S)) return APRIL_ERR_INVALID_ARG;
+    if (n > 0xFFFFFFFFull) return fail(APRIL_ERR_INVALID_ARG, "at most 2^32-1 pairs per call");
+    if (R->parts && mode != APRIL_MODE_BATCHED && mode != APRIL_MODE_BATCHED_PACKED)
+        return fail(APRIL_ERR_INVALID_ARG, "partitioned sets need APRIL_MODE_BATCHED or APRIL_MODE_BATCHED_PACKED");
+    if (mode == APRIL_MODE_BATCHED_PACKED && (!R->pdesc || !S->pdesc))
+        return fail(APRIL_ERR_INVALID_ARG, "APRIL_MODE_BATCHED_PACKED needs sets compressed by april_sets_compress");
     return APRIL_OK;
 }
 
@@ -1311,14 +1361,8 @@ extern "C" april_status april_filter_pairs(april_ctx *ctx, const april_dev_sets 
     if (!ctx || !R || !S) return fail(APRIL_ERR_INVALID_ARG, "NULL argument");
     if (n == 0) return APRIL_OK;
     if (!d_r || !d_s || !d_verdict) return fail(APRIL_ERR_INVALID_ARG, "NULL pair or verdict array");
-    if (R->order != S->order || R->parts != S->parts)
-        return fail(APRIL_ERR_INVALID_ARG, "R and S are on different grids");
-    if (check_layout(R) || check_layout(S)) return APRIL_ERR_INVALID_ARG;
-    if (n > 0xFFFFFFFFull) return fail(APRIL_ERR_INVALID_ARG, "at most 2^32-1 pairs per call");
-    if (R->parts && mode != APRIL_MODE_BATCHED && mode != APRIL_MODE_BATCHED_PACKED)
-        return fail(APRIL_ERR_INVALID_ARG, "partitioned sets need APRIL_MODE_BATCHED or APRIL_MODE_BATCHED_PACKED");
-    if (mode == APRIL_MODE_BATCHED_PACKED && (!R->pdesc || !S->pdesc))
-        return fail(APRIL_ERR_INVALID_ARG, "APRIL_MODE_BATCHED_PACKED needs sets compressed by april_sets_compress");
+    const april_status chk = check_filter_args(R, S, n, mode);
+    if (chk) return chk;
     cudaStream_t st = (cudaStream_t)stream;
     const DevSet dR = dev_set(R), dS = dev_set(S);
     const int sms = ctx->num_sms;
@@ -1521,12 +1565,54 @@ extern "C" april_status april_autotune(april_ctx *ctx, const april_dev_sets *R, 
     return APRIL_OK;
 }
 
+// april_filter_pairs_host in the batched modes pipelines the pairs in chunks
+// of at least kPipeChunkMin pairs (at most kPipeMaxChunks): a chunk's pairs
+// are copied in while the previous chunk is filtered, and its verdicts are
+// copied out while the next one is.  Chunks alternate between two kernel
+// streams, each with its own scratch, so that one chunk's tail overlaps the
+// next chunk's start.  Each chunk costs a launch and a tail, which measured
+// more than the copies it hides below 2^22 pairs (the end-to-end overhead is
+// mostly fixed latency); 10M pairs in three chunks end 5% sooner than in one.
+#ifndef APRIL_PIPE_CHUNK_LOG2
+#define APRIL_PIPE_CHUNK_LOG2 22
+#endif
+constexpr uint64_t kPipeChunkMin = 1ull << APRIL_PIPE_CHUNK_LOG2;
+constexpr uint32_t kPipeMaxChunks = 8;
+static uint32_t pipe_chunks(uint64_t n) {
+    return (uint32_t)std::min<uint64_t>(kPipeMaxChunks, std::max<uint64_t>(1, (n + kPipeChunkMin - 1) / kPipeChunkMin));
+}
+static uint64_t pipe_chunk_size(uint64_t n) {
+    const uint32_t k = pipe_chunks(n);
+    return ((n + k - 1) / k + 63) / 64 * 64;
+}
+
 extern "C" april_status april_filter_host_work_bytes(int mode, uint64_t n, size_t *bytes) {
     if (!bytes) return fail(APRIL_ERR_INVALID_ARG, "bytes is NULL");
     size_t sb = 0;
     april_status st = april_filter_scratch_bytes(mode, n, &sb);
     if (st) return st;
+    if (mode == APRIL_MODE_BATCHED || mode == APRIL_MODE_BATCHED_PACKED) {
+        april_filter_scratch_bytes(mode, pipe_chunk_size(n), &sb);  // per chunk, one region per kernel stream
+        sb = round256(sb) * (pipe_chunks(n) > 1 ? 2 : 1);
+    }
     *bytes = (size_t)(round256(4 * n) * 2 + round256(n) + round256(sb));
+    return APRIL_OK;
+}
+
+static april_status ensure_pipeline(april_ctx *ctx) {
+    if (ctx->pipe[0]) return APRIL_OK;
+    cudaError_t e = cudaSuccess;
+    for (cudaStream_t &p : ctx->pipe)
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p, cudaStreamNonBlocking);
+    for (cudaEvent_t &v : ctx->pev)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        for (cudaStream_t &p : ctx->pipe)
+            if (p) cudaStreamDestroy(p), p = nullptr;
+        for (cudaEvent_t &v : ctx->pev)
+            if (v) cudaEventDestroy(v), v = nullptr;
+        return cuda_fail(e, "creating the host pipeline's streams");
+    }
     return APRIL_OK;
 }
 
@@ -1538,24 +1624,73 @@ extern "C" april_status april_filter_pairs_host(april_ctx *ctx, const april_dev_
     if (n == 0) return APRIL_OK;
     if (!h_r || !h_s || !h_verdict || !d_work) return fail(APRIL_ERR_INVALID_ARG, "NULL host or work buffer");
     if (((uintptr_t)d_work) & 255u) return fail(APRIL_ERR_INVALID_ARG, "work buffer must be 256-byte aligned");
-    size_t need = 0, sb = 0;
+    size_t need = 0;
     april_status st = april_filter_host_work_bytes(mode, n, &need);
     if (st) return st;
     if (work_bytes < need) return fail(APRIL_ERR_INVALID_ARG, "work buffer too small");
-    april_filter_scratch_bytes(mode, n, &sb);
     char *w = (char *)d_work;
     uint32_t *d_r = (uint32_t *)w;
     uint32_t *d_s = (uint32_t *)(w + round256(4 * n));
     uint8_t *d_v = (uint8_t *)(w + 2 * round256(4 * n));
-    void *d_scr = sb ? (void *)(w + 2 * round256(4 * n) + round256(n)) : nullptr;
+    char *d_scr = w + 2 * round256(4 * n) + round256(n);
     cudaStream_t cs = (cudaStream_t)stream;
-    cudaError_t e = cudaMemcpyAsync(d_r, h_r, 4 * n, cudaMemcpyHostToDevice, cs);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_s, h_s, 4 * n, cudaMemcpyHostToDevice, cs);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(pairs)");
-    st = april_filter_pairs(ctx, R, S, d_r, d_s, n, d_v, mode, d_scr, sb, stream);
+    cudaError_t e;
+    if (mode != APRIL_MODE_BATCHED && mode != APRIL_MODE_BATCHED_PACKED) {
+        // the one-pair-per-thread and per-warp modes: copy in, filter, copy out
+        e = cudaMemcpyAsync(d_r, h_r, 4 * n, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_s, h_s, 4 * n, cudaMemcpyHostToDevice, cs);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(pairs)");
+        st = april_filter_pairs(ctx, R, S, d_r, d_s, n, d_v, mode, nullptr, 0, stream);
+        if (st) return st;
+        e = cudaMemcpyAsync(h_verdict, d_v, n, cudaMemcpyDeviceToHost, cs);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(verdicts)");
+        return april_sync_status(ctx, stream);
+    }
+    st = check_filter_args(R, S, n, mode);
     if (st) return st;
-    e = cudaMemcpyAsync(h_verdict, d_v, n, cudaMemcpyDeviceToHost, cs);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(verdicts)");
+    st = ensure_pipeline(ctx);
+    if (st) return st;
+    const bool packed = mode == APRIL_MODE_BATCHED_PACKED;
+    const uint32_t K = pipe_chunks(n);
+    const uint64_t cs_n = pipe_chunk_size(n);
+    size_t sb = 0;
+    april_filter_scratch_bytes(mode, cs_n, &sb);
+    sb = round256(sb);
+    const uint32_t gl = ctx->tune.group_lanes;
+    const int occ = ctx->persistent_blocks_per_sm[(packed ? 4 : 0) + group_index(gl)];
+    const int bps = ctx->tune.blocks_per_sm ? (int)std::min<uint32_t>(ctx->tune.blocks_per_sm, (uint32_t)occ) : occ;
+    const unsigned grid_main = (unsigned)std::max(1, ctx->num_sms * bps);
+    cudaStream_t s_in = ctx->pipe[0], s_out = ctx->pipe[3];
+    cudaEvent_t ev_start = ctx->pev[0], ev_end = ctx->pev[1];
+    // the pipeline follows the work already queued on the caller's stream
+    e = cudaEventRecord(ev_start, cs);
+    for (cudaStream_t p : ctx->pipe)
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(p, ev_start, 0);
+    for (uint32_t c = 0; c < K && e == cudaSuccess; ++c) {
+        const uint64_t off = c * cs_n;
+        if (off >= n) break;
+        const uint64_t cnt = std::min<uint64_t>(cs_n, n - off);
+        cudaStream_t ks = ctx->pipe[1 + (c & 1u)];
+        cudaEvent_t ev_in = ctx->pev[2 + 2 * c], ev_k = ctx->pev[3 + 2 * c];
+        e = cudaMemcpyAsync(d_r + off, h_r + off, 4 * cnt, cudaMemcpyHostToDevice, s_in);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_s + off, h_s + off, 4 * cnt, cudaMemcpyHostToDevice, s_in);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_in, s_in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ks, ev_in, 0);
+        if (e == cudaSuccess) {
+            const unsigned grid_bin = (unsigned)std::min<uint64_t>((cnt + 255) / 256, (uint64_t)ctx->num_sms * 8);
+            e = enqueue_batched(ctx, R, S, d_r + off, d_s + off, cnt, d_v + off, d_scr + (K > 1 ? (c & 1u) * sb : 0),
+                                packed, grid_bin, grid_main, ks);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ev_k, ks);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, ev_k, 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_verdict + off, d_v + off, cnt, cudaMemcpyDeviceToHost, s_out);
+    }
+    // the caller's stream waits for every stream of the pipeline
+    for (uint32_t q = 0; q < 4 && e == cudaSuccess; ++q) {
+        e = cudaEventRecord(ev_end, ctx->pipe[q]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_end, 0);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "april_filter_pairs_host pipeline");
     return april_sync_status(ctx, stream);
 }
 

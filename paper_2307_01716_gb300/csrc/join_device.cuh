@@ -461,7 +461,10 @@ struct PackedList {
 // P NT kPostVec - (P - 1) with P = 4 / STRIDE keys per 16-byte word.  Each
 // thread loads kPostVec 16-byte words of keys (the group's loads cover one
 // aligned run that holds [lo, hi)) and counts; the group sums.
-constexpr uint32_t kPostVec = 2;
+#ifndef APRIL_POST_VEC
+#define APRIL_POST_VEC 2
+#endif
+constexpr uint32_t kPostVec = APRIL_POST_VEC;
 template <uint32_t STRIDE>  // words per key: 1 (posts) or 2 (block anchors, the first word of each pair)
 __device__ __forceinline__ uint32_t post_count(const uint32_t *keys, uint32_t lo, uint32_t hi, uint32_t sh,
                                                uint32_t t, uint32_t tid, uint32_t nt) {
