@@ -77,6 +77,14 @@ typedef struct april_grid {
     uint32_t order;
 } april_grid;
 
+/* The Hilbert id (Sec. 3.2) of the cell of the grid that holds lattice point
+ * (x[k], y[k]), for k < n: the cell (floor((x - ox) / 2^log2_cell),
+ * floor((y - oy) / 2^log2_cell)) taken half-open; UINT64_MAX for a point
+ * outside the grid.  The batched filter's triage maps MBR points to cells the
+ * same way.  x, y and ids are host arrays.  Errors: APRIL_ERR_INVALID_ARG (a
+ * NULL array with n > 0, a bad grid). */
+april_status april_cell_ids(const april_grid *grid, const int64_t *x, const int64_t *y, uint64_t n, uint64_t *ids);
+
 /* ---------------------------------------------------------------- errors */
 
 /* Copies the calling thread's most recent error message (NUL-terminated,
@@ -241,6 +249,10 @@ typedef struct april_dev_sets {
     const uint8_t *gaps;        /* compressed: gap blocks (64 or 128 bytes each) */
     const int32_t *mbr;         /* per object {x0, y0, x1, y1}: closed MBR in lattice units */
     const uint32_t *posts;      /* skip index: the last cell of interval slot 16 q + 15, per q */
+    int64_t grid_ox;            /* grid_known: the grid the lists were built on (lattice origin, */
+    int64_t grid_oy;            /*   log2 of the cell side); the batched filter's triage maps */
+    uint32_t grid_log2_cell;    /*   MBR points to cells with it */
+    uint32_t grid_known;        /* 1: built from polygons on one grid (april_build_sets, april_build_sets_device) */
 } april_dev_sets;
 
 /* Copies the sets into a caller-allocated device buffer of at least
@@ -269,10 +281,11 @@ void april_ctx_destroy(april_ctx *ctx);
 /* ------------------------------------------------------------------ tuning */
 
 /* Knobs of APRIL_MODE_BATCHED (a build-side addition; the paper's CPU
- * filter has none).  Defaults: {0xFFFFFFFF, 4, 32, 128, 0, -, 0, 0}: every
- * pair joined by a group of 4 lanes with windows of 32 intervals per list,
- * galloping (a window that advances one list only is followed by a search of
- * that list); the long-pair scope (cta_threshold, cta_window) is off. */
+ * filter has none).  Defaults: {0xFFFFFFFF, 4, 32, 128, 0, -, 2, 0, 0}: the
+ * triage first (where it applies), then every pair it left joined by a group
+ * of 4 lanes with windows of 32 intervals per list, galloping (a window that
+ * advances one list only is followed by a search of that list), AA first
+ * after the triage; the long-pair scope (cta_threshold, cta_window) is off. */
 typedef struct april_tune {
     uint32_t cta_threshold;  /* pairs with |A(r)| + |A(s)| above this ("long pairs") are joined
                                 first, each by one warp or by a whole CTA (see cta_window) */
@@ -287,11 +300,15 @@ typedef struct april_tune {
     uint32_t join_order;     /* order of a pair's joins in the batched kernels (the verdicts are
                                 the same, Sec. 4.2): 0 = AF, AA, FA (a true hit from AF takes
                                 one join); 1 = AA, AF, FA, Algorithm 2's (a true negative takes
-                                one join) */
+                                one join); 2 (default) = 1 for the pairs the triage left, else 0 */
     uint32_t escalate_windows; /* 0, or 1..64: a join of the lane groups that still runs after
                                 this many windows is handed, at the position it reached, to a
                                 second kernel that joins it by a whole warp (first window
                                 2 * cta_window when that is below 256, else 128) */
+    uint32_t triage_off;     /* 0 (default): with no long-pair threshold, lane groups of 4..16 and raw
+                                sets built from polygons on one grid (grid_known, same grid), a
+                                triage pass first settles the pairs whose MBR-intersection centre
+                                cell lies in A(r) and F(s) or in F(r) and A(s) (true hits); 1: off */
 } april_tune;
 
 april_status april_set_tune(april_ctx *ctx, const april_tune *tune);
@@ -656,10 +673,14 @@ april_status april_host_filter(const april_sets *R, const april_sets *S, const u
                                const uint32_t *ps, uint64_t n, uint32_t n_threads, uint8_t *verdict,
                                uint64_t *consumed);
 
-/* Algorithm 2 run the way the batched GPU kernels run it: the joins in the
- * order AF, AA, FA (an AF or FA overlap implies an AA overlap, so the
- * verdicts are Algorithm 2's whatever the order, Sec. 4.2) and every merge
- * join started at each list's first interval whose last cell reaches the
+/* Algorithm 2 run the way the batched GPU kernels run it with the default
+ * tuning.  On sets built on one shared grid the triage comes first: a pair
+ * whose MBR-intersection centre cell lies in A(r) and F(s), or in F(r) and
+ * A(s), is a true hit; the other pairs are joined in the order AA, AF, FA.
+ * Without the triage the order is AF, AA, FA (an AF or FA overlap implies an
+ * AA overlap, so the verdicts are Algorithm 2's whatever the order, Sec.
+ * 4.2).  Every merge join starts at each list's first interval whose last
+ * cell reaches the
  * other list's first start (found by binary search; the sequential merge from
  * the front passes over the intervals before it without a verdict).  The
  * merge gallops: after 16 consecutive advances of one list it jumps, by
@@ -667,8 +688,9 @@ april_status april_host_filter(const april_sets *R, const april_sets *S, const u
  * other list's current start (the intervals passed over meet nothing).  The
  * verdicts equal april_host_filter's.  consumed[k] counts, for every join
  * that ran, the intervals the merge reads plus the probes of every search
- * (the bit width of the searched length): the bytes model of the kernels'
- * reading, used for their roofline.  (The kernels start up to 16 intervals
+ * (the bit width of the searched length), and for the triage 4 (the two
+ * MBRs' bytes) plus bit_width(n / 16) + 5 for each list looked up: the bytes
+ * model of the kernels' reading, used for their roofline.  (The kernels start up to 16 intervals
  * before the exact start and gallop after a whole window that advanced one
  * list only, so they read at least this much; the verdicts are the same.) */
 april_status april_host_filter_searched(const april_sets *R, const april_sets *S, const uint32_t *pr,

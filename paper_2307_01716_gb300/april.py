@@ -52,7 +52,7 @@ class april_tune(ctypes.Structure):
     _fields_ = [("cta_threshold", ctypes.c_uint32), ("group_lanes", ctypes.c_uint32),
                 ("group_window", ctypes.c_uint32), ("cta_window", ctypes.c_uint32),
                 ("blocks_per_sm", ctypes.c_uint32), ("ms", ctypes.c_float), ("join_order", ctypes.c_uint32),
-                ("escalate_windows", ctypes.c_uint32)]
+                ("escalate_windows", ctypes.c_uint32), ("triage_off", ctypes.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -89,7 +89,9 @@ class april_dev_sets(ctypes.Structure):
                 ("order", ctypes.c_uint32), ("iv_slots", ctypes.c_uint64), ("n_entries", ctypes.c_uint32),
                 ("parts", ctypes.c_uint32), ("obj_ll", ctypes.c_void_p), ("obj_entry", ctypes.c_void_p),
                 ("entry_pid", ctypes.c_void_p), ("pdesc", ctypes.c_void_p), ("anchors", ctypes.c_void_p),
-                ("gaps", ctypes.c_void_p), ("mbr", ctypes.c_void_p), ("posts", ctypes.c_void_p)]
+                ("gaps", ctypes.c_void_p), ("mbr", ctypes.c_void_p), ("posts", ctypes.c_void_p),
+                ("grid_ox", ctypes.c_int64), ("grid_oy", ctypes.c_int64), ("grid_log2_cell", ctypes.c_uint32),
+                ("grid_known", ctypes.c_uint32)]
 
 
 _vp = ctypes.c_void_p
@@ -101,6 +103,7 @@ _st = ctypes.c_int32
 SIGNATURES = {
     "april_last_error": (_st, [ctypes.c_char_p, ctypes.c_size_t]),
     "april_build_sets": (_st, [_vp, _vp, _u32, ctypes.POINTER(april_grid), _u32, ctypes.POINTER(_vp)]),
+    "april_cell_ids": (_st, [ctypes.POINTER(april_grid), _vp, _vp, _u64, _vp]),
     "april_sets_destroy": (None, [_vp]),
     "april_sets_get_info": (_st, [_vp, ctypes.POINTER(april_sets_info)]),
     "april_sets_list": (_st, [_vp, _u32, ctypes.c_int, ctypes.POINTER(ctypes.POINTER(_u32)),
@@ -285,6 +288,15 @@ class Sets:
         if n.value == 0:
             return np.zeros((0, 2), dtype=np.uint32)
         return np.ctypeslib.as_array(p, shape=(n.value * 2,)).reshape(-1, 2).copy()
+
+
+def april_cell_ids(grd: april_grid, x, y) -> np.ndarray:
+    """Hilbert ids of the grid cells holding lattice points (x, y) (UINT64_MAX outside the grid)."""
+    x = np.ascontiguousarray(x, dtype=np.int64)
+    y = np.ascontiguousarray(y, dtype=np.int64)
+    ids = np.zeros(len(x), dtype=np.uint64)
+    check(load().april_cell_ids(ctypes.byref(grd), _ptr(x), _ptr(y), len(x), _ptr(ids)))
+    return ids
 
 
 def april_quantize_polygons(xy, vert_off):

@@ -45,6 +45,12 @@ struct april_sets {
     std::vector<uint32_t> obj_entry;  // parts > 0: n + 1 entry offsets (entries of an object are contiguous)
     std::vector<uint32_t> entry_pid;  // parts > 0: partition id of each entry (ascending within an object)
     std::vector<int64_t> part_grid;   // parts > 0: 4 per partition: ox, oy, log2_cell, used(0/1)
+    // the grid of sets built from polygons on one grid (parts == 0): lattice
+    // origin and log2 of the cell side, with which the batched filter's
+    // triage maps an MBR point to its cell
+    bool grid_known = false;
+    int64_t grid_ox = 0, grid_oy = 0;
+    uint32_t grid_log2_cell = 0;
     // compressed lists (Sec. 5.1), see april_sets_compress
     bool packed = false;
     std::vector<uint32_t> pdesc;      // 4 per entry: {a_block, a_len, f_block, f_len} (block-table indices)

@@ -883,5 +883,9 @@ extern "C" april_status april_build_sets_device(april_ctx *ctx, const int32_t *d
     out->order = g.order;
     out->iv_slots = h.slots;
     out->n_entries = n_polys;
+    out->grid_ox = g.ox;
+    out->grid_oy = g.oy;
+    out->grid_log2_cell = grid->log2_cell;
+    out->grid_known = 1;
     return APRIL_OK;
 }

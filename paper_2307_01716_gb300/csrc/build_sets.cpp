@@ -359,6 +359,10 @@ extern "C" april_status april_build_sets(const int32_t *xy, const uint64_t *vert
         S->n = n_polys;
         S->n_entries = n_polys;
         S->order = g.order;
+        S->grid_known = true;
+        S->grid_ox = g.ox;
+        S->grid_oy = g.oy;
+        S->grid_log2_cell = grid->log2_cell;
         S->mbr.resize(4 * (size_t)n_polys);
         for (uint32_t p = 0; p < n_polys; ++p) {
             const Mbr m = poly_mbr(xy + 2 * vert_off[p], vert_off[p + 1] - vert_off[p]);
@@ -375,6 +379,23 @@ extern "C" april_status april_build_sets(const int32_t *xy, const uint64_t *vert
     } catch (const std::bad_alloc &) {
         return fail(APRIL_ERR_NO_MEMORY, "host allocation failed while building sets");
     }
+}
+
+extern "C" april_status april_cell_ids(const april_grid *grid, const int64_t *x, const int64_t *y, uint64_t n,
+                                       uint64_t *ids) {
+    GridI g;
+    april_status st = check_grid(grid, g);
+    if (st) return st;
+    if (n && (!x || !y || !ids)) return fail(APRIL_ERR_INVALID_ARG, "NULL array");
+    uint8_t lut[64];
+    april_geom::hilbert_lut_build(lut);
+    for (uint64_t k = 0; k < n; ++k) {
+        const int64_t cx = floor_div(x[k] - g.ox, g.h), cy = floor_div(y[k] - g.oy, g.h);
+        ids[k] = cx < 0 || cy < 0 || cx >= g.G || cy >= g.G
+                     ? ~0ull
+                     : april_geom::hilbert_id_lut(lut, g.order, (uint32_t)cx, (uint32_t)cy);
+    }
+    return APRIL_OK;
 }
 
 extern "C" april_status april_sets_from_lists(uint32_t n, uint32_t order, const uint64_t *a_off,
@@ -868,11 +889,52 @@ extern "C" april_status april_route_pairs(const april_sets *R, const april_sets 
     return APRIL_OK;
 }
 
+// Whether list L (n intervals) holds cell c; *used counts the lookup as the
+// triage kernel reads it: a binary search over the list's skip index (one
+// post per 16 intervals), then over at most 16 intervals.
+static bool host_list_holds(const uint32_t *L, uint32_t n, uint32_t c, uint64_t *used) {
+    *used += bit_width(n / 16) + 5;
+    const uint32_t i = lower_bound_last(L, n, c);
+    return i < n && L[2 * i] <= c;
+}
+
+// The triage of the batched kernels: whether the cell under the centre of
+// MBR(r) n MBR(s) lies in A(r) and F(s), or in F(r) and A(s) (a true hit).
+// *used counts the two MBRs (4 intervals' worth of bytes) and the lookups.
+static bool host_triage_hit(const april_sets *R, const april_sets *S, uint32_t r, uint32_t s, const uint8_t *lut,
+                            const uint32_t *Ar, uint32_t nar, const uint32_t *Fr, uint32_t nfr, const uint32_t *As,
+                            uint32_t nas, const uint32_t *Fs, uint32_t nfs, uint64_t *used) {
+    *used += 4;
+    const int32_t *a = &R->mbr[4 * (size_t)r], *b = &S->mbr[4 * (size_t)s];
+    const int64_t x0 = std::max(a[0], b[0]), y0 = std::max(a[1], b[1]), x1 = std::min(a[2], b[2]),
+                  y1 = std::min(a[3], b[3]);
+    if (x0 > x1 || y0 > y1) return false;
+    const int64_t cx = floor_div((x0 + x1) / 2 - R->grid_ox, (int64_t)1 << R->grid_log2_cell);
+    const int64_t cy = floor_div((y0 + y1) / 2 - R->grid_oy, (int64_t)1 << R->grid_log2_cell);
+    const int64_t side = (int64_t)1 << R->order;
+    if (cx < 0 || cy < 0 || cx >= side || cy >= side) return false;
+    const uint32_t c = (uint32_t)hilbert_id_lut(lut, R->order, (uint32_t)cx, (uint32_t)cy);
+    if (nfs && nar) {  // the kernel looks both lists up in lockstep
+        const bool h1 = host_list_holds(Fs, nfs, c, used), h2 = host_list_holds(Ar, nar, c, used);
+        if (h1 && h2) return true;
+    }
+    if (nfr && nas) {
+        const bool h1 = host_list_holds(Fr, nfr, c, used), h2 = host_list_holds(As, nas, c, used);
+        if (h1 && h2) return true;
+    }
+    return false;
+}
+
 static april_status host_filter(const april_sets *R, const april_sets *S, const uint32_t *pr, const uint32_t *ps,
                                 uint64_t n, uint32_t n_threads, uint8_t *verdict, uint64_t *consumed, bool searched) {
     auto join = searched ? host_join_searched : host_join;
     if (!R || !S || (n && (!pr || !ps || !verdict))) return fail(APRIL_ERR_INVALID_ARG, "NULL argument");
     if (R->parts != S->parts || R->order != S->order) return fail(APRIL_ERR_INVALID_ARG, "R and S use different grids");
+    // the batched kernels' triage applies to sets built on one shared grid
+    const bool triage = searched && !R->parts && R->grid_known && S->grid_known && R->grid_ox == S->grid_ox &&
+                        R->grid_oy == S->grid_oy && R->grid_log2_cell == S->grid_log2_cell;
+    uint8_t lut[64];
+    hilbert_lut_build(lut);
     parallel_for(n, resolve_threads(n_threads), 4096, [&](uint32_t, uint64_t b, uint64_t e) {
         for (uint64_t k = b; k < e; ++k) {
             uint32_t r = pr[k], s = ps[k];
@@ -890,7 +952,14 @@ static april_status host_filter(const april_sets *R, const april_sets *S, const 
                     else if (join(Ar, dr[1], Fs, ds[3], &used)) v = APRIL_TRUE_HIT;
                     else if (join(Fr, dr[3], As, ds[1], &used)) v = APRIL_TRUE_HIT;
                     else v = APRIL_INCONCLUSIVE;
-                } else {  // the GPU kernels' order: AF, AA, FA (same verdicts)
+                } else if (triage && host_triage_hit(R, S, r, s, lut, Ar, dr[1], Fr, dr[3], As, ds[1], Fs, ds[3], &used)) {
+                    v = APRIL_TRUE_HIT;  // settled by the triage (an AF or FA overlap)
+                } else if (triage) {  // the pairs the triage left: AA, AF, FA, as the kernels join them
+                    if (!join(Ar, dr[1], As, ds[1], &used)) v = APRIL_TRUE_NEGATIVE;
+                    else if (join(Ar, dr[1], Fs, ds[3], &used)) v = APRIL_TRUE_HIT;
+                    else if (join(Fr, dr[3], As, ds[1], &used)) v = APRIL_TRUE_HIT;
+                    else v = APRIL_INCONCLUSIVE;
+                } else {  // the GPU kernels' order without the triage: AF, AA, FA (same verdicts)
                     if (join(Ar, dr[1], Fs, ds[3], &used)) v = APRIL_TRUE_HIT;
                     else if (!join(Ar, dr[1], As, ds[1], &used)) v = APRIL_TRUE_NEGATIVE;
                     else if (join(Fr, dr[3], As, ds[1], &used)) v = APRIL_TRUE_HIT;

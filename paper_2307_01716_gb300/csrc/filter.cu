@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "april_internal.h"
+#include "geom.h"
 #include "join_device.cuh"
 
 using namespace april_dev;
@@ -51,6 +52,13 @@ constexpr uint32_t kCtaWMax = 2048;              // largest CTA window per list
 // cta_threshold value meaning "no long pairs": every pair goes to the lane
 // groups, whatever its length, and the binning kernel is not launched
 constexpr uint32_t kNoLongPairs = 0xffffffffu;
+// join_order value meaning: AA, AF, FA when the triage ran (the pairs left are
+// mostly true negatives and inconclusive pairs, which AA settles or must
+// see), AF, AA, FA otherwise (most true hits end in AF)
+constexpr uint32_t kJoinOrderAuto = 2;
+static inline uint32_t join_order_of(uint32_t jo, bool triaged) {
+    return jo == kJoinOrderAuto ? (triaged ? 1u : 0u) : jo;
+}
 constexpr uint32_t kWarpFirstWindow = 64;        // first window of a join in APRIL_MODE_WARP
 constexpr uint32_t kWarpBuf = kWarpWMax + 2;     // staging buffer per list (odd start + rounding)
 constexpr uint32_t kCtaBuf = kCtaWMax + 2;
@@ -85,7 +93,8 @@ static_assert(kWarpBuf % 2 == 0 && kCtaBuf % 2 == 0, "buffers must stay 16-byte 
 // entries of partitioned sets, then the queue of joins handed from the lane
 // groups to whole warps (one uint4 {pair, step, i0, j0} each, room for a
 // quarter of the pairs; when it is full a group finishes its join itself)
-constexpr uint32_t C_BIG_COUNT = 0, C_BIG_HEAD = 1, C_CHUNK_HEAD = 2, C_ESC_COUNT = 3, C_ESC_HEAD = 4;
+constexpr uint32_t C_BIG_COUNT = 0, C_BIG_HEAD = 1, C_CHUNK_HEAD = 2, C_ESC_COUNT = 3, C_ESC_HEAD = 4,
+                   C_REST_COUNT = 5;
 static inline uint64_t esc_capacity(uint64_t n) { return (n + 3) / 4; }
 constexpr uint32_t kMaxEscalateWindows = 64;
 constexpr size_t kCounterBytes = 256;
@@ -319,6 +328,156 @@ __global__ void __launch_bounds__(256) k_bin(SetsT R, SetsT S, const uint32_t *_
     }
 }
 
+// --------------------------------------------------- K2: triage (batched)
+// A true hit proven by one cell.  The cell c under the centre of
+// MBR(r) n MBR(s), on the sets' grid, is looked up in A(r) and F(s), then in
+// F(r) and A(s): if one pair of lists holds it, the AF or FA join has an
+// overlap and Algorithm 2's verdict is a true hit (Sec. 4.2: an AF or FA
+// overlap implies the AA one, so the verdict is the same in any join order).
+// The pairs the probe does not settle are listed, with warp-aggregated
+// appends, for the lane groups; out-of-range ids get error verdicts.  One
+// thread per pair.  A lookup is a binary search over the list's skip index
+// (posts below c), then over the at most 16 intervals that follow.
+struct TriageGrid {
+    int64_t ox, oy;
+    uint32_t log2_cell, order;
+};
+
+// The table of april_geom::hilbert_lut_build, passed by value to the
+// triage kernel, which copies it to shared memory.
+struct HilbertLut {
+    uint8_t e[64];
+};
+
+static HilbertLut triage_lut() {
+    HilbertLut L{};
+    april_geom::hilbert_lut_build(L.e);
+    return L;
+}
+
+// Lookups of cell c0 in list L0 and of c1 in L1 (for two pairs a thread
+// handles at once), each only where `on`: binary searches in lockstep, so that
+// their loads overlap.  A list holds cell c when its first interval whose
+// last cell reaches c starts at or before c; the search runs over the list's
+// skip index (posts below c), then over the at most 16 intervals that follow.
+__device__ __forceinline__ void holds2(const RawList &L0, uint32_t c0, bool on0, const RawList &L1, uint32_t c1,
+                                       bool on1, bool &h0, bool &h1) {
+    on0 = on0 && L0.n;
+    on1 = on1 && L1.n;
+    uint32_t lo0 = 0, hi0 = on0 ? L0.keys_n() : 0u, lo1 = 0, hi1 = on1 ? L1.keys_n() : 0u;
+    while (lo0 < hi0 || lo1 < hi1) {
+        const bool a0 = lo0 < hi0, a1 = lo1 < hi1;
+        const uint32_t m0 = (lo0 + hi0) >> 1, m1 = (lo1 + hi1) >> 1;
+        const uint32_t k0 = a0 ? L0.key(m0) : 0u, k1 = a1 ? L1.key(m1) : 0u;
+        if (a0) {
+            if (k0 < c0) lo0 = m0 + 1;
+            else hi0 = m0;
+        }
+        if (a1) {
+            if (k1 < c1) lo1 = m1 + 1;
+            else hi1 = m1;
+        }
+    }
+    uint32_t a = on0 ? L0.start_of(lo0) : 0u, b = on0 ? min(L0.n, a + 16u) : 0u;
+    uint32_t p = on1 ? L1.start_of(lo1) : 0u, q = on1 ? min(L1.n, p + 16u) : 0u;
+    while (a < b || p < q) {
+        const bool a0 = a < b, a1 = p < q;
+        const uint32_t m0 = (a + b) >> 1, m1 = (p + q) >> 1;
+        const uint32_t l0 = a0 ? __ldg(&L0.p[m0].y) - 1u : 0u, l1 = a1 ? __ldg(&L1.p[m1].y) - 1u : 0u;
+        if (a0) {
+            if (l0 < c0) a = m0 + 1;
+            else b = m0;
+        }
+        if (a1) {
+            if (l1 < c1) p = m1 + 1;
+            else q = m1;
+        }
+    }
+    const bool r0 = on0 && a < L0.n, r1 = on1 && p < L1.n;
+    const uint32_t s0 = r0 ? __ldg(&L0.p[a].x) : 0u, s1 = r1 ? __ldg(&L1.p[p].x) : 0u;
+    h0 = r0 && s0 <= c0;
+    h1 = r1 && s1 <= c1;
+}
+
+// The probe cell of pair (r, s): the cell under the centre of
+// MBR(r) n MBR(s); false when the MBRs are disjoint or the centre is off the grid.
+__device__ __forceinline__ bool triage_cell(const int4 *__restrict__ mbr_r, const int4 *__restrict__ mbr_s,
+                                            const TriageGrid &g, const uint8_t *lut, uint32_t r, uint32_t s,
+                                            uint32_t &c) {
+    const int4 a = __ldg(mbr_r + r), b = __ldg(mbr_s + s);
+    const int64_t x0 = max(a.x, b.x), y0 = max(a.y, b.y), x1 = min(a.z, b.z), y1 = min(a.w, b.w);
+    if (x0 > x1 || y0 > y1) return false;
+    const int64_t cx = ((x0 + x1) / 2 - g.ox) >> g.log2_cell, cy = ((y0 + y1) / 2 - g.oy) >> g.log2_cell;
+    const int64_t side = (int64_t)1 << g.order;
+    if (cx < 0 || cy < 0 || cx >= side || cy >= side) return false;
+    c = (uint32_t)april_geom::hilbert_id_lut(lut, g.order, (uint32_t)cx, (uint32_t)cy);
+    return true;
+}
+
+// One thread per two pairs (k and k + 32 of its warp's 64): ids, probe cells,
+// then F(s) and, where it holds the cell, A(r); then F(r) and A(s) for the
+// pairs not settled yet.  Six CTAs per SM (at most 40 registers a thread):
+// the kernel waits on chains of dependent loads, and more threads hide more.
+#ifndef APRIL_TRIAGE_MIN_BLOCKS
+#define APRIL_TRIAGE_MIN_BLOCKS 6
+#endif
+__global__ void __launch_bounds__(256, APRIL_TRIAGE_MIN_BLOCKS) k_triage(RawSets R, RawSets S, const int4 *__restrict__ mbr_r,
+                                                const int4 *__restrict__ mbr_s, TriageGrid g, HilbertLut lut_in,
+                                                const uint32_t *__restrict__ pr, const uint32_t *__restrict__ ps,
+                                                uint64_t n, uint8_t *__restrict__ out, uint32_t *status,
+                                                uint32_t *rest, uint32_t *counters) {
+    __shared__ uint8_t lut[64];
+    if (threadIdx.x < 64) lut[threadIdx.x] = lut_in.e[threadIdx.x];
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t stride = 2ull * gridDim.x * blockDim.x;
+    for (uint64_t kb = 2ull * ((uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u)); kb < n; kb += stride) {
+        const uint64_t k[2] = {kb + lane, kb + 32 + lane};
+        bool valid[2], probe[2] = {false, false}, hit[2] = {false, false};
+        uint32_t c[2] = {0, 0};
+        uint4 dr[2], ds[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            valid[h] = false;
+            dr[h] = ds[h] = make_uint4(0, 0, 0, 0);
+            if (k[h] < n) {
+                const uint32_t r = __ldg(pr + k[h]), s = __ldg(ps + k[h]);
+                if (r < R.n() && s < S.n()) {
+                    valid[h] = true;
+                    dr[h] = R.load(r);
+                    ds[h] = S.load(s);
+                    probe[h] = triage_cell(mbr_r, mbr_s, g, lut, r, s, c[h]);
+                } else {
+                    out[k[h]] = APRIL_VERDICT_ERROR;
+                    atomicOr(status, ST_BAD_ID);
+                }
+            }
+        }
+        bool f0, f1;
+        holds2(S.list(ds[0], true), c[0], probe[0], S.list(ds[1], true), c[1], probe[1], f0, f1);  // F(s)
+        holds2(R.list(dr[0], false), c[0], f0, R.list(dr[1], false), c[1], f1, hit[0], hit[1]);    // A(r)
+        holds2(R.list(dr[0], true), c[0], probe[0] && !hit[0], R.list(dr[1], true), c[1], probe[1] && !hit[1], f0,
+               f1);                                                                                   // F(r)
+        bool g0, g1;
+        holds2(S.list(ds[0], false), c[0], f0, S.list(ds[1], false), c[1], f1, g0, g1);            // A(s)
+        hit[0] = hit[0] || g0;
+        hit[1] = hit[1] || g1;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (valid[h] && hit[h]) out[k[h]] = APRIL_TRUE_HIT;
+            const bool keep = valid[h] && !hit[h];
+            const uint32_t mask = __ballot_sync(kFull, keep);
+            if (mask) {
+                const uint32_t leader = __ffs(mask) - 1;
+                uint32_t pos = 0;
+                if (lane == leader) pos = atomicAdd(&counters[C_REST_COUNT], __popc(mask));
+                pos = __shfl_sync(kFull, pos, leader) + __popc(mask & ((1u << lane) - 1u));
+                if (keep) rest[pos] = (uint32_t)k[h];
+            }
+        }
+    }
+}
+
 // ------------------------------------------ K3: persistent filter (batched)
 // Group engine.  A warp is split into 32/G groups of G lanes; each group
 // filters one pair at a time (its three joins in Algorithm 2's order), with
@@ -438,21 +597,21 @@ template <uint32_t G, class SetsT>
 __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, const uint32_t *__restrict__ pr,
                                              const uint32_t *__restrict__ ps, uint64_t n, uint8_t *__restrict__ out,
                                              uint32_t *status, uint32_t *counters, uint32_t cta_threshold, uint2 *wbuf,
-                                             uint4 *chunk_desc, uint8_t *chunk_lane, uint32_t bars, uint32_t lane,
-                                             uint32_t w0, uint32_t jo, uint32_t esc_windows, uint4 *esc,
-                                             uint32_t esc_cap) {
+                                             uint4 *chunk_desc, uint32_t *chunk_k, uint32_t bars,
+                                             uint32_t lane, uint32_t w0, uint32_t jo, uint32_t esc_windows, uint4 *esc,
+                                             uint32_t esc_cap, const uint32_t *__restrict__ rest) {
     using C = GroupCfg<G>;
     const bool no_long = cta_threshold == kNoLongPairs;  // every pair is joined here; no binning kernel ran
+
     const uint32_t g = lane / G, t = lane % G, glead = g * G;
     const uint32_t gbits = (G == 32 ? kFull : ((1u << G) - 1u)) << glead;
     uint2 *xb = wbuf + g * 2 * C::BUF, *yb = xb + C::BUF;
     const uint32_t bar = bars + 8u * g;  // this group's mbarrier
     uint32_t phase = 0;
-    const uint64_t nchunks = (n + 31) / 32;
-    // the warp's chunk of 32 pairs from pair `base`: pair base + l has its two
-    // descriptors in chunk_desc[l] and chunk_desc[32 + l]; chunk_lane lists
-    // the lanes of the eligible pairs in order, and its entries
-    // [cur, cur + left) are still to be handed out
+    // the warp's chunk of 32 pairs (from position `base` of the pair list or
+    // of the triage's list): the pairs it takes are stored compacted, pair
+    // chunk_k[i] with its two descriptors in chunk_desc[i] and
+    // chunk_desc[32 + i]; entries [cur, cur + left) are still to be handed out
     uint32_t base = 0;
     uint32_t cur = 0, left = 0;
     bool exhausted = false;
@@ -475,7 +634,9 @@ __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, con
                 uint32_t c = 0;
                 if (lane == 0) c = atomicAdd(&counters[C_CHUNK_HEAD], 1u);
                 c = __shfl_sync(kFull, c, 0);
-                if (c >= nchunks) {
+                // the pairs to join: all n, or the ones the triage listed (rest)
+                const uint64_t nn = rest ? (uint64_t)*((volatile uint32_t *)&counters[C_REST_COUNT]) : n;
+                if (c >= (nn + 31) / 32) {
                     exhausted = true;
                     break;
                 }
@@ -483,20 +644,28 @@ __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, con
                 const uint32_t qk = base + lane;
                 bool take = false;
                 __syncwarp();  // every group has read its descriptors from the previous chunk
-                if (qk < n) {
-                    const uint32_t r = __ldg(pr + qk), s2 = __ldg(ps + qk);
+                uint32_t kk = 0;
+                uint4 qdr = make_uint4(0, 0, 0, 0), qds = qdr;
+                if (qk < nn) {
+                    kk = rest ? __ldg(rest + qk) : qk;
+                    const uint32_t r = __ldg(pr + kk), s2 = __ldg(ps + kk);
                     if (r < R.n() && s2 < S.n()) {
-                        const uint4 qdr = R.load(r), qds = S.load(s2);
-                        chunk_desc[lane] = qdr;
-                        chunk_desc[32 + lane] = qds;
+                        qdr = R.load(r);
+                        qds = S.load(s2);
                         take = no_long || (uint64_t)qdr.y + qds.y <= (uint64_t)cta_threshold;
                     } else if (no_long) {  // no binning kernel ran to report them
-                        out[qk] = APRIL_VERDICT_ERROR;
+                        out[kk] = APRIL_VERDICT_ERROR;
                         atomicOr(status, ST_BAD_ID);
                     }
                 }
+                // the pairs this warp takes, compacted in order
                 const uint32_t tb = __ballot_sync(kFull, take);
-                if (take) chunk_lane[__popc(tb & ((1u << lane) - 1u))] = (uint8_t)lane;
+                if (take) {
+                    const uint32_t pos = __popc(tb & ((1u << lane) - 1u));
+                    chunk_k[pos] = kk;
+                    chunk_desc[pos] = qdr;
+                    chunk_desc[32 + pos] = qds;
+                }
                 cur = 0;
                 left = __popc(tb);
                 __syncwarp();
@@ -506,8 +675,8 @@ __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, con
             const uint32_t grank = __popc(needg & ((1u << glead) - 1u));
             const bool gets = ((needg >> glead) & 1u) && grank < cnt;
             if (gets) {
-                const uint32_t src = chunk_lane[cur + grank];
-                k = base + src;
+                const uint32_t src = cur + grank;
+                k = chunk_k[src];
                 dr = chunk_desc[src];
                 ds = chunk_desc[32 + src];
                 stage = 0;
@@ -590,7 +759,7 @@ __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, con
             // and stop this warp
             if (!ok) mbar_drain(bar, phase ^ 1u);
             if (active && t == 0) out[k] = APRIL_VERDICT_ERROR;
-            if (lane < left) out[base + chunk_lane[cur + lane]] = APRIL_VERDICT_ERROR;
+            if (lane < left) out[chunk_k[cur + lane]] = APRIL_VERDICT_ERROR;
             if (lane == 0) atomicOr(status, ST_TIMEOUT);
             return;
         }
@@ -667,13 +836,14 @@ __global__ void APRIL_PERSISTENT_BOUNDS k_persistent(SetsT R, SetsT S,
                                                        uint8_t *__restrict__ out, uint32_t *status,
                                                        uint32_t cta_threshold, const uint32_t *__restrict__ big_list,
                                                        uint32_t *counters, uint32_t w0_group, uint32_t w0_cta,
-                                                       uint32_t jo, uint32_t esc_windows, uint4 *esc, uint32_t esc_cap) {
+                                                       uint32_t jo, uint32_t esc_windows, uint4 *esc, uint32_t esc_cap,
+                                                       const uint32_t *__restrict__ rest) {
     using C = GroupCfg<G>;
     __shared__ __align__(16) uint2 sm[kWarpsPerBlock * C::SHARE];
     __shared__ uint32_t s_item, s_slot;
     __shared__ uint64_t bars[C::BARS];  // see GroupCfg
     __shared__ uint4 s_chunk[kWarpsPerBlock][64];     // group engine: each warp's chunk descriptors
-    __shared__ uint8_t s_chunk_lane[kWarpsPerBlock][32];  // and the chunk lanes they came from
+    __shared__ uint32_t s_chunk_k[kWarpsPerBlock][32];    // and their pairs
     if constexpr (kStage2 && G < 32 && !SetsT::kPacked) {
         // the lane groups' mbarriers take two arrivals a window (see group_engine)
         for (uint32_t i = threadIdx.x; i < C::BARS; i += blockDim.x) {
@@ -741,9 +911,9 @@ __global__ void APRIL_PERSISTENT_BOUNDS k_persistent(SetsT R, SetsT S,
                 return;
         }
     } else {
-        group_engine<G>(R, S, pr, ps, n, out, status, counters, cta_threshold, wbuf, s_chunk[warp],
-                        s_chunk_lane[warp], smem_addr(&bars[C::group_bar(warp, 0)]), lane, w0_group, jo,
-                        esc_windows, esc, esc_cap);
+        group_engine<G>(R, S, pr, ps, n, out, status, counters, cta_threshold, wbuf, s_chunk[warp], s_chunk_k[warp],
+                        smem_addr(&bars[C::group_bar(warp, 0)]), lane, w0_group, jo, esc_windows, esc, esc_cap,
+                        rest);
     }
 }
 
@@ -975,8 +1145,14 @@ struct GraphKey {
     bool packed;
     uint32_t parts;
     const void *r_pdesc, *s_pdesc;
+    const void *r_mbr, *s_mbr;
+    int64_t r_ox, r_oy, s_ox, s_oy;
+    uint32_t r_log2, s_log2, r_grid, s_grid;
     bool operator==(const GraphKey &o) const {
         return packed == o.packed && parts == o.parts && r_pdesc == o.r_pdesc && s_pdesc == o.s_pdesc &&
+               r_mbr == o.r_mbr && s_mbr == o.s_mbr && r_ox == o.r_ox && r_oy == o.r_oy && s_ox == o.s_ox &&
+               s_oy == o.s_oy && r_log2 == o.r_log2 && s_log2 == o.s_log2 && r_grid == o.r_grid &&
+               s_grid == o.s_grid && tune.triage_off == o.tune.triage_off &&
                r_desc == o.r_desc && r_iv == o.r_iv && s_desc == o.s_desc && s_iv == o.s_iv &&
                r_posts == o.r_posts && s_posts == o.s_posts && rn == o.rn &&
                sn == o.sn && d_r == o.d_r && d_s == o.d_s && out == o.out && scratch == o.scratch && n == o.n &&
@@ -1025,8 +1201,9 @@ static april_tune default_tune() {
     t.group_lanes = 4;
     t.group_window = 32;
     t.cta_window = 128;      // with a threshold set: long pairs one per warp, first window 128
-    t.join_order = 0;        // AF, AA, FA
+    t.join_order = kJoinOrderAuto;  // AA first after the triage, AF first otherwise
     t.escalate_windows = 0;  // lane groups finish every join they start
+    t.triage_off = 0;        // the triage pass runs where it applies
     t.blocks_per_sm = 0;
     t.ms = 0.f;
     return t;
@@ -1040,8 +1217,10 @@ static april_status check_tune(const april_tune &t) {
         return fail(APRIL_ERR_INVALID_ARG, "group_window must be a power of two in [group_lanes, 8*group_lanes]");
     if (t.cta_window < 32 || t.cta_window > kCtaWMax || (t.cta_window & (t.cta_window - 1)))
         return fail(APRIL_ERR_INVALID_ARG, "cta_window must be a power of two in [32, 2048]");
-    if (t.join_order > 1) return fail(APRIL_ERR_INVALID_ARG, "join_order must be 0 (AF AA FA) or 1 (AA AF FA)");
+    if (t.join_order > kJoinOrderAuto)
+        return fail(APRIL_ERR_INVALID_ARG, "join_order must be 0 (AF AA FA), 1 (AA AF FA) or 2 (automatic)");
     if (t.escalate_windows > kMaxEscalateWindows) return fail(APRIL_ERR_INVALID_ARG, "escalate_windows must be 0..64");
+    if (t.triage_off > 1) return fail(APRIL_ERR_INVALID_ARG, "triage_off must be 0 or 1");
     return APRIL_OK;
 }
 
@@ -1155,6 +1334,12 @@ extern "C" april_status april_upload(const april_sets *S, void *dev_buf, size_t 
     out->parts = S->parts;
     out->mbr = S->mbr.empty() ? nullptr : (const int32_t *)(base + L.mbr);
     out->posts = (const uint32_t *)(base + L.posts);
+    if (S->grid_known && !S->parts && !S->mbr.empty()) {
+        out->grid_ox = S->grid_ox;
+        out->grid_oy = S->grid_oy;
+        out->grid_log2_cell = S->grid_log2_cell;
+        out->grid_known = 1;
+    }
     if (S->parts) {
         out->obj_ll = (const int32_t *)(base + L.obj_ll);
         out->obj_entry = (const uint32_t *)(base + L.obj_entry);
@@ -1224,6 +1409,19 @@ static inline PartView part_view(const april_dev_sets *d) {
 // tuning escalates long joins, K3b for the joins the lane groups handed over.
 // `esc_windows` overrides the tuning's escalate_windows (the allocation-free
 // entry point has no room for the queue and passes 0).
+// Whether the triage pass (K2) runs before the lane groups: raw sets on one
+// shared grid whose MBRs are known, and a tuning with every pair in lane
+// groups of 4..16 lanes.
+static bool triage_applies(const april_tune &t, const april_dev_sets *R, const april_dev_sets *S, bool packed) {
+    return !t.triage_off && t.cta_threshold == kNoLongPairs && t.group_lanes < 32 && !packed && !R->parts &&
+           R->grid_known && S->grid_known && R->mbr && S->mbr && R->order == S->order && R->grid_ox == S->grid_ox &&
+           R->grid_oy == S->grid_oy && R->grid_log2_cell == S->grid_log2_cell;
+}
+
+static TriageGrid triage_grid(const april_dev_sets *R) {
+    return TriageGrid{R->grid_ox, R->grid_oy, R->grid_log2_cell, R->order};
+}
+
 static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, const april_dev_sets *Sd,
                                    const uint32_t *d_r, const uint32_t *d_s, uint64_t n, uint8_t *out, void *scratch,
                                    bool packed, unsigned grid_bin, unsigned grid_main, cudaStream_t st,
@@ -1250,12 +1448,13 @@ static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, con
     }
     if (packed) {
         const PackedSets R = packed_set(Rd), S = packed_set(Sd);
+        const uint32_t jo = join_order_of(t.join_order, false);
         if (t.cta_threshold != kNoLongPairs)
             k_bin<<<grid_bin, 256, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold, big_list, counters);
 #define APRIL_LAUNCH_PACKED(G)                                                                                  \
     k_persistent<G, PackedSets><<<grid_main, kBlock, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold,   \
                                                               big_list, counters, t.group_window, t.cta_window,   \
-                                                              t.join_order, escw, esc, esc_cap)
+                                                              jo, escw, esc, esc_cap, nullptr)
         switch (t.group_lanes) {
             case 4: APRIL_LAUNCH_PACKED(4); break;
             case 8: APRIL_LAUNCH_PACKED(8); break;
@@ -1264,17 +1463,23 @@ static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, con
         }
 #undef APRIL_LAUNCH_PACKED
         if (escw)
-            k_long<<<grid_long, kBlock, 0, st>>>(R, S, d_r, d_s, out, status, esc, counters, esc_cap, w0_long,
-                                                  t.join_order);
+            k_long<<<grid_long, kBlock, 0, st>>>(R, S, d_r, d_s, out, status, esc, counters, esc_cap, w0_long, jo);
         return cudaGetLastError();
     }
     const RawSets R{dev_set(Rd)}, S{dev_set(Sd)};
-    if (t.cta_threshold != kNoLongPairs)
+    const uint32_t *rest = nullptr;  // the pairs the lane groups join (nullptr: all)
+    if (triage_applies(t, Rd, Sd, false)) {
+        k_triage<<<grid_bin, 256, 0, st>>>(R, S, (const int4 *)Rd->mbr, (const int4 *)Sd->mbr, triage_grid(Rd),
+                                           triage_lut(), d_r, d_s, n, out, status, big_list, counters);
+        rest = big_list;
+    } else if (t.cta_threshold != kNoLongPairs) {
         k_bin<<<grid_bin, 256, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold, big_list, counters);
+    }
+    const uint32_t jo = join_order_of(t.join_order, rest != nullptr);
 #define APRIL_LAUNCH_PERSISTENT(G)                                                                            \
     k_persistent<G, RawSets><<<grid_main, kBlock, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold,       \
                                                            big_list, counters, t.group_window, t.cta_window,      \
-                                                           t.join_order, escw, esc, esc_cap)
+                                                           jo, escw, esc, esc_cap, rest)
     switch (t.group_lanes) {
         case 4: APRIL_LAUNCH_PERSISTENT(4); break;
         case 8: APRIL_LAUNCH_PERSISTENT(8); break;
@@ -1283,8 +1488,7 @@ static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, con
     }
 #undef APRIL_LAUNCH_PERSISTENT
     if (escw)
-        k_long<<<grid_long, kBlock, 0, st>>>(R, S, d_r, d_s, out, status, esc, counters, esc_cap, w0_long,
-                                              t.join_order);
+        k_long<<<grid_long, kBlock, 0, st>>>(R, S, d_r, d_s, out, status, esc, counters, esc_cap, w0_long, jo);
     return cudaGetLastError();
 }
 
@@ -1299,8 +1503,11 @@ static april_status launch_batched(april_ctx *ctx, const april_dev_sets *R, cons
     const int occ = ctx->persistent_blocks_per_sm[(packed ? 4 : 0) + group_index(gl)];
     const int bps = ctx->tune.blocks_per_sm ? (int)std::min<uint32_t>(ctx->tune.blocks_per_sm, (uint32_t)occ) : occ;
     const unsigned grid_main = (unsigned)std::max(1, ctx->num_sms * bps);
-    GraphKey key{R->desc, R->iv, S->desc, S->iv, R->posts, S->posts, R->n_objects, S->n_objects, d_r, d_s, out,
-                 scratch, n, ctx->tune, grid_bin, grid_main, packed, R->parts, R->pdesc, S->pdesc};
+    GraphKey key{R->desc,         R->iv,          S->desc,          S->iv,          R->posts,       S->posts,
+                 R->n_objects,    S->n_objects,   d_r,              d_s,            out,            scratch,
+                 n,               ctx->tune,      grid_bin,         grid_main,      packed,         R->parts,
+                 R->pdesc,        S->pdesc,       R->mbr,           S->mbr,         R->grid_ox,     R->grid_oy,
+                 S->grid_ox,      S->grid_oy,     R->grid_log2_cell, S->grid_log2_cell, R->grid_known, S->grid_known};
     cudaError_t e;
     if (!ctx->graph || !(key == ctx->key)) {
         if (ctx->graph) {
@@ -1377,7 +1584,7 @@ extern "C" april_status april_filter_pairs(april_ctx *ctx, const april_dev_sets 
             uint64_t blocks = (n + kBlock - 1) / kBlock;
             unsigned grid = (unsigned)std::min<uint64_t>(blocks, (uint64_t)sms * 16);
             k_warp<<<grid, kBlock, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, ctx->d_status, kWarpFirstWindow,
-                                            ctx->tune.join_order);
+                                            join_order_of(ctx->tune.join_order, false));
             break;
         }
         case APRIL_MODE_BATCHED:
@@ -1466,7 +1673,7 @@ extern "C" april_status april_filter_pairs_ex(april_ctx *ctx, const april_dev_se
     uint32_t *counters = (uint32_t *)d_scratch;
     uint32_t *big_list = (uint32_t *)((char *)d_scratch + kCounterBytes);
     const RawSets dR{dev_set(R)}, dS{dev_set(S)};
-    const Plan P = make_plan(predicate, R->order, S->order, ctx->tune.join_order);
+    const Plan P = make_plan(predicate, R->order, S->order, join_order_of(ctx->tune.join_order, false));
     const unsigned grid_bin = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)ctx->num_sms * 8);
     int bps = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_general, kBlock, 0);
@@ -1745,7 +1952,7 @@ NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
 // The persistent kernel instance for the default tuning's lane groups.
 using PersistentRaw = void (*)(RawSets, RawSets, const uint32_t *, const uint32_t *, uint64_t, uint8_t *,
                                uint32_t *, uint32_t, const uint32_t *, uint32_t *, uint32_t, uint32_t, uint32_t,
-                               uint32_t, uint4 *, uint32_t);
+                               uint32_t, uint4 *, uint32_t, const uint32_t *);
 static PersistentRaw noalloc_kernel(uint32_t group_lanes) {
     switch (group_lanes) {
         case 4: return k_persistent<4, RawSets>;
@@ -1814,12 +2021,19 @@ extern "C" april_status april_filter_pairs_noalloc(const april_dev_sets *R, cons
     const RawSets dR{dev_set(R)}, dS{dev_set(S)};
     const unsigned grid_bin = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)nd.num_sms * 8);
     const unsigned grid_main = (unsigned)std::max(1, nd.num_sms * nd.blocks_per_sm);
-    if (t.cta_threshold != kNoLongPairs)
+    const uint32_t *rest = nullptr;
+    if (triage_applies(t, R, S, false)) {
+        k_triage<<<grid_bin, 256, 0, st>>>(dR, dS, (const int4 *)R->mbr, (const int4 *)S->mbr, triage_grid(R),
+                                           triage_lut(), d_r, d_s, n, d_verdict, status, big_list, counters);
+        rest = big_list;
+    } else if (t.cta_threshold != kNoLongPairs) {
         k_bin<<<grid_bin, 256, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, status, t.cta_threshold, big_list, counters);
+    }
     // no escalation: the static array has no room for the queue of handed-over joins
     noalloc_kernel(t.group_lanes)<<<grid_main, kBlock, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, status,
                                                                 t.cta_threshold, big_list, counters, t.group_window,
-                                                                t.cta_window, t.join_order, 0u, nullptr, 0u);
+                                                                t.cta_window, join_order_of(t.join_order, rest != nullptr),
+                                                                0u, nullptr, 0u, rest);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "april_filter_pairs_noalloc launch");
     return APRIL_OK;

@@ -62,6 +62,47 @@ APRIL_HD void hilbert_cell(uint32_t order, uint64_t d, uint32_t &x, uint32_t &y)
     }
 }
 
+// Two levels of the map at once: entry (s << 4) | (x2 << 2) | y2 of the
+// table holds (the two base-4 digits << 2) | the next symmetry, for symmetry
+// s and two bits x2, y2 of each coordinate (the higher level in bit 1).
+APRIL_HD void hilbert_lut_build(uint8_t *lut) {
+    for (uint32_t s = 0; s < 4; ++s)
+        for (uint32_t x2 = 0; x2 < 4; ++x2)
+            for (uint32_t y2 = 0; y2 < 4; ++y2) {
+                uint32_t st = s, d = 0;
+                for (int k = 1; k >= 0; --k) {
+                    uint32_t bx = (x2 >> k) & 1u, by = (y2 >> k) & 1u;
+                    apply_sym(st, bx, by);
+                    const uint32_t digit = (bx << 1) | (bx ^ by);
+                    d = (d << 2) | digit;
+                    if (digit == 0) st ^= 1u;
+                    else if (digit == 3) st ^= 2u;
+                }
+                lut[(s << 4) | (x2 << 2) | y2] = (uint8_t)((d << 2) | st);
+            }
+}
+
+// hilbert_id by two levels a step through a table from hilbert_lut_build
+// (an odd order takes its top level alone, from symmetry 0).
+APRIL_HD uint64_t hilbert_id_lut(const uint8_t *lut, uint32_t order, uint32_t x, uint32_t y) {
+    uint32_t s = 0;
+    uint64_t d = 0;
+    int k = (int)order - 2;
+    if (order & 1u) {
+        const uint32_t bx = (x >> (order - 1)) & 1u, by = (y >> (order - 1)) & 1u;
+        const uint32_t digit = (bx << 1) | (bx ^ by);
+        d = digit;
+        s = digit == 0 ? 1u : digit == 3 ? 2u : 0u;
+        k = (int)order - 3;
+    }
+    for (; k >= 0; k -= 2) {
+        const uint32_t e = lut[(s << 4) | (((x >> k) & 3u) << 2) | ((y >> k) & 3u)];
+        d = (d << 4) | (e >> 2);
+        s = e & 3u;
+    }
+    return d;
+}
+
 // ------------------------------------------------------------- predicates
 APRIL_HD int64_t imin(int64_t a, int64_t b) { return a < b ? a : b; }
 APRIL_HD int64_t imax(int64_t a, int64_t b) { return a > b ? a : b; }

@@ -249,8 +249,12 @@ def test_tune_validation(ctx):
                 (100, 8, 32, 16), (100, 8, 32, 96)]:
         with pytest.raises(A.AprilError):
             ctx.set_tune(A.april_tune(*bad, 0, 0.0))
-    with pytest.raises(A.AprilError):
-        ctx.set_tune(A.april_tune(100, 8, 32, 64, 0, 0.0, 2))
+    saved = ctx.get_tune()
+    for bad in [(3, 0), (0, 2)]:  # join_order 3, triage_off 2
+        with pytest.raises(A.AprilError):
+            ctx.set_tune(A.april_tune(100, 8, 32, 64, 0, 0.0, bad[0], 0, bad[1]))
+    ctx.set_tune(A.april_tune(100, 8, 32, 64, 0, 0.0, 2, 0, 1))  # automatic join order, triage off: valid
+    ctx.set_tune(saved)
 
 
 def test_batched_scratch_checks(torch_cuda, ctx):
