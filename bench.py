@@ -80,8 +80,8 @@ def parse():
     ap.add_argument("--autotuned", action="store_true",
                     help="time the headline with the autotuner's pick instead of the default tuning")
     ap.add_argument("--tune", default=None,
-                    help="T,G,W,CW[,JO[,ESC]]: fixed batched tuning instead of the default (JO: join order 0 or 1; "
-                         "ESC: escalate_windows)")
+                    help="T,G,W,CW[,JO[,ESC[,TRIAGE_OFF]]]: fixed batched tuning instead of the default (JO: join "
+                         "order 0, 1 or 2 = automatic; ESC: escalate_windows; TRIAGE_OFF: 1 = no triage pass)")
     ap.add_argument("--no-workloads", action="store_true", help="skip the skewed and partitioned workloads")
     ap.add_argument("--no-oracle-sample", action="store_true", help="skip the oracle parity samples")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
@@ -114,7 +114,15 @@ def kernel_source_sha() -> str:
 
 def tune_key(t):
     return [t["cta_threshold"], t["group_lanes"], t["group_window"], t["cta_window"], t.get("join_order", 0),
-            t.get("escalate_windows", 0)]
+            t.get("escalate_windows", 0), t.get("triage_off", 0)]
+
+
+def triage_applies(tune, partitions, mode) -> bool:
+    """Whether the batched filter runs its triage kernel (include/april.h,
+    april_tune.triage_off): raw sets built from polygons (one grid or
+    partitioned), no long-pair threshold, lane groups below 32."""
+    return (mode == "batched" and tune is not None and not tune.get("triage_off", 0)
+            and tune["cta_threshold"] == 0xFFFFFFFF and tune["group_lanes"] < 32)
 
 
 def kernel_traffic(kernel: str, workload: str, mode: str, tune):
@@ -392,6 +400,11 @@ class Leg:
         achieved = self.b_alg / (ms * 1e-3) / 1e9
         kernel = {"plain": "k_plain", "warp": "k_warp", "batched": "k_persistent", "packed": "k_persistent"}[mode]
         traffic, src = kernel_traffic(kernel, self.w.name, mode, tune)
+        if triage_applies(tune, self.w.partitions, mode):
+            # the batched step is two kernels: the triage, then the lane groups
+            kernel = "k_triage + k_persistent"
+            t2, src2 = kernel_traffic("k_triage", self.w.name, mode, tune)
+            traffic, src = (traffic + t2, f"{src} + {src2}") if traffic is not None and t2 is not None else (None, None)
         r = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
              "traffic": traffic, "kernel": kernel, "peak_kind": f"{peak_kind} copy bandwidth (burst)",
              "achieved_bytes": "galloping search-start model (algorithmic_bytes_per_step)",
@@ -728,9 +741,11 @@ def selection_build_only(A, torch, dev):
 
 
 def parse_tune(A, spec):
+    """T,G,W,CW[,JO[,ESC[,TRIAGE_OFF]]] (april_tune; JO 2 = automatic when omitted)."""
     vals = [int(x) for x in spec.split(",")]
     T, G, W, CW = vals[:4]
-    return A.april_tune(T, G, W, CW, 0, 0.0, vals[4] if len(vals) > 4 else 0, vals[5] if len(vals) > 5 else 0)
+    return A.april_tune(T, G, W, CW, 0, 0.0, vals[4] if len(vals) > 4 else 2, vals[5] if len(vals) > 5 else 0,
+                        vals[6] if len(vals) > 6 else 0)
 
 
 def run_leg(A, torch, ctx, dev, stream, flush, cfg, args, mode, peak, peak_kind, default_tune, ws=1, rank=0,

@@ -252,7 +252,10 @@ typedef struct april_dev_sets {
     int64_t grid_ox;            /* grid_known: the grid the lists were built on (lattice origin, */
     int64_t grid_oy;            /*   log2 of the cell side); the batched filter's triage maps */
     uint32_t grid_log2_cell;    /*   MBR points to cells with it */
-    uint32_t grid_known;        /* 1: built from polygons on one grid (april_build_sets, april_build_sets_device) */
+    uint32_t grid_known;        /* 1: built from polygons (april_build_sets, april_build_sets_device,
+                                   april_build_partitioned_sets) */
+    const int64_t *part_grid;   /* parts > 0 and grid_known: per partition {ox, oy, log2_cell, used} */
+    uint64_t grid_id;           /* grid_known: fingerprint of the grid(s); the triage needs R's == S's */
 } april_dev_sets;
 
 /* Copies the sets into a caller-allocated device buffer of at least

@@ -91,7 +91,7 @@ class april_dev_sets(ctypes.Structure):
                 ("entry_pid", ctypes.c_void_p), ("pdesc", ctypes.c_void_p), ("anchors", ctypes.c_void_p),
                 ("gaps", ctypes.c_void_p), ("mbr", ctypes.c_void_p), ("posts", ctypes.c_void_p),
                 ("grid_ox", ctypes.c_int64), ("grid_oy", ctypes.c_int64), ("grid_log2_cell", ctypes.c_uint32),
-                ("grid_known", ctypes.c_uint32)]
+                ("grid_known", ctypes.c_uint32), ("part_grid", ctypes.c_void_p), ("grid_id", ctypes.c_uint64)]
 
 
 _vp = ctypes.c_void_p

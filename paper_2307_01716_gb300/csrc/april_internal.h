@@ -45,12 +45,14 @@ struct april_sets {
     std::vector<uint32_t> obj_entry;  // parts > 0: n + 1 entry offsets (entries of an object are contiguous)
     std::vector<uint32_t> entry_pid;  // parts > 0: partition id of each entry (ascending within an object)
     std::vector<int64_t> part_grid;   // parts > 0: 4 per partition: ox, oy, log2_cell, used(0/1)
-    // the grid of sets built from polygons on one grid (parts == 0): lattice
-    // origin and log2 of the cell side, with which the batched filter's
-    // triage maps an MBR point to its cell
+    // sets built from polygons: the grid of one-grid sets (parts == 0) as
+    // lattice origin and log2 of the cell side (partitioned sets: part_grid),
+    // with which the batched filter's triage maps an MBR point to its cell,
+    // and a fingerprint of the grid(s) (april_grid_id / april_part_grid_id)
     bool grid_known = false;
     int64_t grid_ox = 0, grid_oy = 0;
     uint32_t grid_log2_cell = 0;
+    uint64_t grid_id = 0;
     // compressed lists (Sec. 5.1), see april_sets_compress
     bool packed = false;
     std::vector<uint32_t> pdesc;      // 4 per entry: {a_block, a_len, f_block, f_len} (block-table indices)
@@ -59,6 +61,23 @@ struct april_sets {
 };
 
 inline uint64_t april_round256(uint64_t b) { return (b + 255) / 256 * 256; }
+
+// Fingerprints of the grids sets were built on (FNV-1a over the defining
+// integers): two sets may share the triage's cell mapping only when equal.
+inline uint64_t april_fnv(uint64_t h, int64_t v) {
+    for (int b = 0; b < 8; ++b) h = (h ^ (uint64_t)((v >> (8 * b)) & 0xFF)) * 1099511628211ull;
+    return h;
+}
+inline uint64_t april_grid_id(int64_t ox, int64_t oy, uint32_t log2_cell, uint32_t order) {
+    uint64_t h = 14695981039346656037ull;
+    for (int64_t v : {ox, oy, (int64_t)log2_cell, (int64_t)order}) h = april_fnv(h, v);
+    return h | 1;  // never 0
+}
+inline uint64_t april_part_grid_id(const std::vector<int64_t> &part_grid, uint32_t order, uint32_t parts) {
+    uint64_t h = april_fnv(april_fnv(14695981039346656037ull, order), parts);
+    for (int64_t v : part_grid) h = april_fnv(h, v);
+    return h | 1;
+}
 
 // Skip index of a set's interval array ("posts"): posts[q] is the last cell
 // (end - 1, in uint32) of interval slot 16 q + 15, one word per 16 slots; the
@@ -72,9 +91,9 @@ int april_launch_posts(const uint32_t *iv, uint64_t iv_slots, uint32_t *posts, v
 // Device image layout (each section starts 256-byte aligned):
 //   desc (16 B/entry) | iv (8 B/slot, then a 16-byte pad) | posts (4 B per 16 slots) | obj_ll (8 B/object)
 //   | obj_entry (4 B x (n+1)) | entry_pid (4 B/entry) | pdesc (16 B/entry) | block table (8 B/block) | gaps
-//   | mbr (16 B/object)
+//   | mbr (16 B/object) | part_grid (32 B/partition: ox, oy, log2_cell, used as int64)
 struct april_image_layout {
-    uint64_t desc, iv, posts, obj_ll, obj_entry, entry_pid, pdesc, anchors, gaps, mbr, total;
+    uint64_t desc, iv, posts, obj_ll, obj_entry, entry_pid, pdesc, anchors, gaps, mbr, pgrid, total;
 };
 
 inline april_image_layout april_layout(const april_sets &S) {
@@ -100,6 +119,8 @@ inline april_image_layout april_layout(const april_sets &S) {
     o += april_round256((uint64_t)S.gaps.size());
     L.mbr = o;
     o += april_round256((uint64_t)S.mbr.size() * 4);
+    L.pgrid = o;
+    o += april_round256((uint64_t)S.part_grid.size() * 8);
     L.total = o;
     return L;
 }

@@ -887,5 +887,6 @@ extern "C" april_status april_build_sets_device(april_ctx *ctx, const int32_t *d
     out->grid_oy = g.oy;
     out->grid_log2_cell = grid->log2_cell;
     out->grid_known = 1;
+    out->grid_id = april_grid_id(g.ox, g.oy, grid->log2_cell, g.order);
     return APRIL_OK;
 }

@@ -363,6 +363,7 @@ extern "C" april_status april_build_sets(const int32_t *xy, const uint64_t *vert
         S->grid_ox = g.ox;
         S->grid_oy = g.oy;
         S->grid_log2_cell = grid->log2_cell;
+        S->grid_id = april_grid_id(g.ox, g.oy, grid->log2_cell, g.order);
         S->mbr.resize(4 * (size_t)n_polys);
         for (uint32_t p = 0; p < n_polys; ++p) {
             const Mbr m = poly_mbr(xy + 2 * vert_off[p], vert_off[p + 1] - vert_off[p]);
@@ -659,6 +660,8 @@ extern "C" april_status april_build_partitioned_sets(const int32_t *r_xy, const 
             S->order = order;
             S->parts = parts;
             S->part_grid = grid_desc;
+            S->grid_known = true;
+            S->grid_id = april_part_grid_id(grid_desc, order, parts);
             S->obj_ll.resize(2 * (size_t)S->n);
             S->mbr.resize(4 * (size_t)S->n);
             for (uint32_t p = 0; p < S->n; ++p) {
@@ -901,16 +904,18 @@ static bool host_list_holds(const uint32_t *L, uint32_t n, uint32_t c, uint64_t 
 // The triage of the batched kernels: whether the cell under the centre of
 // MBR(r) n MBR(s) lies in A(r) and F(s), or in F(r) and A(s) (a true hit).
 // *used counts the two MBRs (4 intervals' worth of bytes) and the lookups.
-static bool host_triage_hit(const april_sets *R, const april_sets *S, uint32_t r, uint32_t s, const uint8_t *lut,
-                            const uint32_t *Ar, uint32_t nar, const uint32_t *Fr, uint32_t nfr, const uint32_t *As,
-                            uint32_t nas, const uint32_t *Fs, uint32_t nfs, uint64_t *used) {
+// ro, so: the pairs' objects (their MBRs); the lists' grid: (ox, oy, log2_cell).
+static bool host_triage_hit(const april_sets *R, const april_sets *S, uint32_t ro, uint32_t so, int64_t ox,
+                            int64_t oy, uint32_t log2_cell, const uint8_t *lut, const uint32_t *Ar, uint32_t nar,
+                            const uint32_t *Fr, uint32_t nfr, const uint32_t *As, uint32_t nas, const uint32_t *Fs,
+                            uint32_t nfs, uint64_t *used) {
     *used += 4;
-    const int32_t *a = &R->mbr[4 * (size_t)r], *b = &S->mbr[4 * (size_t)s];
+    const int32_t *a = &R->mbr[4 * (size_t)ro], *b = &S->mbr[4 * (size_t)so];
     const int64_t x0 = std::max(a[0], b[0]), y0 = std::max(a[1], b[1]), x1 = std::min(a[2], b[2]),
                   y1 = std::min(a[3], b[3]);
     if (x0 > x1 || y0 > y1) return false;
-    const int64_t cx = floor_div((x0 + x1) / 2 - R->grid_ox, (int64_t)1 << R->grid_log2_cell);
-    const int64_t cy = floor_div((y0 + y1) / 2 - R->grid_oy, (int64_t)1 << R->grid_log2_cell);
+    const int64_t cx = floor_div((x0 + x1) / 2 - ox, (int64_t)1 << log2_cell);
+    const int64_t cy = floor_div((y0 + y1) / 2 - oy, (int64_t)1 << log2_cell);
     const int64_t side = (int64_t)1 << R->order;
     if (cx < 0 || cy < 0 || cx >= side || cy >= side) return false;
     const uint32_t c = (uint32_t)hilbert_id_lut(lut, R->order, (uint32_t)cx, (uint32_t)cy);
@@ -930,20 +935,27 @@ static april_status host_filter(const april_sets *R, const april_sets *S, const 
     auto join = searched ? host_join_searched : host_join;
     if (!R || !S || (n && (!pr || !ps || !verdict))) return fail(APRIL_ERR_INVALID_ARG, "NULL argument");
     if (R->parts != S->parts || R->order != S->order) return fail(APRIL_ERR_INVALID_ARG, "R and S use different grids");
-    // the batched kernels' triage applies to sets built on one shared grid
-    const bool triage = searched && !R->parts && R->grid_known && S->grid_known && R->grid_ox == S->grid_ox &&
-                        R->grid_oy == S->grid_oy && R->grid_log2_cell == S->grid_log2_cell;
+    // the batched kernels' triage applies to sets built from polygons on the same grid(s)
+    const bool triage = searched && R->grid_known && S->grid_known && R->grid_id == S->grid_id;
     uint8_t lut[64];
     hilbert_lut_build(lut);
     parallel_for(n, resolve_threads(n_threads), 4096, [&](uint32_t, uint64_t b, uint64_t e) {
         for (uint64_t k = b; k < e; ++k) {
             uint32_t r = pr[k], s = ps[k];
+            const uint32_t ro = r, so = s;
             uint64_t used = 0;
             uint8_t v;
             route_pair(R, S, r, s);
             if (r >= R->n_entries || s >= S->n_entries) {
                 v = APRIL_VERDICT_ERROR;
             } else {
+                int64_t gox = R->grid_ox, goy = R->grid_oy;
+                uint32_t glc = R->grid_log2_cell;
+                bool gok = true;
+                if (R->parts) {  // the entry's partition grid
+                    const int64_t *pg = &R->part_grid[4 * (size_t)R->entry_pid[r]];
+                    gox = pg[0], goy = pg[1], glc = (uint32_t)pg[2], gok = pg[3] != 0;
+                }
                 const uint32_t *dr = &R->desc[4 * (size_t)r], *ds = &S->desc[4 * (size_t)s];
                 const uint32_t *Ar = &R->iv[2 * (size_t)dr[0]], *Fr = &R->iv[2 * (size_t)dr[2]];
                 const uint32_t *As = &S->iv[2 * (size_t)ds[0]], *Fs = &S->iv[2 * (size_t)ds[2]];
@@ -952,7 +964,8 @@ static april_status host_filter(const april_sets *R, const april_sets *S, const 
                     else if (join(Ar, dr[1], Fs, ds[3], &used)) v = APRIL_TRUE_HIT;
                     else if (join(Fr, dr[3], As, ds[1], &used)) v = APRIL_TRUE_HIT;
                     else v = APRIL_INCONCLUSIVE;
-                } else if (triage && host_triage_hit(R, S, r, s, lut, Ar, dr[1], Fr, dr[3], As, ds[1], Fs, ds[3], &used)) {
+                } else if (triage && gok && host_triage_hit(R, S, ro, so, gox, goy, glc, lut, Ar, dr[1], Fr, dr[3], As,
+                                                           ds[1], Fs, ds[3], &used)) {
                     v = APRIL_TRUE_HIT;  // settled by the triage (an AF or FA overlap)
                 } else if (triage) {  // the pairs the triage left: AA, AF, FA, as the kernels join them
                     if (!join(Ar, dr[1], As, ds[1], &used)) v = APRIL_TRUE_NEGATIVE;

@@ -416,16 +416,29 @@ __device__ __forceinline__ bool triage_cell(const int4 *__restrict__ mbr_r, cons
 
 // One thread per two pairs (k and k + 32 of its warp's 64): ids, probe cells,
 // then F(s) and, where it holds the cell, A(r); then F(r) and A(s) for the
-// pairs not settled yet.  Six CTAs per SM (at most 40 registers a thread):
-// the kernel waits on chains of dependent loads, and more threads hide more.
+// pairs not settled yet.  Over partitioned sets (PART, Sec. 5.2) the pairs'
+// entries come from the routing (er, es), the MBRs from the objects (pr, ps),
+// and the grid from the entry's partition.  Six CTAs per SM (at most 40
+// registers a thread): the kernel waits on chains of dependent loads, and
+// more threads hide more.
 #ifndef APRIL_TRIAGE_MIN_BLOCKS
 #define APRIL_TRIAGE_MIN_BLOCKS 6
 #endif
-__global__ void __launch_bounds__(256, APRIL_TRIAGE_MIN_BLOCKS) k_triage(RawSets R, RawSets S, const int4 *__restrict__ mbr_r,
-                                                const int4 *__restrict__ mbr_s, TriageGrid g, HilbertLut lut_in,
-                                                const uint32_t *__restrict__ pr, const uint32_t *__restrict__ ps,
-                                                uint64_t n, uint8_t *__restrict__ out, uint32_t *status,
-                                                uint32_t *rest, uint32_t *counters) {
+struct TriageArgs {
+    const int4 *mbr_r, *mbr_s;
+    TriageGrid g;                // one-grid sets
+    const int64_t *part_grid;    // PART: per partition {ox, oy, log2_cell, used}
+    const uint32_t *entry_pid;   // PART: R's entries' partitions
+    const uint32_t *er, *es;     // PART: the routed entries of the pairs
+};
+
+template <bool PART>
+__global__ void __launch_bounds__(256, APRIL_TRIAGE_MIN_BLOCKS) k_triage(RawSets R, RawSets S, TriageArgs ta,
+                                                                          HilbertLut lut_in,
+                                                                          const uint32_t *__restrict__ pr,
+                                                                          const uint32_t *__restrict__ ps, uint64_t n,
+                                                                          uint8_t *__restrict__ out, uint32_t *status,
+                                                                          uint32_t *rest, uint32_t *counters) {
     __shared__ uint8_t lut[64];
     if (threadIdx.x < 64) lut[threadIdx.x] = lut_in.e[threadIdx.x];
     __syncthreads();
@@ -441,12 +454,23 @@ __global__ void __launch_bounds__(256, APRIL_TRIAGE_MIN_BLOCKS) k_triage(RawSets
             valid[h] = false;
             dr[h] = ds[h] = make_uint4(0, 0, 0, 0);
             if (k[h] < n) {
-                const uint32_t r = __ldg(pr + k[h]), s = __ldg(ps + k[h]);
+                uint32_t r = __ldg(pr + k[h]), s = __ldg(ps + k[h]);  // objects
+                const uint32_t ro = r, so = s;
+                if constexpr (PART) {  // their entries (out of range when the routing found none)
+                    r = __ldg(ta.er + k[h]);
+                    s = __ldg(ta.es + k[h]);
+                }
                 if (r < R.n() && s < S.n()) {
                     valid[h] = true;
                     dr[h] = R.load(r);
                     ds[h] = S.load(s);
-                    probe[h] = triage_cell(mbr_r, mbr_s, g, lut, r, s, c[h]);
+                    if constexpr (PART) {
+                        const int64_t *pg = ta.part_grid + 4 * (size_t)__ldg(ta.entry_pid + r);
+                        const TriageGrid g{__ldg(pg), __ldg(pg + 1), (uint32_t)__ldg(pg + 2), ta.g.order};
+                        probe[h] = __ldg(pg + 3) != 0 && triage_cell(ta.mbr_r, ta.mbr_s, g, lut, ro, so, c[h]);
+                    } else {
+                        probe[h] = triage_cell(ta.mbr_r, ta.mbr_s, ta.g, lut, ro, so, c[h]);
+                    }
                 } else {
                     out[k[h]] = APRIL_VERDICT_ERROR;
                     atomicOr(status, ST_BAD_ID);
@@ -1148,11 +1172,14 @@ struct GraphKey {
     const void *r_mbr, *s_mbr;
     int64_t r_ox, r_oy, s_ox, s_oy;
     uint32_t r_log2, s_log2, r_grid, s_grid;
+    uint64_t r_gid, s_gid;
+    const void *r_pgrid;
     bool operator==(const GraphKey &o) const {
         return packed == o.packed && parts == o.parts && r_pdesc == o.r_pdesc && s_pdesc == o.s_pdesc &&
                r_mbr == o.r_mbr && s_mbr == o.s_mbr && r_ox == o.r_ox && r_oy == o.r_oy && s_ox == o.s_ox &&
                s_oy == o.s_oy && r_log2 == o.r_log2 && s_log2 == o.s_log2 && r_grid == o.r_grid &&
-               s_grid == o.s_grid && tune.triage_off == o.tune.triage_off &&
+               s_grid == o.s_grid && r_gid == o.r_gid && s_gid == o.s_gid && r_pgrid == o.r_pgrid &&
+               tune.triage_off == o.tune.triage_off &&
                r_desc == o.r_desc && r_iv == o.r_iv && s_desc == o.s_desc && s_iv == o.s_iv &&
                r_posts == o.r_posts && s_posts == o.s_posts && rn == o.rn &&
                sn == o.sn && d_r == o.d_r && d_s == o.d_s && out == o.out && scratch == o.scratch && n == o.n &&
@@ -1320,6 +1347,7 @@ extern "C" april_status april_upload(const april_sets *S, void *dev_buf, size_t 
     put(L.anchors, S->anchors.data(), S->anchors.size() * 4);
     put(L.gaps, S->gaps.data(), S->gaps.size());
     put(L.mbr, S->mbr.data(), S->mbr.size() * 4);
+    put(L.pgrid, S->part_grid.data(), S->part_grid.size() * 8);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(upload)");
     e = (cudaError_t)april_launch_posts((const uint32_t *)(base + L.iv), S->iv.size() / 2,
                                         (uint32_t *)(base + L.posts), stream);
@@ -1334,11 +1362,13 @@ extern "C" april_status april_upload(const april_sets *S, void *dev_buf, size_t 
     out->parts = S->parts;
     out->mbr = S->mbr.empty() ? nullptr : (const int32_t *)(base + L.mbr);
     out->posts = (const uint32_t *)(base + L.posts);
-    if (S->grid_known && !S->parts && !S->mbr.empty()) {
+    if (S->grid_known && !S->mbr.empty()) {
         out->grid_ox = S->grid_ox;
         out->grid_oy = S->grid_oy;
         out->grid_log2_cell = S->grid_log2_cell;
         out->grid_known = 1;
+        out->grid_id = S->grid_id;
+        if (S->parts) out->part_grid = (const int64_t *)(base + L.pgrid);
     }
     if (S->parts) {
         out->obj_ll = (const int32_t *)(base + L.obj_ll);
@@ -1409,17 +1439,28 @@ static inline PartView part_view(const april_dev_sets *d) {
 // tuning escalates long joins, K3b for the joins the lane groups handed over.
 // `esc_windows` overrides the tuning's escalate_windows (the allocation-free
 // entry point has no room for the queue and passes 0).
-// Whether the triage pass (K2) runs before the lane groups: raw sets on one
-// shared grid whose MBRs are known, and a tuning with every pair in lane
-// groups of 4..16 lanes.
+// Whether the triage pass (K2) runs before the lane groups: raw sets built
+// from polygons on the same grid(s) (equal fingerprints; for partitioned sets
+// the same partition grids), and a tuning with every pair in lane groups of
+// 4..16 lanes.
 static bool triage_applies(const april_tune &t, const april_dev_sets *R, const april_dev_sets *S, bool packed) {
-    return !t.triage_off && t.cta_threshold == kNoLongPairs && t.group_lanes < 32 && !packed && !R->parts &&
-           R->grid_known && S->grid_known && R->mbr && S->mbr && R->order == S->order && R->grid_ox == S->grid_ox &&
-           R->grid_oy == S->grid_oy && R->grid_log2_cell == S->grid_log2_cell;
+    if (t.triage_off || t.cta_threshold != kNoLongPairs || t.group_lanes >= 32 || packed) return false;
+    if (!R->grid_known || !S->grid_known || !R->mbr || !S->mbr || R->order != S->order || R->grid_id != S->grid_id)
+        return false;
+    return !R->parts || (R->part_grid && R->entry_pid);
 }
 
-static TriageGrid triage_grid(const april_dev_sets *R) {
-    return TriageGrid{R->grid_ox, R->grid_oy, R->grid_log2_cell, R->order};
+static TriageArgs triage_args(const april_dev_sets *R, const april_dev_sets *S, const uint32_t *er,
+                              const uint32_t *es) {
+    TriageArgs a{};
+    a.mbr_r = (const int4 *)R->mbr;
+    a.mbr_s = (const int4 *)S->mbr;
+    a.g = TriageGrid{R->grid_ox, R->grid_oy, R->grid_log2_cell, R->order};
+    a.part_grid = R->part_grid;
+    a.entry_pid = R->entry_pid;
+    a.er = er;
+    a.es = es;
+    return a;
 }
 
 static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, const april_dev_sets *Sd,
@@ -1437,6 +1478,7 @@ static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, con
     const unsigned grid_long = (unsigned)std::max(1, ctx->num_sms * ctx->long_blocks_per_sm);
     cudaError_t e = cudaMemsetAsync(counters, 0, kCounterBytes, st);
     if (e != cudaSuccess) return e;
+    const uint32_t *obj_r = d_r, *obj_s = d_s;  // the pairs' objects (their MBRs)
     if (Rd->parts) {
         uint32_t *er = (uint32_t *)((char *)scratch + kCounterBytes + round256(4 * n));
         uint32_t *es = (uint32_t *)((char *)scratch + kCounterBytes + 2 * round256(4 * n));
@@ -1469,8 +1511,12 @@ static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, con
     const RawSets R{dev_set(Rd)}, S{dev_set(Sd)};
     const uint32_t *rest = nullptr;  // the pairs the lane groups join (nullptr: all)
     if (triage_applies(t, Rd, Sd, false)) {
-        k_triage<<<grid_bin, 256, 0, st>>>(R, S, (const int4 *)Rd->mbr, (const int4 *)Sd->mbr, triage_grid(Rd),
-                                           triage_lut(), d_r, d_s, n, out, status, big_list, counters);
+        if (Rd->parts)
+            k_triage<true><<<grid_bin, 256, 0, st>>>(R, S, triage_args(Rd, Sd, d_r, d_s), triage_lut(), obj_r, obj_s,
+                                                     n, out, status, big_list, counters);
+        else
+            k_triage<false><<<grid_bin, 256, 0, st>>>(R, S, triage_args(Rd, Sd, nullptr, nullptr), triage_lut(), d_r,
+                                                      d_s, n, out, status, big_list, counters);
         rest = big_list;
     } else if (t.cta_threshold != kNoLongPairs) {
         k_bin<<<grid_bin, 256, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold, big_list, counters);
@@ -1507,7 +1553,8 @@ static april_status launch_batched(april_ctx *ctx, const april_dev_sets *R, cons
                  R->n_objects,    S->n_objects,   d_r,              d_s,            out,            scratch,
                  n,               ctx->tune,      grid_bin,         grid_main,      packed,         R->parts,
                  R->pdesc,        S->pdesc,       R->mbr,           S->mbr,         R->grid_ox,     R->grid_oy,
-                 S->grid_ox,      S->grid_oy,     R->grid_log2_cell, S->grid_log2_cell, R->grid_known, S->grid_known};
+                 S->grid_ox,      S->grid_oy,     R->grid_log2_cell, S->grid_log2_cell, R->grid_known, S->grid_known,
+                 R->grid_id,      S->grid_id,     R->part_grid};
     cudaError_t e;
     if (!ctx->graph || !(key == ctx->key)) {
         if (ctx->graph) {
@@ -2023,8 +2070,8 @@ extern "C" april_status april_filter_pairs_noalloc(const april_dev_sets *R, cons
     const unsigned grid_main = (unsigned)std::max(1, nd.num_sms * nd.blocks_per_sm);
     const uint32_t *rest = nullptr;
     if (triage_applies(t, R, S, false)) {
-        k_triage<<<grid_bin, 256, 0, st>>>(dR, dS, (const int4 *)R->mbr, (const int4 *)S->mbr, triage_grid(R),
-                                           triage_lut(), d_r, d_s, n, d_verdict, status, big_list, counters);
+        k_triage<false><<<grid_bin, 256, 0, st>>>(dR, dS, triage_args(R, S, nullptr, nullptr), triage_lut(), d_r, d_s,
+                                                  n, d_verdict, status, big_list, counters);
         rest = big_list;
     } else if (t.cta_threshold != kNoLongPairs) {
         k_bin<<<grid_bin, 256, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, status, t.cta_threshold, big_list, counters);

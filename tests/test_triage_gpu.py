@@ -79,3 +79,34 @@ def test_triage_on_gpu_built_sets(torch_cuda, ctx):
     pr, ps = np.array(w.pr, dtype=np.uint32), np.array(w.ps, dtype=np.uint32)
     want, _ = A.april_host_filter(Rh, S, pr, ps)
     assert np.array_equal(_run(torch, ctx, dR, dS, pr, ps, 0), want)
+
+
+def test_triage_on_partitioned_sets(torch_cuda, ctx):
+    """Partitioned sets (Sec. 5.2): each pair's probe cell is taken on the grid
+    of the partition the routing picks, and looked up in the entries' lists."""
+    w = _data.workload(4, 0.05)
+    R, S = A.april_build_partitioned_sets(w.R.xy, w.R.off, w.S.xy, w.S.off, w.partitions, w.order)
+    dR, dS = A.april_upload(R), A.april_upload(S)
+    assert dR.c.grid_known == 1 and dR.c.grid_id == dS.c.grid_id and dR.c.part_grid
+    pr, ps = np.array(w.pr, dtype=np.uint32), np.array(w.ps, dtype=np.uint32)
+    pr[::1009] = 0xFFFFFFF0
+    want, _ = A.april_host_filter(R, S, pr, ps)
+    assert np.array_equal(_run(torch_cuda, ctx, dR, dS, pr, ps, 1), want)
+    bad = np.flatnonzero(_run(torch_cuda, ctx, dR, dS, pr, ps, 0) != want)
+    assert len(bad) == 0, (len(bad), bad[:10])
+
+
+def test_no_triage_across_different_grids(torch_cuda, ctx):
+    """Sets on grids of the same order but other origins have different
+    fingerprints, so the triage stays off (a cell id means another cell on
+    each side) and the verdicts are host Algorithm 2's over the given lists."""
+    w = _data.workload(1, 1.0)
+    R = A.april_build_sets(w.R.xy, w.R.off, A.global_grid(w.order))
+    g2 = A.global_grid(w.order)
+    g2.ox -= 1 << g2.log2_cell
+    S = A.april_build_sets(w.S.xy, w.S.off, g2)
+    dR, dS = A.april_upload(R), A.april_upload(S)
+    assert dR.c.grid_id != dS.c.grid_id
+    pr, ps = np.array(w.pr, dtype=np.uint32), np.array(w.ps, dtype=np.uint32)
+    want, _ = A.april_host_filter(R, S, pr, ps)
+    assert np.array_equal(_run(torch_cuda, ctx, dR, dS, pr, ps, 0), want)
