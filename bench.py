@@ -119,9 +119,9 @@ def tune_key(t):
 
 def triage_applies(tune, partitions, mode) -> bool:
     """Whether the batched filter runs its triage kernel (include/april.h,
-    april_tune.triage_off): raw sets built from polygons (one grid or
-    partitioned), no long-pair threshold, lane groups below 32."""
-    return (mode == "batched" and tune is not None and not tune.get("triage_off", 0)
+    april_tune.triage_off): sets built from polygons (one grid or partitioned,
+    raw or compressed), no long-pair threshold, lane groups below 32."""
+    return (mode in ("batched", "packed") and tune is not None and not tune.get("triage_off", 0)
             and tune["cta_threshold"] == 0xFFFFFFFF and tune["group_lanes"] < 32)
 
 

@@ -399,6 +399,62 @@ __device__ __forceinline__ void holds2(const RawList &L0, uint32_t c0, bool on0,
     h1 = r1 && s1 <= c1;
 }
 
+// Whether compressed list L (Sec. 5.1 blocks of 32 endpoints: an anchor and
+// 31 gaps) holds cell c: the last block whose anchor (the start of its first
+// interval) is at most c, by binary search over the block table (an earlier
+// block's intervals end before that anchor, a later block's start after c),
+// then its endpoints decoded from 16-byte loads of the gaps.
+__device__ __forceinline__ bool holds_packed(const PackedList &L, uint32_t c) {
+    const uint32_t n = L.n;
+    if (!n) return false;
+    uint32_t lo = 0, hi = (2 * n + 31) / 32;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(&L.blocks[mid].x) <= c) lo = mid + 1;
+        else hi = mid;
+    }
+    if (!lo) return false;
+    const uint32_t b = lo - 1;
+    const uint2 meta = __ldg(L.blocks + b);
+    const uint32_t ne = min(32u, 2 * n - 32 * b);  // endpoints in this block
+    const uint4 *gw = (const uint4 *)(L.gaps + 64ull * (meta.y & 0x7FFFFFFFu));
+    const bool wide = meta.y >> 31;
+    uint32_t e = meta.x, st = 0;  // endpoint j, and the start of the open interval
+    bool held = false;
+#pragma unroll
+    for (uint32_t w = 0; w < 8; ++w) {  // 16-byte words: 8 of 32-bit gaps or 4 of 16-bit gaps
+        if (!wide && w >= 4) break;
+        const uint4 q = __ldg(gw + w);
+        const uint32_t per = wide ? 4u : 8u;
+#pragma unroll
+        for (uint32_t i = 0; i < 8; ++i) {
+            if (i >= per) break;
+            const uint32_t j = w * per + i;  // gap slot j gives endpoint j (slot 0: the anchor itself)
+            const uint32_t word = i < 4 || !wide ? (i >> (wide ? 0 : 1)) : 0u;
+            const uint32_t raw = word == 0 ? q.x : word == 1 ? q.y : word == 2 ? q.z : q.w;
+            const uint32_t gap = wide ? raw : (i & 1u ? raw >> 16 : raw & 0xFFFFu);
+            if (j > 0) e += gap;
+            if (j < ne) {
+                if (!(j & 1u)) st = e;
+                else held = held || (st <= c && c <= e - 1u);
+            }
+        }
+    }
+    return held;
+}
+
+// The lookups of two pairs' cells: raw lists in lockstep (holds2),
+// compressed lists one after the other.
+__device__ __forceinline__ void lookup2(const RawList &L0, uint32_t c0, bool on0, const RawList &L1, uint32_t c1,
+                                        bool on1, bool &h0, bool &h1) {
+    holds2(L0, c0, on0, L1, c1, on1, h0, h1);
+}
+__device__ __forceinline__ void lookup2(const PackedList &L0, uint32_t c0, bool on0, const PackedList &L1, uint32_t c1,
+                                        bool on1, bool &h0, bool &h1) {
+    h0 = on0 && holds_packed(L0, c0);
+    h1 = on1 && holds_packed(L1, c1);
+}
+
 // The probe cell of pair (r, s): the cell under the centre of
 // MBR(r) n MBR(s); false when the MBRs are disjoint or the centre is off the grid.
 __device__ __forceinline__ bool triage_cell(const int4 *__restrict__ mbr_r, const int4 *__restrict__ mbr_s,
@@ -432,8 +488,8 @@ struct TriageArgs {
     const uint32_t *er, *es;     // PART: the routed entries of the pairs
 };
 
-template <bool PART>
-__global__ void __launch_bounds__(256, APRIL_TRIAGE_MIN_BLOCKS) k_triage(RawSets R, RawSets S, TriageArgs ta,
+template <bool PART, class SetsT>
+__global__ void __launch_bounds__(256, APRIL_TRIAGE_MIN_BLOCKS) k_triage(SetsT R, SetsT S, TriageArgs ta,
                                                                           HilbertLut lut_in,
                                                                           const uint32_t *__restrict__ pr,
                                                                           const uint32_t *__restrict__ ps, uint64_t n,
@@ -478,12 +534,12 @@ __global__ void __launch_bounds__(256, APRIL_TRIAGE_MIN_BLOCKS) k_triage(RawSets
             }
         }
         bool f0, f1;
-        holds2(S.list(ds[0], true), c[0], probe[0], S.list(ds[1], true), c[1], probe[1], f0, f1);  // F(s)
-        holds2(R.list(dr[0], false), c[0], f0, R.list(dr[1], false), c[1], f1, hit[0], hit[1]);    // A(r)
-        holds2(R.list(dr[0], true), c[0], probe[0] && !hit[0], R.list(dr[1], true), c[1], probe[1] && !hit[1], f0,
-               f1);                                                                                   // F(r)
+        lookup2(S.list(ds[0], true), c[0], probe[0], S.list(ds[1], true), c[1], probe[1], f0, f1);  // F(s)
+        lookup2(R.list(dr[0], false), c[0], f0, R.list(dr[1], false), c[1], f1, hit[0], hit[1]);    // A(r)
+        lookup2(R.list(dr[0], true), c[0], probe[0] && !hit[0], R.list(dr[1], true), c[1], probe[1] && !hit[1], f0,
+                f1);                                                                                   // F(r)
         bool g0, g1;
-        holds2(S.list(ds[0], false), c[0], f0, S.list(ds[1], false), c[1], f1, g0, g1);            // A(s)
+        lookup2(S.list(ds[0], false), c[0], f0, S.list(ds[1], false), c[1], f1, g0, g1);            // A(s)
         hit[0] = hit[0] || g0;
         hit[1] = hit[1] || g1;
 #pragma unroll
@@ -1444,7 +1500,8 @@ static inline PartView part_view(const april_dev_sets *d) {
 // the same partition grids), and a tuning with every pair in lane groups of
 // 4..16 lanes.
 static bool triage_applies(const april_tune &t, const april_dev_sets *R, const april_dev_sets *S, bool packed) {
-    if (t.triage_off || t.cta_threshold != kNoLongPairs || t.group_lanes >= 32 || packed) return false;
+    if (t.triage_off || t.cta_threshold != kNoLongPairs || t.group_lanes >= 32) return false;
+    if (packed && (!R->pdesc || !S->pdesc)) return false;
     if (!R->grid_known || !S->grid_known || !R->mbr || !S->mbr || R->order != S->order || R->grid_id != S->grid_id)
         return false;
     return !R->parts || (R->part_grid && R->entry_pid);
@@ -1490,13 +1547,24 @@ static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, con
     }
     if (packed) {
         const PackedSets R = packed_set(Rd), S = packed_set(Sd);
-        const uint32_t jo = join_order_of(t.join_order, false);
-        if (t.cta_threshold != kNoLongPairs)
+        const uint32_t *prest = nullptr;
+        if (triage_applies(t, Rd, Sd, true)) {
+            if (Rd->parts)
+                k_triage<true, PackedSets><<<grid_bin, 256, 0, st>>>(R, S, triage_args(Rd, Sd, d_r, d_s), triage_lut(),
+                                                                     obj_r, obj_s, n, out, status, big_list, counters);
+            else
+                k_triage<false, PackedSets><<<grid_bin, 256, 0, st>>>(R, S, triage_args(Rd, Sd, nullptr, nullptr),
+                                                                      triage_lut(), d_r, d_s, n, out, status, big_list,
+                                                                      counters);
+            prest = big_list;
+        } else if (t.cta_threshold != kNoLongPairs) {
             k_bin<<<grid_bin, 256, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold, big_list, counters);
+        }
+        const uint32_t jo = join_order_of(t.join_order, prest != nullptr);
 #define APRIL_LAUNCH_PACKED(G)                                                                                  \
     k_persistent<G, PackedSets><<<grid_main, kBlock, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold,   \
                                                               big_list, counters, t.group_window, t.cta_window,   \
-                                                              jo, escw, esc, esc_cap, nullptr)
+                                                              jo, escw, esc, esc_cap, prest)
         switch (t.group_lanes) {
             case 4: APRIL_LAUNCH_PACKED(4); break;
             case 8: APRIL_LAUNCH_PACKED(8); break;
@@ -1512,11 +1580,11 @@ static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, con
     const uint32_t *rest = nullptr;  // the pairs the lane groups join (nullptr: all)
     if (triage_applies(t, Rd, Sd, false)) {
         if (Rd->parts)
-            k_triage<true><<<grid_bin, 256, 0, st>>>(R, S, triage_args(Rd, Sd, d_r, d_s), triage_lut(), obj_r, obj_s,
-                                                     n, out, status, big_list, counters);
+            k_triage<true, RawSets><<<grid_bin, 256, 0, st>>>(R, S, triage_args(Rd, Sd, d_r, d_s), triage_lut(), obj_r,
+                                                              obj_s, n, out, status, big_list, counters);
         else
-            k_triage<false><<<grid_bin, 256, 0, st>>>(R, S, triage_args(Rd, Sd, nullptr, nullptr), triage_lut(), d_r,
-                                                      d_s, n, out, status, big_list, counters);
+            k_triage<false, RawSets><<<grid_bin, 256, 0, st>>>(R, S, triage_args(Rd, Sd, nullptr, nullptr), triage_lut(),
+                                                               d_r, d_s, n, out, status, big_list, counters);
         rest = big_list;
     } else if (t.cta_threshold != kNoLongPairs) {
         k_bin<<<grid_bin, 256, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold, big_list, counters);
@@ -2070,8 +2138,8 @@ extern "C" april_status april_filter_pairs_noalloc(const april_dev_sets *R, cons
     const unsigned grid_main = (unsigned)std::max(1, nd.num_sms * nd.blocks_per_sm);
     const uint32_t *rest = nullptr;
     if (triage_applies(t, R, S, false)) {
-        k_triage<false><<<grid_bin, 256, 0, st>>>(dR, dS, triage_args(R, S, nullptr, nullptr), triage_lut(), d_r, d_s,
-                                                  n, d_verdict, status, big_list, counters);
+        k_triage<false, RawSets><<<grid_bin, 256, 0, st>>>(dR, dS, triage_args(R, S, nullptr, nullptr), triage_lut(),
+                                                           d_r, d_s, n, d_verdict, status, big_list, counters);
         rest = big_list;
     } else if (t.cta_threshold != kNoLongPairs) {
         k_bin<<<grid_bin, 256, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, status, t.cta_threshold, big_list, counters);

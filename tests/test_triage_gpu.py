@@ -26,7 +26,7 @@ def ctx(torch_cuda):
     return A.Context(0)
 
 
-def _run(torch, ctx, dR, dS, pr, ps, triage_off):
+def _run(torch, ctx, dR, dS, pr, ps, triage_off, mode=A.MODE_BATCHED):
     n = len(pr)
     saved = ctx.get_tune()
     t = A.april_tune(0xFFFFFFFF, 4, 32, 128, 0, 0.0, 0, 0, triage_off)
@@ -35,8 +35,8 @@ def _run(torch, ctx, dR, dS, pr, ps, triage_off):
         d_r = torch.from_numpy(pr.view(np.int32)).cuda()
         d_s = torch.from_numpy(ps.view(np.int32)).cuda()
         out = torch.full((n,), 0xEE, dtype=torch.uint8, device="cuda")
-        scratch = torch.empty(ctx.scratch_bytes(A.MODE_BATCHED, n), dtype=torch.uint8, device="cuda")
-        ctx.april_filter_pairs(dR, dS, d_r, d_s, n, out, A.MODE_BATCHED, scratch)
+        scratch = torch.empty(ctx.scratch_bytes(mode, n), dtype=torch.uint8, device="cuda")
+        ctx.april_filter_pairs(dR, dS, d_r, d_s, n, out, mode, scratch)
         try:
             ctx.april_sync_status()
         except A.AprilError as e:
@@ -46,19 +46,26 @@ def _run(torch, ctx, dR, dS, pr, ps, triage_off):
         ctx.set_tune(saved)
 
 
+@pytest.mark.parametrize("packed", [False, True])
 @pytest.mark.parametrize("cfg,scale", [(1, 1.0), (2, 0.05), (3, 0.02)])
-def test_triage_keeps_the_verdicts(torch_cuda, ctx, cfg, scale):
+def test_triage_keeps_the_verdicts(torch_cuda, ctx, cfg, scale, packed):
     w = _data.workload(cfg, scale)
     g = A.global_grid(w.order)
     R = A.april_build_sets(w.R.xy, w.R.off, g)
     S = A.april_build_sets(w.S.xy, w.S.off, g)
+    want_sets = (A.april_build_sets(w.R.xy, w.R.off, g), A.april_build_sets(w.S.xy, w.S.off, g))
+    mode = A.MODE_BATCHED
+    if packed:
+        R.compress()
+        S.compress()
+        mode = A.MODE_BATCHED_PACKED
     dR, dS = A.april_upload(R), A.april_upload(S)
     assert dR.c.grid_known == 1 and dS.c.grid_known == 1
     pr, ps = np.array(w.pr, dtype=np.uint32), np.array(w.ps, dtype=np.uint32)
     pr[::997] = 0xFFFFFFF0  # bad ids: error verdicts either way
-    want, _ = A.april_host_filter(R, S, pr, ps)
-    on = _run(torch_cuda, ctx, dR, dS, pr, ps, 0)
-    off = _run(torch_cuda, ctx, dR, dS, pr, ps, 1)
+    want, _ = A.april_host_filter(*want_sets, pr, ps)
+    on = _run(torch_cuda, ctx, dR, dS, pr, ps, 0, mode)
+    off = _run(torch_cuda, ctx, dR, dS, pr, ps, 1, mode)
     assert np.array_equal(off, want)
     bad = np.flatnonzero(on != want)
     assert len(bad) == 0, (len(bad), bad[:10])
@@ -81,18 +88,25 @@ def test_triage_on_gpu_built_sets(torch_cuda, ctx):
     assert np.array_equal(_run(torch, ctx, dR, dS, pr, ps, 0), want)
 
 
-def test_triage_on_partitioned_sets(torch_cuda, ctx):
+@pytest.mark.parametrize("packed", [False, True])
+def test_triage_on_partitioned_sets(torch_cuda, ctx, packed):
     """Partitioned sets (Sec. 5.2): each pair's probe cell is taken on the grid
-    of the partition the routing picks, and looked up in the entries' lists."""
+    of the partition the routing picks, and looked up in the entries' lists,
+    raw or compressed (Sec. 5.1)."""
     w = _data.workload(4, 0.05)
     R, S = A.april_build_partitioned_sets(w.R.xy, w.R.off, w.S.xy, w.S.off, w.partitions, w.order)
+    mode = A.MODE_BATCHED
+    if packed:
+        R.compress()
+        S.compress()
+        mode = A.MODE_BATCHED_PACKED
     dR, dS = A.april_upload(R), A.april_upload(S)
     assert dR.c.grid_known == 1 and dR.c.grid_id == dS.c.grid_id and dR.c.part_grid
     pr, ps = np.array(w.pr, dtype=np.uint32), np.array(w.ps, dtype=np.uint32)
     pr[::1009] = 0xFFFFFFF0
     want, _ = A.april_host_filter(R, S, pr, ps)
-    assert np.array_equal(_run(torch_cuda, ctx, dR, dS, pr, ps, 1), want)
-    bad = np.flatnonzero(_run(torch_cuda, ctx, dR, dS, pr, ps, 0) != want)
+    assert np.array_equal(_run(torch_cuda, ctx, dR, dS, pr, ps, 1, mode), want)
+    bad = np.flatnonzero(_run(torch_cuda, ctx, dR, dS, pr, ps, 0, mode) != want)
     assert len(bad) == 0, (len(bad), bad[:10])
 
 
