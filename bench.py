@@ -125,6 +125,20 @@ def triage_applies(tune, partitions, mode) -> bool:
             and tune["cta_threshold"] == 0xFFFFFFFF and tune["group_lanes"] < 32)
 
 
+def launches_per_step(tune, partitions, mode) -> int:
+    """This library's kernels in one filter step: the partition routing, then
+    the triage or the length binning (or neither), the persistent kernel and,
+    with escalation, the kernel that finishes the handed-over joins."""
+    if mode not in ("batched", "packed"):
+        return 1
+    n = 1 + (1 if partitions else 0)
+    if triage_applies(tune, partitions, mode) or tune["cta_threshold"] != 0xFFFFFFFF:
+        n += 1
+    if tune.get("escalate_windows", 0) and tune["group_lanes"] < 32:
+        n += 1
+    return n
+
+
 def kernel_traffic(kernel: str, workload: str, mode: str, tune):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
     the current kernel sources for the same workload, mode and tuning."""
@@ -886,7 +900,8 @@ def main():
                                    "verdicts gathered to rank 0 after the timed region") if ws > 1 else "single GPU"},
         "roofline": roof,
         "e2e": head["e2e"],
-        "gpu_launches": (2 if mode in ("batched", "packed") else 1) * args.steps,
+        "gpu_launches": launches_per_step(head.get("tune") or ctx.get_tune().as_dict(), L.w.partitions,
+                                          mode) * args.steps,
         "clocks": clk,
     }
     for k, v in head.items():
