@@ -399,40 +399,22 @@ __device__ __forceinline__ void holds2(const RawList &L0, uint32_t c0, bool on0,
     h1 = r1 && s1 <= c1;
 }
 
-// Whether compressed list L (Sec. 5.1 blocks of 32 endpoints: an anchor and
-// 31 gaps) holds cell c: the last block whose anchor (the start of its first
-// interval) is at most c, by binary search over the block table (an earlier
-// block's intervals end before that anchor, a later block's start after c),
-// then its endpoints decoded from 16-byte loads of the gaps.
-__device__ __forceinline__ bool holds_packed(const PackedList &L, uint32_t c) {
-    const uint32_t n = L.n;
-    if (!n) return false;
-    uint32_t lo = 0, hi = (2 * n + 31) / 32;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (__ldg(&L.blocks[mid].x) <= c) lo = mid + 1;
-        else hi = mid;
-    }
-    if (!lo) return false;
-    const uint32_t b = lo - 1;
-    const uint2 meta = __ldg(L.blocks + b);
-    const uint32_t ne = min(32u, 2 * n - 32 * b);  // endpoints in this block
-    const uint4 *gw = (const uint4 *)(L.gaps + 64ull * (meta.y & 0x7FFFFFFFu));
-    const bool wide = meta.y >> 31;
-    uint32_t e = meta.x, st = 0;  // endpoint j, and the start of the open interval
+// Whether the decoded block of compressed list L that starts at endpoint
+// 32 b holds cell c: the block's endpoints (its anchor, then 31 gaps read
+// with 16-byte loads, 16-bit or 32-bit) taken as [start, end) pairs.
+template <bool WIDE>
+__device__ __forceinline__ bool block_holds(const uint4 *gw, uint32_t anchor, uint32_t ne, uint32_t c) {
+    constexpr uint32_t PER = WIDE ? 4u : 8u, WORDS = 32u / PER;
+    uint32_t e = anchor, st = 0;
     bool held = false;
 #pragma unroll
-    for (uint32_t w = 0; w < 8; ++w) {  // 16-byte words: 8 of 32-bit gaps or 4 of 16-bit gaps
-        if (!wide && w >= 4) break;
+    for (uint32_t w = 0; w < WORDS; ++w) {
         const uint4 q = __ldg(gw + w);
-        const uint32_t per = wide ? 4u : 8u;
+        const uint32_t v[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-        for (uint32_t i = 0; i < 8; ++i) {
-            if (i >= per) break;
-            const uint32_t j = w * per + i;  // gap slot j gives endpoint j (slot 0: the anchor itself)
-            const uint32_t word = i < 4 || !wide ? (i >> (wide ? 0 : 1)) : 0u;
-            const uint32_t raw = word == 0 ? q.x : word == 1 ? q.y : word == 2 ? q.z : q.w;
-            const uint32_t gap = wide ? raw : (i & 1u ? raw >> 16 : raw & 0xFFFFu);
+        for (uint32_t i = 0; i < PER; ++i) {
+            const uint32_t j = w * PER + i;  // slot j gives endpoint j (slot 0: the anchor itself)
+            const uint32_t gap = WIDE ? v[i] : (i & 1u ? v[i >> 1] >> 16 : v[i >> 1] & 0xFFFFu);
             if (j > 0) e += gap;
             if (j < ne) {
                 if (!(j & 1u)) st = e;
@@ -443,16 +425,56 @@ __device__ __forceinline__ bool holds_packed(const PackedList &L, uint32_t c) {
     return held;
 }
 
-// The lookups of two pairs' cells: raw lists in lockstep (holds2),
-// compressed lists one after the other.
+// Whether compressed lists L0 and L1 (Sec. 5.1 blocks of 32 endpoints: an
+// anchor and 31 gaps) hold cells c0 and c1 (for two pairs a thread handles
+// at once), each only where `on`: the last block whose anchor (the start of
+// its first interval) is at most c, by binary searches over the block tables
+// in lockstep (an earlier block's intervals end before that anchor, a later
+// block's start after c), then that block decoded.
+__device__ __forceinline__ void holds2_packed(const PackedList &L0, uint32_t c0, bool on0, const PackedList &L1,
+                                              uint32_t c1, bool on1, bool &h0, bool &h1) {
+    on0 = on0 && L0.n;
+    on1 = on1 && L1.n;
+    uint32_t lo0 = 0, hi0 = on0 ? (2 * L0.n + 31) / 32 : 0u, lo1 = 0, hi1 = on1 ? (2 * L1.n + 31) / 32 : 0u;
+    while (lo0 < hi0 || lo1 < hi1) {
+        const bool a0 = lo0 < hi0, a1 = lo1 < hi1;
+        const uint32_t m0 = (lo0 + hi0) >> 1, m1 = (lo1 + hi1) >> 1;
+        const uint32_t k0 = a0 ? __ldg(&L0.blocks[m0].x) : 0u, k1 = a1 ? __ldg(&L1.blocks[m1].x) : 0u;
+        if (a0) {
+            if (k0 <= c0) lo0 = m0 + 1;
+            else hi0 = m0;
+        }
+        if (a1) {
+            if (k1 <= c1) lo1 = m1 + 1;
+            else hi1 = m1;
+        }
+    }
+    on0 = on0 && lo0 > 0;
+    on1 = on1 && lo1 > 0;
+    const uint2 m0 = on0 ? __ldg(L0.blocks + lo0 - 1) : make_uint2(0, 0);
+    const uint2 m1 = on1 ? __ldg(L1.blocks + lo1 - 1) : make_uint2(0, 0);
+    h0 = h1 = false;
+    if (on0) {
+        const uint4 *gw = (const uint4 *)(L0.gaps + 64ull * (m0.y & 0x7FFFFFFFu));
+        const uint32_t ne = min(32u, 2 * L0.n - 32 * (lo0 - 1));
+        h0 = m0.y >> 31 ? block_holds<true>(gw, m0.x, ne, c0) : block_holds<false>(gw, m0.x, ne, c0);
+    }
+    if (on1) {
+        const uint4 *gw = (const uint4 *)(L1.gaps + 64ull * (m1.y & 0x7FFFFFFFu));
+        const uint32_t ne = min(32u, 2 * L1.n - 32 * (lo1 - 1));
+        h1 = m1.y >> 31 ? block_holds<true>(gw, m1.x, ne, c1) : block_holds<false>(gw, m1.x, ne, c1);
+    }
+}
+
+// The lookups of two pairs' cells, in lockstep: raw lists (holds2),
+// compressed lists (holds2_packed).
 __device__ __forceinline__ void lookup2(const RawList &L0, uint32_t c0, bool on0, const RawList &L1, uint32_t c1,
                                         bool on1, bool &h0, bool &h1) {
     holds2(L0, c0, on0, L1, c1, on1, h0, h1);
 }
 __device__ __forceinline__ void lookup2(const PackedList &L0, uint32_t c0, bool on0, const PackedList &L1, uint32_t c1,
                                         bool on1, bool &h0, bool &h1) {
-    h0 = on0 && holds_packed(L0, c0);
-    h1 = on1 && holds_packed(L1, c1);
+    holds2_packed(L0, c0, on0, L1, c1, on1, h0, h1);
 }
 
 // The probe cell of pair (r, s): the cell under the centre of
