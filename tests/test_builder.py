@@ -131,6 +131,20 @@ def test_searched_host_filter(cfg, scale):
     assert c1.sum() < c0.sum()
 
 
+def test_searched_host_filter_partitioned():
+    """The kernels' reading over partitioned sets (Sec. 5.2): the triage takes
+    each pair's probe cell on the grid of the partition the routing picks; the
+    verdicts stay Algorithm 2's, and the searched reading reads less than
+    sequential Algorithm 2."""
+    from tests import _data
+    w = _data.workload(4, 0.02)
+    R, S = A.april_build_partitioned_sets(w.R.xy, w.R.off, w.S.xy, w.S.off, w.partitions, w.order)
+    v0, c0 = A.april_host_filter(R, S, w.pr, w.ps)
+    v1, c1 = A.april_host_filter(R, S, w.pr, w.ps, searched=True)
+    assert np.array_equal(v0, v1)
+    assert c1.sum() < c0.sum()
+
+
 def test_quantize_polygons():
     """Reading C3: x -> nearest integer of x * 2^24 (ties to even), clamped to
     [0, 2^24], consecutive and closing duplicates dropped; checked against
