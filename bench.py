@@ -105,10 +105,16 @@ def peaks():
 
 
 def kernel_source_sha() -> str:
-    """Hash of the kernel sources a profile was taken on."""
+    """Hash of the kernel sources a profile was taken on: filter.cu and
+    join_device.cuh with their comments and whitespace removed, so that a
+    comment edit keeps the profiles' DRAM figures attached."""
+    import re
     h = hashlib.sha256()
     for f in ("filter.cu", "join_device.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2307_01716_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_2307_01716_gb300", "csrc", f), encoding="utf-8").read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 
