@@ -582,16 +582,19 @@ __global__ void __launch_bounds__(256, APRIL_TRIAGE_MIN_BLOCKS) k_triage(SetsT R
 
 // ------------------------------------------ K3: persistent filter (batched)
 // Group engine.  A warp is split into 32/G groups of G lanes; each group
-// filters one pair at a time (its three joins in Algorithm 2's order), with
-// its own window of at most 8*G intervals per list staged in shared memory.
+// filters one pair at a time (its joins in the tuned order, see
+// step_outcome), with its own window of at most 8*G intervals per list
+// staged in shared memory.
 // One pass of the loop below advances every group's current join by one
 // window, so the fixed cost of a window step (staging, the per-thread merge-
 // path search, the vote) is shared by 32/G joins.  When a group finishes its
 // pair it takes the next one from the warp's current chunk of 32 pairs, whose
 // eligible pairs are listed compacted in shared memory (a group takes the
 // entry at the list's cursor plus its rank among the groups asking); the warp
-// pops a new chunk from a global counter when the list is used up.  Pairs above the
-// CTA threshold are skipped here (phase 1 did them).
+// pops a new chunk from a global counter when the list is used up.  The
+// pairs are all n, or, after the triage (K2), the ones it listed.  Pairs
+// above a CTA threshold, when one is set, are skipped here (phase 1 did
+// them).
 template <uint32_t G>
 struct GroupCfg {
     static constexpr uint32_t NG = 32 / G;
@@ -927,9 +930,10 @@ __device__ __forceinline__ void group_engine(const SetsT &R, const SetsT &S, con
     }
 }
 
-// Phase 1: the long pairs, each joined by one warp (first window below 256)
-// or by the whole CTA (the merge path of one join split over 256 threads).
-// Phase 2: the group engine on the short pairs (whole warps when G = 32).
+// Phase 1 (only with a long-pair threshold): the long pairs, each joined by
+// one warp (first window below 256) or by the whole CTA (the merge path of one
+// join split over 256 threads).  Phase 2: the group engine on the other pairs
+// (whole warps when G = 32), or on the pairs the triage left.
 // Work is handed out by atomic counters; nothing waits on another CTA.
 template <uint32_t G, class SetsT>
 __global__ void APRIL_PERSISTENT_BOUNDS k_persistent(SetsT R, SetsT S,
