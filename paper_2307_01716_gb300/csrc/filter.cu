@@ -335,9 +335,11 @@ __global__ void __launch_bounds__(256) k_bin(SetsT R, SetsT S, const uint32_t *_
 // overlap and Algorithm 2's verdict is a true hit (Sec. 4.2: an AF or FA
 // overlap implies the AA one, so the verdict is the same in any join order).
 // The pairs the probe does not settle are listed, with warp-aggregated
-// appends, for the lane groups; out-of-range ids get error verdicts.  One
-// thread per pair.  A lookup is a binary search over the list's skip index
-// (posts below c), then over the at most 16 intervals that follow.
+// appends, for the lane groups; out-of-range ids get error verdicts.  A
+// thread takes two pairs at once (k_triage).  A lookup is a binary search
+// over the list's skip index (posts below c), then over the at most 16
+// intervals that follow; over compressed lists, over the block table, then
+// one block decoded.
 struct TriageGrid {
     int64_t ox, oy;
     uint32_t log2_cell, order;
@@ -399,9 +401,10 @@ __device__ __forceinline__ void holds2(const RawList &L0, uint32_t c0, bool on0,
     h1 = r1 && s1 <= c1;
 }
 
-// Whether the decoded block of compressed list L that starts at endpoint
-// 32 b holds cell c: the block's endpoints (its anchor, then 31 gaps read
-// with 16-byte loads, 16-bit or 32-bit) taken as [start, end) pairs.
+// Whether a block of a compressed list (ne of its 32 endpoints in the list)
+// holds cell c: its endpoints (the anchor, then the gaps at gw, read with
+// 16-byte loads, 16-bit or 32-bit) taken as [start, end) pairs.  The 32
+// endpoints of a block are 16 whole intervals.
 template <bool WIDE>
 __device__ __forceinline__ bool block_holds(const uint4 *gw, uint32_t anchor, uint32_t ne, uint32_t c) {
     constexpr uint32_t PER = WIDE ? 4u : 8u, WORDS = 32u / PER;
