@@ -12,8 +12,10 @@ run with the library's default tuning.  The same JSON line carries:
   - the plain one-pair-per-thread and one-pair-per-warp kernels on the same
     pairs (the speed-up of batching), the autotuner's pick, the end-to-end
     number through the host-buffer entry point, the HBM roofline of the
-    dominant kernel (with the ncu DRAM bytes of the same kernel, workload and
-    tuning when profiles/traffic.json has them);
+    batched step (the triage and the lane-group kernel; algorithmic bytes of
+    april_host_filter_searched's model over the step time, with the ncu DRAM
+    bytes of the same kernels, workload and tuning when profiles/traffic.json
+    has them for the current kernel sources);
   - `workloads`: the skewed 10M-pair workload (Pareto radii, lists of 1 to
     ~10^5 intervals) and the partitioned workload (16x16 partitions of order
     14, raw and compressed lists), each with the same figures;
