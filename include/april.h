@@ -408,7 +408,14 @@ april_status april_filter_pairs_host(april_ctx *ctx, const april_dev_sets *R, co
  *     then whether every A(r) interval lies inside one F(s) interval
  *     (APRIL_TRUE_HIT: r is within s) or not (APRIL_INCONCLUSIVE).
  * Other arguments and the scratch size are those of april_filter_pairs with
- * APRIL_MODE_BATCHED; the context's cta_threshold applies. */
+ * APRIL_MODE_BATCHED; the context's cta_threshold applies.  For
+ * APRIL_PREDICATE_INTERSECTS on different orders with no long-pair threshold
+ * (the default tuning), triage_off 0, and sets built from polygons on one
+ * grid each with the same origin and extent (grid_ox, grid_oy and
+ * grid_log2_cell + order equal), a first pass settles as APRIL_TRUE_HIT the
+ * pairs whose MBR-intersection centre lies in a coarse cell c of the coarse
+ * side's F-list while the finer side's A-list meets the fine cells of c; the
+ * verdicts are the same. */
 #define APRIL_PREDICATE_INTERSECTS 0
 #define APRIL_PREDICATE_WITHIN 1
 april_status april_filter_pairs_ex(april_ctx *ctx, const april_dev_sets *R, const april_dev_sets *S,

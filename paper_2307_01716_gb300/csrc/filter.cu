@@ -583,6 +583,75 @@ __global__ void __launch_bounds__(256, APRIL_TRIAGE_MIN_BLOCKS) k_triage(SetsT R
     }
 }
 
+// K2c: the triage of the different-granularity filter (Sec. 5.3).  For a
+// pair whose MBR-intersection centre lies in cell c of the coarser set's
+// grid, c in the coarse side's F-list and an interval of the finer side's
+// A-list meeting the fine cells of c (ids c << sh to ((c + 1) << sh) - 1 on
+// nested grids, the coarsening the plan applies) mean that the plan's F join
+// (the finer side's A, coarsened, against the coarse side's F) has an overlap,
+// and with it the AA join: a true hit.  The other pairs are listed for the
+// variant kernel; out-of-range ids get error verdicts.  One thread per pair.
+__device__ __forceinline__ bool list_meets(const RawList &L, uint32_t lo, uint32_t hi) {
+    if (!L.n) return false;  // whether an interval has last cell >= lo and start <= hi
+    uint32_t a = 0, b = L.keys_n();
+    while (a < b) {
+        const uint32_t m = (a + b) >> 1;
+        if (L.key(m) < lo) a = m + 1;
+        else b = m;
+    }
+    uint32_t i = L.start_of(a), j = min(L.n, i + 16u);
+    while (i < j) {
+        const uint32_t m = (i + j) >> 1;
+        if (__ldg(&L.p[m].y) - 1u < lo) i = m + 1;
+        else j = m;
+    }
+    return i < L.n && __ldg(&L.p[i].x) <= hi;
+}
+
+__global__ void __launch_bounds__(256) k_triage_coarse(RawSets R, RawSets S, const int4 *__restrict__ mbr_r,
+                                                       const int4 *__restrict__ mbr_s, TriageGrid g,
+                                                       HilbertLut lut_in, uint32_t sh, bool r_finer,
+                                                       const uint32_t *__restrict__ pr,
+                                                       const uint32_t *__restrict__ ps, uint64_t n,
+                                                       uint8_t *__restrict__ out, uint32_t *status, uint32_t *rest,
+                                                       uint32_t *counters) {
+    __shared__ uint8_t lut[64];
+    if (threadIdx.x < 64) lut[threadIdx.x] = lut_in.e[threadIdx.x];
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t kb = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); kb < n; kb += stride) {
+        const uint64_t k = kb + lane;
+        bool keep = false;
+        if (k < n) {
+            const uint32_t r = __ldg(pr + k), s = __ldg(ps + k);
+            if (r < R.n() && s < S.n()) {
+                uint32_t c = 0;
+                bool hit = false;
+                if (triage_cell(mbr_r, mbr_s, g, lut, r, s, c)) {
+                    const uint4 dr = R.load(r), ds = S.load(s);
+                    const uint32_t lo = c << sh, hi = ((c + 1) << sh) - 1u;  // wraps to 2^32 - 1 at the top
+                    hit = r_finer ? list_meets(S.list(ds, true), c, c) && list_meets(R.list(dr, false), lo, hi)
+                                  : list_meets(R.list(dr, true), c, c) && list_meets(S.list(ds, false), lo, hi);
+                }
+                keep = !hit;
+                if (hit) out[k] = APRIL_TRUE_HIT;
+            } else {
+                out[k] = APRIL_VERDICT_ERROR;
+                atomicOr(status, ST_BAD_ID);
+            }
+        }
+        const uint32_t mask = __ballot_sync(kFull, keep);
+        if (mask) {
+            const uint32_t leader = __ffs(mask) - 1;
+            uint32_t pos = 0;
+            if (lane == leader) pos = atomicAdd(&counters[C_REST_COUNT], __popc(mask));
+            pos = __shfl_sync(kFull, pos, leader) + __popc(mask & ((1u << lane) - 1u));
+            if (keep) rest[pos] = (uint32_t)k;
+        }
+    }
+}
+
 // ------------------------------------------ K3: persistent filter (batched)
 // Group engine.  A warp is split into 32/G groups of G lanes; each group
 // filters one pair at a time (its joins in the tuned order, see
@@ -1102,7 +1171,8 @@ __global__ void __launch_bounds__(kBlock, APRIL_GENERAL_MIN_BLOCKS) k_general(Pl
                                                     const uint32_t *__restrict__ ps, uint64_t n,
                                                     uint8_t *__restrict__ out, uint32_t *status,
                                                     uint32_t cta_threshold, const uint32_t *__restrict__ big_list,
-                                                    uint32_t *counters, uint32_t long_window) {
+                                                    uint32_t *counters, uint32_t long_window,
+                                                    const uint32_t *__restrict__ rest) {
     __shared__ __align__(16) uint2 sm[kSharedIv];
     __shared__ uint32_t s_item, s_slot;
     __shared__ uint64_t bars[1 + kWarpsPerBlock];
@@ -1149,13 +1219,16 @@ __global__ void __launch_bounds__(kBlock, APRIL_GENERAL_MIN_BLOCKS) k_general(Pl
         }
         __syncthreads();
     }
-    const uint64_t nchunks = (n + 31) / 32;
+    // the pairs: all n, or the ones the coarse triage left (rest)
+    const uint64_t nn = rest ? (uint64_t)*((volatile uint32_t *)&counters[C_REST_COUNT]) : n;
+    const uint64_t nchunks = (nn + 31) / 32;
     for (;;) {
         uint32_t c = 0;
         if (lane == 0) c = atomicAdd(&counters[C_CHUNK_HEAD], 1u);
         c = __shfl_sync(kFull, c, 0);
         if (c >= nchunks) break;
-        const uint64_t k = (uint64_t)c * 32 + lane;
+        const uint64_t q = (uint64_t)c * 32 + lane;
+        const uint64_t k = q < nn ? (rest ? (uint64_t)__ldg(rest + q) : q) : n;
         uint4 dr = make_uint4(0, 0, 0, 0), ds = make_uint4(0, 0, 0, 0);
         bool take = false;
         if (k < n) {
@@ -1824,10 +1897,28 @@ extern "C" april_status april_filter_pairs_ex(april_ctx *ctx, const april_dev_se
     const unsigned grid_main = (unsigned)std::max(1, ctx->num_sms * std::max(bps, 1));
     cudaError_t e = cudaMemsetAsync(counters, 0, kCounterBytes, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    k_bin<<<grid_bin, 256, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, ctx->d_status, ctx->tune.cta_threshold, big_list,
-                                    counters);
-    k_general<<<grid_main, kBlock, 0, st>>>(P, dR.s, dS.s, d_r, d_s, n, d_verdict, ctx->d_status,
-                                            ctx->tune.cta_threshold, big_list, counters, ctx->tune.cta_window);
+    // the coarse triage (K2c): sets built from polygons on nested grids (same
+    // origin and extent), no long-pair threshold
+    const april_tune &t = ctx->tune;
+    const bool coarse_triage = predicate == APRIL_PREDICATE_INTERSECTS && R->order != S->order && !t.triage_off &&
+                               t.cta_threshold == kNoLongPairs && R->grid_known && S->grid_known && !R->parts && !S->parts && R->mbr &&
+                               S->mbr && R->grid_ox == S->grid_ox && R->grid_oy == S->grid_oy &&
+                               R->grid_log2_cell + R->order == S->grid_log2_cell + S->order;
+    const uint32_t *rest = nullptr;
+    if (coarse_triage) {
+        const april_dev_sets *C = R->order < S->order ? R : S;
+        const uint32_t sh = 2 * (R->order > S->order ? R->order - S->order : S->order - R->order);
+        k_triage_coarse<<<grid_bin, 256, 0, st>>>(dR, dS, (const int4 *)R->mbr, (const int4 *)S->mbr,
+                                                  TriageGrid{C->grid_ox, C->grid_oy, C->grid_log2_cell, C->order},
+                                                  triage_lut(), sh, R->order > S->order, d_r, d_s, n, d_verdict,
+                                                  ctx->d_status, big_list, counters);
+        rest = big_list;
+    } else {
+        k_bin<<<grid_bin, 256, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, ctx->d_status, t.cta_threshold, big_list,
+                                        counters);
+    }
+    k_general<<<grid_main, kBlock, 0, st>>>(P, dR.s, dS.s, d_r, d_s, n, d_verdict, ctx->d_status, t.cta_threshold,
+                                            big_list, counters, t.cta_window, rest);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return APRIL_OK;

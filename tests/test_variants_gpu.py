@@ -2,7 +2,8 @@
 oracle, bit-exact: intersects on equal orders (Algorithm 2), on grids of
 different order with either side the finer one (Sec. 5.3), and the within
 filter (Sec. 4.3.2); configs 1-3 at reduced sizes with every pair checked,
-both execution paths (whole-CTA joins and warp joins), config 2 at full size
+both execution paths (whole-CTA joins and warp joins), the coarse-grid
+triage on and off, config 2 at full size
 on a sampled subset plus agreement with the host execution on every pair,
 and the argument checks."""
 import numpy as np
@@ -77,6 +78,26 @@ def test_variants_both_paths(torch_cuda, ctx, threshold, long_window):
             got = run_ex(torch_cuda, ctx, dR, dS, w.pr, w.ps, pred)
             want = _data.oracle_verdicts_ex(2, 0.01, o_r, o_s, pred)
             assert np.array_equal(got, want), ((o_r, o_s), pred, threshold)
+    finally:
+        ctx.set_tune(saved)
+
+
+def test_variants_coarse_triage_on_and_off(torch_cuda, ctx):
+    """On different orders the default tuning runs the coarse-grid triage
+    first (Sec. 5.3 coarsening on nested global grids); with triage_off the
+    variant kernel joins every pair.  Both equal the oracle."""
+    w = _data.workload(2, 0.01)
+    saved = ctx.get_tune()
+    try:
+        for off in (0, 1):
+            t = ctx.get_tune()
+            t.triage_off = off
+            ctx.set_tune(t)
+            for o_r, o_s in [(w.order, w.order - 2), (w.order - 2, w.order), (w.order, w.order - 4)]:
+                _, _, dR, dS = _sets(w, o_r, o_s)
+                got = run_ex(torch_cuda, ctx, dR, dS, w.pr, w.ps, 0)
+                want = _data.oracle_verdicts_ex(2, 0.01, o_r, o_s, 0)
+                assert np.array_equal(got, want), ((o_r, o_s), off, np.nonzero(got != want)[0][:10])
     finally:
         ctx.set_tune(saved)
 
