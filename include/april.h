@@ -308,8 +308,9 @@ typedef struct april_tune {
                                 this many windows is handed, at the position it reached, to a
                                 second kernel that joins it by a whole warp (first window
                                 2 * cta_window when that is below 256, else 128) */
-    uint32_t triage_off;     /* 0 (default): with no long-pair threshold, lane groups of 4..16 and raw
-                                sets built from polygons on one grid (grid_known, same grid), a
+    uint32_t triage_off;     /* 0 (default): with no long-pair threshold, lane groups of 4..16 and
+                                sets built from polygons on the same grid(s) (grid_known, equal
+                                grid_id; raw or compressed, one grid or partitioned), a
                                 triage pass first settles the pairs whose MBR-intersection centre
                                 cell lies in A(r) and F(s) or in F(r) and A(s) (true hits); 1: off */
 } april_tune;
@@ -383,11 +384,16 @@ april_status april_filter_pairs(april_ctx *ctx, const april_dev_sets *R, const a
  * memory makes the copies asynchronous DMA); d_work is a caller-allocated
  * device buffer of april_filter_host_work_bytes() bytes (256-byte aligned)
  * that holds the staged pairs, the verdicts and the mode's scratch.  In the
- * batched modes the pairs are pipelined in up to 8 chunks of at least 2^22
- * pairs: a chunk's pairs are copied in while the previous chunk is filtered
- * and its verdicts copied out while the next is, on streams of the context
- * (created on first use) that follow the work queued on `stream` before the
- * call and that `stream` waits for.  The verdicts are those of one
+ * batched modes the pairs are pipelined in up to 8 chunks, on streams of the
+ * context (created on first use) that follow the work queued on `stream`
+ * before the call and that `stream` waits for.  Where the triage runs (see
+ * april_tune.triage_off), the chunks double from 2^18 to 2^21
+ * pairs (the last takes what is left), each is triaged as soon as it has
+ * been copied in while the next one is, and one lane-group launch over the
+ * pairs left follows before the verdicts are copied out.  Otherwise the
+ * chunks hold at least 2^22 pairs, and a chunk's pairs are copied in while
+ * the previous chunk is filtered and its verdicts copied out while the next
+ * is.  The verdicts are those of one
  * april_filter_pairs call over all n pairs.  Returns the same codes as
  * april_filter_pairs followed by april_sync_status. */
 april_status april_filter_host_work_bytes(int mode, uint64_t n, size_t *bytes);

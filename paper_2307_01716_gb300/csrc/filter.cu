@@ -499,9 +499,10 @@ __device__ __forceinline__ bool triage_cell(const int4 *__restrict__ mbr_r, cons
 // then F(s) and, where it holds the cell, A(r); then F(r) and A(s) for the
 // pairs not settled yet.  Over partitioned sets (PART, Sec. 5.2) the pairs'
 // entries come from the routing (er, es), the MBRs from the objects (pr, ps),
-// and the grid from the entry's partition.  Six CTAs per SM (at most 40
-// registers a thread): the kernel waits on chains of dependent loads, and
-// more threads hide more.
+// and the grid from the entry's partition.  The rest list holds pair indices
+// plus k_base (a launch over one chunk of a longer pair array).  Six CTAs per
+// SM (at most 40 registers a thread): the kernel waits on chains of dependent
+// loads, and more threads hide more.
 #ifndef APRIL_TRIAGE_MIN_BLOCKS
 #define APRIL_TRIAGE_MIN_BLOCKS 6
 #endif
@@ -519,7 +520,8 @@ __global__ void __launch_bounds__(256, APRIL_TRIAGE_MIN_BLOCKS) k_triage(SetsT R
                                                                           const uint32_t *__restrict__ pr,
                                                                           const uint32_t *__restrict__ ps, uint64_t n,
                                                                           uint8_t *__restrict__ out, uint32_t *status,
-                                                                          uint32_t *rest, uint32_t *counters) {
+                                                                          uint32_t *rest, uint32_t *counters,
+                                                                          uint32_t k_base) {
     __shared__ uint8_t lut[64];
     if (threadIdx.x < 64) lut[threadIdx.x] = lut_in.e[threadIdx.x];
     __syncthreads();
@@ -577,7 +579,7 @@ __global__ void __launch_bounds__(256, APRIL_TRIAGE_MIN_BLOCKS) k_triage(SetsT R
                 uint32_t pos = 0;
                 if (lane == leader) pos = atomicAdd(&counters[C_REST_COUNT], __popc(mask));
                 pos = __shfl_sync(kFull, pos, leader) + __popc(mask & ((1u << lane) - 1u));
-                if (keep) rest[pos] = (uint32_t)k[h];
+                if (keep) rest[pos] = (uint32_t)k[h] + k_base;
             }
         }
     }
@@ -1622,6 +1624,11 @@ static TriageArgs triage_args(const april_dev_sets *R, const april_dev_sets *S, 
     return a;
 }
 
+static cudaError_t enqueue_groups(april_ctx *ctx, const april_dev_sets *Rd, const april_dev_sets *Sd,
+                                  const uint32_t *d_r, const uint32_t *d_s, uint64_t n, uint8_t *out, void *scratch,
+                                  bool packed, unsigned grid_main, cudaStream_t st, uint32_t *status,
+                                  const uint32_t *rest);
+
 static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, const april_dev_sets *Sd,
                                    const uint32_t *d_r, const uint32_t *d_s, uint64_t n, uint8_t *out, void *scratch,
                                    bool packed, unsigned grid_bin, unsigned grid_main, cudaStream_t st,
@@ -1629,12 +1636,7 @@ static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, con
     if (!status) status = ctx->d_status;
     uint32_t *counters = (uint32_t *)scratch;
     uint32_t *big_list = (uint32_t *)((char *)scratch + kCounterBytes);
-    uint4 *esc = (uint4 *)((char *)scratch + kCounterBytes + 3 * round256(4 * n));
     const april_tune &t = ctx->tune;
-    const uint32_t escw = t.group_lanes < 32 ? t.escalate_windows : 0u;
-    const uint32_t w0_long = t.cta_window < kBlock ? std::min<uint32_t>(2 * t.cta_window, kWarpWMax) : 128u;
-    const uint32_t esc_cap = (uint32_t)esc_capacity(n);
-    const unsigned grid_long = (unsigned)std::max(1, ctx->num_sms * ctx->long_blocks_per_sm);
     cudaError_t e = cudaMemsetAsync(counters, 0, kCounterBytes, st);
     if (e != cudaSuccess) return e;
     const uint32_t *obj_r = d_r, *obj_s = d_s;  // the pairs' objects (their MBRs)
@@ -1647,26 +1649,61 @@ static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, con
         d_r = er;
         d_s = es;
     }
+    const uint32_t *rest = nullptr;  // the pairs the lane groups join (nullptr: all)
     if (packed) {
         const PackedSets R = packed_set(Rd), S = packed_set(Sd);
-        const uint32_t *prest = nullptr;
         if (triage_applies(t, Rd, Sd, true)) {
             if (Rd->parts)
                 k_triage<true, PackedSets><<<grid_bin, 256, 0, st>>>(R, S, triage_args(Rd, Sd, d_r, d_s), triage_lut(),
-                                                                     obj_r, obj_s, n, out, status, big_list, counters);
+                                                                     obj_r, obj_s, n, out, status, big_list, counters,
+                                                                     0u);
             else
                 k_triage<false, PackedSets><<<grid_bin, 256, 0, st>>>(R, S, triage_args(Rd, Sd, nullptr, nullptr),
                                                                       triage_lut(), d_r, d_s, n, out, status, big_list,
-                                                                      counters);
-            prest = big_list;
+                                                                      counters, 0u);
+            rest = big_list;
         } else if (t.cta_threshold != kNoLongPairs) {
             k_bin<<<grid_bin, 256, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold, big_list, counters);
         }
-        const uint32_t jo = join_order_of(t.join_order, prest != nullptr);
+        return enqueue_groups(ctx, Rd, Sd, d_r, d_s, n, out, scratch, true, grid_main, st, status, rest);
+    }
+    const RawSets R{dev_set(Rd)}, S{dev_set(Sd)};
+    if (triage_applies(t, Rd, Sd, false)) {
+        if (Rd->parts)
+            k_triage<true, RawSets><<<grid_bin, 256, 0, st>>>(R, S, triage_args(Rd, Sd, d_r, d_s), triage_lut(), obj_r,
+                                                              obj_s, n, out, status, big_list, counters, 0u);
+        else
+            k_triage<false, RawSets><<<grid_bin, 256, 0, st>>>(R, S, triage_args(Rd, Sd, nullptr, nullptr), triage_lut(),
+                                                               d_r, d_s, n, out, status, big_list, counters, 0u);
+        rest = big_list;
+    } else if (t.cta_threshold != kNoLongPairs) {
+        k_bin<<<grid_bin, 256, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold, big_list, counters);
+    }
+    return enqueue_groups(ctx, Rd, Sd, d_r, d_s, n, out, scratch, false, grid_main, st, status, rest);
+}
+
+// The lane-group stage of the batched pipeline (K3, then K3b when the tuning
+// escalates long joins) over the pairs (d_r, d_s: routed entries for
+// partitioned sets), or over the rest list a triage left.
+static cudaError_t enqueue_groups(april_ctx *ctx, const april_dev_sets *Rd, const april_dev_sets *Sd,
+                                  const uint32_t *d_r, const uint32_t *d_s, uint64_t n, uint8_t *out, void *scratch,
+                                  bool packed, unsigned grid_main, cudaStream_t st, uint32_t *status,
+                                  const uint32_t *rest) {
+    uint32_t *counters = (uint32_t *)scratch;
+    uint32_t *big_list = (uint32_t *)((char *)scratch + kCounterBytes);
+    uint4 *esc = (uint4 *)((char *)scratch + kCounterBytes + 3 * round256(4 * n));
+    const april_tune &t = ctx->tune;
+    const uint32_t escw = t.group_lanes < 32 ? t.escalate_windows : 0u;
+    const uint32_t w0_long = t.cta_window < kBlock ? std::min<uint32_t>(2 * t.cta_window, kWarpWMax) : 128u;
+    const uint32_t esc_cap = (uint32_t)esc_capacity(n);
+    const unsigned grid_long = (unsigned)std::max(1, ctx->num_sms * ctx->long_blocks_per_sm);
+    const uint32_t jo = join_order_of(t.join_order, rest != nullptr);
+    if (packed) {
+        const PackedSets R = packed_set(Rd), S = packed_set(Sd);
 #define APRIL_LAUNCH_PACKED(G)                                                                                  \
     k_persistent<G, PackedSets><<<grid_main, kBlock, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold,   \
                                                               big_list, counters, t.group_window, t.cta_window,   \
-                                                              jo, escw, esc, esc_cap, prest)
+                                                              jo, escw, esc, esc_cap, rest)
         switch (t.group_lanes) {
             case 4: APRIL_LAUNCH_PACKED(4); break;
             case 8: APRIL_LAUNCH_PACKED(8); break;
@@ -1679,19 +1716,6 @@ static cudaError_t enqueue_batched(april_ctx *ctx, const april_dev_sets *Rd, con
         return cudaGetLastError();
     }
     const RawSets R{dev_set(Rd)}, S{dev_set(Sd)};
-    const uint32_t *rest = nullptr;  // the pairs the lane groups join (nullptr: all)
-    if (triage_applies(t, Rd, Sd, false)) {
-        if (Rd->parts)
-            k_triage<true, RawSets><<<grid_bin, 256, 0, st>>>(R, S, triage_args(Rd, Sd, d_r, d_s), triage_lut(), obj_r,
-                                                              obj_s, n, out, status, big_list, counters);
-        else
-            k_triage<false, RawSets><<<grid_bin, 256, 0, st>>>(R, S, triage_args(Rd, Sd, nullptr, nullptr), triage_lut(),
-                                                               d_r, d_s, n, out, status, big_list, counters);
-        rest = big_list;
-    } else if (t.cta_threshold != kNoLongPairs) {
-        k_bin<<<grid_bin, 256, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold, big_list, counters);
-    }
-    const uint32_t jo = join_order_of(t.join_order, rest != nullptr);
 #define APRIL_LAUNCH_PERSISTENT(G)                                                                            \
     k_persistent<G, RawSets><<<grid_main, kBlock, 0, st>>>(R, S, d_r, d_s, n, out, status, t.cta_threshold,       \
                                                            big_list, counters, t.group_window, t.cta_window,      \
@@ -2028,14 +2052,27 @@ static uint64_t pipe_chunk_size(uint64_t n) {
     return ((n + k - 1) / k + 63) / 64 * 64;
 }
 
+// With the triage (K2), the pipeline is finer: the pairs are copied in
+// chunks that double from kTriageChunk0 pairs up to kTriageChunkMax (at most
+// kPipeMaxChunks, the last one taking what is left), and each chunk is
+// triaged on one of two kernel streams as soon as it has arrived, while the
+// next one is copied.  The triage appends to one rest list over all n pairs
+// (indices plus the chunk's offset), so the lane groups then join it in one
+// launch, with no chunk tails, and the verdicts are copied out.  The copies
+// hide behind the triage, which reads about 3 pairs in the time the copy
+// engine brings one in.
+constexpr uint64_t kTriageChunk0 = 1ull << 18;
+constexpr uint64_t kTriageChunkMax = 1ull << 21;
+
 extern "C" april_status april_filter_host_work_bytes(int mode, uint64_t n, size_t *bytes) {
     if (!bytes) return fail(APRIL_ERR_INVALID_ARG, "bytes is NULL");
     size_t sb = 0;
     april_status st = april_filter_scratch_bytes(mode, n, &sb);
     if (st) return st;
     if (mode == APRIL_MODE_BATCHED || mode == APRIL_MODE_BATCHED_PACKED) {
-        april_filter_scratch_bytes(mode, pipe_chunk_size(n), &sb);  // per chunk, one region per kernel stream
-        sb = round256(sb) * (pipe_chunks(n) > 1 ? 2 : 1);
+        size_t sc = 0;  // per chunk, one region per kernel stream; the triage pipeline takes n's
+        april_filter_scratch_bytes(mode, pipe_chunk_size(n), &sc);
+        sb = std::max<size_t>(round256(sb), round256(sc) * (pipe_chunks(n) > 1 ? 2 : 1));
     }
     *bytes = (size_t)(round256(4 * n) * 2 + round256(n) + round256(sb));
     return APRIL_OK;
@@ -2056,6 +2093,72 @@ static april_status ensure_pipeline(april_ctx *ctx) {
         return cuda_fail(e, "creating the host pipeline's streams");
     }
     return APRIL_OK;
+}
+
+// The triage of pairs [off, off + cnt) of a call over n pairs (partition
+// routing first for partitioned sets), appending to the call's rest list.
+template <class SetsT>
+static void enqueue_triage_chunk(april_ctx *ctx, const SetsT &R, const SetsT &S, const april_dev_sets *Rd,
+                                 const april_dev_sets *Sd, const uint32_t *d_r, const uint32_t *d_s, uint64_t n,
+                                 uint64_t off, uint64_t cnt, uint8_t *out, void *scratch, cudaStream_t st) {
+    uint32_t *counters = (uint32_t *)scratch;
+    uint32_t *big_list = (uint32_t *)((char *)scratch + kCounterBytes);
+    const unsigned grid_bin = (unsigned)std::min<uint64_t>((cnt + 255) / 256, (uint64_t)ctx->num_sms * 8);
+    if (Rd->parts) {
+        uint32_t *er = (uint32_t *)((char *)scratch + kCounterBytes + round256(4 * n)) + off;
+        uint32_t *es = (uint32_t *)((char *)scratch + kCounterBytes + 2 * round256(4 * n)) + off;
+        uint32_t lg = 0;
+        while ((1u << lg) < Rd->parts) ++lg;
+        k_route<<<grid_bin, 256, 0, st>>>(part_view(Rd), part_view(Sd), lg, d_r + off, d_s + off, cnt, er, es);
+        k_triage<true, SetsT><<<grid_bin, 256, 0, st>>>(R, S, triage_args(Rd, Sd, er, es), triage_lut(), d_r + off,
+                                                        d_s + off, cnt, out + off, ctx->d_status, big_list, counters,
+                                                        (uint32_t)off);
+    } else {
+        k_triage<false, SetsT><<<grid_bin, 256, 0, st>>>(R, S, triage_args(Rd, Sd, nullptr, nullptr), triage_lut(),
+                                                         d_r + off, d_s + off, cnt, out + off, ctx->d_status, big_list,
+                                                         counters, (uint32_t)off);
+    }
+}
+
+static cudaError_t host_triage_pipeline(april_ctx *ctx, const april_dev_sets *R, const april_dev_sets *S,
+                                        const uint32_t *h_r, const uint32_t *h_s, uint64_t n, uint8_t *h_verdict,
+                                        uint32_t *d_r, uint32_t *d_s, uint8_t *d_v, void *d_scr, bool packed,
+                                        unsigned grid_main) {
+    cudaStream_t s_in = ctx->pipe[0], k1 = ctx->pipe[1], k2 = ctx->pipe[2];
+    cudaError_t e = cudaMemsetAsync(d_scr, 0, kCounterBytes, k1);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->pev[3], k1);  // the counters are reset
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(k2, ctx->pev[3], 0);
+    uint64_t off = 0;
+    for (uint32_t c = 0; off < n && e == cudaSuccess; ++c) {
+        const uint64_t take = c + 1 == kPipeMaxChunks
+                                  ? n - off
+                                  : std::min<uint64_t>(std::min<uint64_t>(kTriageChunk0 << c, kTriageChunkMax), n - off);
+        cudaStream_t ks = c & 1u ? k2 : k1;
+        e = cudaMemcpyAsync(d_r + off, h_r + off, 4 * take, cudaMemcpyHostToDevice, s_in);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_s + off, h_s + off, 4 * take, cudaMemcpyHostToDevice, s_in);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->pev[2 + 2 * c], s_in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ks, ctx->pev[2 + 2 * c], 0);
+        if (e == cudaSuccess) {
+            if (packed)
+                enqueue_triage_chunk(ctx, packed_set(R), packed_set(S), R, S, d_r, d_s, n, off, take, d_v, d_scr, ks);
+            else
+                enqueue_triage_chunk(ctx, RawSets{dev_set(R)}, RawSets{dev_set(S)}, R, S, d_r, d_s, n, off, take, d_v,
+                                     d_scr, ks);
+            e = cudaGetLastError();
+        }
+        off += take;
+    }
+    // the lane groups join the rest list once both kernel streams' triages are done
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->pev[5], k2);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(k1, ctx->pev[5], 0);
+    if (e == cudaSuccess) {
+        const uint32_t *er = (const uint32_t *)((char *)d_scr + kCounterBytes + round256(4 * n));
+        const uint32_t *es = (const uint32_t *)((char *)d_scr + kCounterBytes + 2 * round256(4 * n));
+        e = enqueue_groups(ctx, R, S, R->parts ? er : d_r, R->parts ? es : d_s, n, d_v, d_scr, packed, grid_main, k1,
+                           ctx->d_status, (const uint32_t *)((char *)d_scr + kCounterBytes));
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_verdict, d_v, n, cudaMemcpyDeviceToHost, k1);
+    return e;
 }
 
 extern "C" april_status april_filter_pairs_host(april_ctx *ctx, const april_dev_sets *R, const april_dev_sets *S,
@@ -2108,7 +2211,10 @@ extern "C" april_status april_filter_pairs_host(april_ctx *ctx, const april_dev_
     e = cudaEventRecord(ev_start, cs);
     for (cudaStream_t p : ctx->pipe)
         if (e == cudaSuccess) e = cudaStreamWaitEvent(p, ev_start, 0);
-    for (uint32_t c = 0; c < K && e == cudaSuccess; ++c) {
+    const bool triaged = triage_applies(ctx->tune, R, S, packed);
+    if (triaged && e == cudaSuccess)
+        e = host_triage_pipeline(ctx, R, S, h_r, h_s, n, h_verdict, d_r, d_s, d_v, d_scr, packed, grid_main);
+    for (uint32_t c = 0; c < K && e == cudaSuccess && !triaged; ++c) {
         const uint64_t off = c * cs_n;
         if (off >= n) break;
         const uint64_t cnt = std::min<uint64_t>(cs_n, n - off);
@@ -2259,7 +2365,7 @@ extern "C" april_status april_filter_pairs_noalloc(const april_dev_sets *R, cons
     const uint32_t *rest = nullptr;
     if (triage_applies(t, R, S, false)) {
         k_triage<false, RawSets><<<grid_bin, 256, 0, st>>>(dR, dS, triage_args(R, S, nullptr, nullptr), triage_lut(),
-                                                           d_r, d_s, n, d_verdict, status, big_list, counters);
+                                                           d_r, d_s, n, d_verdict, status, big_list, counters, 0u);
         rest = big_list;
     } else if (t.cta_threshold != kNoLongPairs) {
         k_bin<<<grid_bin, 256, 0, st>>>(dR, dS, d_r, d_s, n, d_verdict, status, t.cta_threshold, big_list, counters);

@@ -1,10 +1,12 @@
 """The end-to-end entry point april_filter_pairs_host (GPU only): host pairs in,
-host verdicts out.  In the batched modes it pipelines the pairs in chunks of
-at least 2^22 over two kernel streams; its verdicts must equal host
-Algorithm 2 (which the CPU tests pin to the oracle) pair for pair whether the
-call takes one chunk or several with a ragged last one, on raw, compressed
-and partitioned sets, and bad ids in a later chunk must give error verdicts
-and the OUT_OF_RANGE_ID status."""
+host verdicts out.  In the batched modes it pipelines the pairs: with the
+triage, in chunks doubling from 2^18 to 2^21 pairs, each triaged as it
+arrives, then one lane-group launch over the rest list; without it, in
+chunks of at least 2^22 over two kernel streams.  Its verdicts must equal
+host Algorithm 2 (which the CPU tests pin to the oracle) pair for pair
+whether the call takes one chunk or several with a ragged last one, on raw,
+compressed and partitioned sets, with the triage on and off, and bad ids in
+a later chunk must give error verdicts and the OUT_OF_RANGE_ID status."""
 import numpy as np
 import pytest
 
@@ -13,7 +15,7 @@ from paper_2307_01716_gb300 import april as A
 
 pytestmark = pytest.mark.gpu
 
-CHUNK = 1 << 22  # the pipeline's smallest chunk
+CHUNK = 1 << 22  # the smallest chunk of the pipeline without the triage
 
 
 @pytest.fixture(scope="module")
@@ -82,6 +84,23 @@ def test_host_path_single_kernel_modes(torch_cuda, ctx, global_sets, mode):
     pr, ps = _tiled(w, 20_000, 5)
     want, _ = A.april_host_filter(R, S, pr, ps)
     got = _host_call(torch_cuda, ctx, A.april_upload(R), A.april_upload(S), pr, ps, mode)
+    assert np.array_equal(got, want)
+
+
+def test_host_path_without_triage(torch_cuda, ctx, global_sets):
+    """triage_off: chunks of at least 2^22 pairs, each filtered whole."""
+    w, R, S = global_sets
+    n = 2 * CHUNK + 12345
+    pr, ps = _tiled(w, n, 17)
+    want, _ = A.april_host_filter(R, S, pr, ps)
+    saved = ctx.get_tune()
+    t = ctx.get_tune()
+    t.triage_off = 1
+    ctx.set_tune(t)
+    try:
+        got = _host_call(torch_cuda, ctx, A.april_upload(R), A.april_upload(S), pr, ps, A.MODE_BATCHED)
+    finally:
+        ctx.set_tune(saved)
     assert np.array_equal(got, want)
 
 
