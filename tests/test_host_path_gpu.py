@@ -104,12 +104,17 @@ def test_host_path_without_triage(torch_cuda, ctx, global_sets):
     assert np.array_equal(got, want)
 
 
-def test_host_path_partitioned(torch_cuda, ctx):
+@pytest.mark.parametrize("packed", [False, True])
+def test_host_path_partitioned(torch_cuda, ctx, packed):
     w = _data.workload(4, 0.02)
     R, S = A.april_build_partitioned_sets(w.R.xy, w.R.off, w.S.xy, w.S.off, w.partitions, w.order)
     pr, ps = _tiled(w, CHUNK + 777, 9)
     want, _ = A.april_host_filter(R, S, pr, ps)
-    got = _host_call(torch_cuda, ctx, A.april_upload(R), A.april_upload(S), pr, ps, A.MODE_BATCHED)
+    if packed:
+        R.compress()
+        S.compress()
+    mode = A.MODE_BATCHED_PACKED if packed else A.MODE_BATCHED
+    got = _host_call(torch_cuda, ctx, A.april_upload(R), A.april_upload(S), pr, ps, mode)
     assert np.array_equal(got, want)
 
 
