@@ -38,3 +38,24 @@ def test_no_device_error_paths():
         A.check(A.load().april_filter_scratch_bytes(99, 10, ctypes.byref(ctypes.c_size_t())))
     assert e.value.status == -1
     assert A.load().april_filter_pairs(None, None, None, None, None, 0, None, 0, None, 0, None) == -1
+
+
+def test_host_work_bytes_cover_both_pipelines():
+    """april_filter_host_work_bytes (no device needed) leaves room for the
+    staged pairs and verdicts plus the batched scratch of all n pairs (the
+    triage pipeline's one rest list) and of two chunks (the chunk-whole
+    pipeline); the other modes need the pairs and verdicts only."""
+    L = A.load()
+
+    def q(fn, mode, n):
+        b = ctypes.c_size_t()
+        A.check(fn(mode, n, ctypes.byref(b)))
+        return b.value
+
+    for n in (1, 1000, (1 << 18) + 5, (1 << 22) - 1, 1 << 22, 3 * (1 << 22) + 77, 10_000_000):
+        for mode in (A.MODE_BATCHED, A.MODE_BATCHED_PACKED):
+            work = q(L.april_filter_host_work_bytes, mode, n)
+            assert work >= 9 * n + q(L.april_filter_scratch_bytes, mode, n)
+        for mode in (A.MODE_PLAIN, A.MODE_WARP):
+            assert q(L.april_filter_scratch_bytes, mode, n) == 0
+            assert q(L.april_filter_host_work_bytes, mode, n) >= 9 * n
