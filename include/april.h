@@ -342,8 +342,9 @@ april_status april_autotune(april_ctx *ctx, const april_dev_sets *R, const april
 
 /* Device scratch (bytes) april_filter_pairs needs for `mode` and n pairs.
  * PLAIN and WARP need none; BATCHED and BATCHED_PACKED need 256 bytes of
- * work counters plus 16 bytes per pair (the list of long pairs, for
- * partitioned sets each pair's two routed entries, and a queue of joins
+ * work counters plus 16 bytes per pair (the list of long pairs or of the
+ * pairs the triage left, for partitioned sets each pair's two routed
+ * entries, and a queue of joins
  * handed from the lane groups to whole warps with room for a quarter of the
  * pairs), each part rounded up to 256 bytes. */
 april_status april_filter_scratch_bytes(int mode, uint64_t n, size_t *bytes);
@@ -359,14 +360,16 @@ april_status april_filter_scratch_bytes(int mode, uint64_t n, size_t *bytes);
  *              sets (april_build_partitioned_sets) need one of the BATCHED
  *              modes: each pair is first routed to the partition of the
  *              lower-left corner of MBR(r) n MBR(s) (Sec. 5.2).  BATCHED_PACKED
- *              needs compressed sets (april_sets_compress) and joins with
- *              whole warps (groups of 32 lanes) and CTAs.
+ *              needs compressed sets (april_sets_compress) and decodes their
+ *              blocks while the same kernels join them.
  *   d_scratch  device scratch of april_filter_scratch_bytes() bytes
  *              (256-byte aligned), or NULL when that is 0.
  *   stream     cudaStream_t (void*); all work is enqueued on it.
  *
- * APRIL_MODE_BATCHED enqueues a CUDA graph (counter reset, length binning,
- * persistent filter) that is captured on first use of an argument set and
+ * APRIL_MODE_BATCHED enqueues a CUDA graph (counter reset, partition
+ * routing for partitioned sets, the triage or the length binning as the
+ * tuning says, the persistent lane-group filter) that is captured on first
+ * use of an argument set and
  * replayed afterwards; the context's tuning (april_set_tune /
  * april_autotune) applies.  Calls on one context must not overlap in time
  * from several host threads.
